@@ -1,0 +1,295 @@
+"""FP64 CPU oracle for point-based Gaussian ray tracing -- TEST INFRASTRUCTURE.
+
+Only tests/, the CUDA-path smoke check (``__graft_entry__.smoke``) and the CPU
+baseline of ``bench.py`` may import this package.  It is a plain, slow,
+obviously-correct restatement of the method (see ``rt_oracle.c`` for the
+passage each function follows) and shares no code with the CUDA library.
+
+``build()`` compiles ``rt_oracle.c`` with gcc (OpenMP, ``-ffp-contract=off``)
+into ``oracle/_build/``; the numpy wrappers below call it through ctypes.
+
+Parity status: every function here is pinned by tests/test_oracle_*.py
+(closed forms, invariants, brute force, an independent numpy formulation,
+finite differences, library routines), except the surrogate's visibility MAE,
+which has no reference value (parity unpinned: the bar is MAE <= 0.01 against
+the tracer).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_SRC = os.path.join(_HERE, "rt_oracle.c")
+_lock = threading.Lock()
+_lib = None
+
+# band flag bits of oracle_trace
+FLAG_M2, FLAG_ALPHA, FLAG_T, FLAG_TMIN = 1, 2, 4, 8
+# default band widths: m^2 within 1e-4 of K^2 (FP32 m^2 error of flattened
+# Gaussians seen from far away), alpha within 1e-6 of the cutoff, t* within
+# 1e-6 of 0, T within 1e-7 of T_min.
+DEFAULT_BANDS = dict(band_m2=1e-4, band_alpha=1e-6, band_t=1e-6, band_T=1e-7)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library (idempotent)."""
+    with _lock:
+        if (not force and os.path.exists(_SO)
+                and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)):
+            return _SO
+        os.makedirs(_BUILD, exist_ok=True)
+        tmp = _SO + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-std=c11", "-D_GNU_SOURCE", "-O2", "-fopenmp", "-ffp-contract=off",
+               "-fno-fast-math", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _SO)
+        return _SO
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        path = build()
+        lib = C.CDLL(path)
+        P = C.c_void_p
+        i64, i32, u32, f32, f64 = C.c_int64, C.c_int32, C.c_uint32, C.c_float, C.c_double
+        sig = {
+            "oracle_rotation": (None, [P, P]),
+            "oracle_trace": (None, [i64, P, P, P, P, i64, P, P, P, f64, f64, f64,
+                                    f64, f64, f64, f64, P, P, P, P]),
+            "oracle_trace_hits": (None, [i64, P, P, P, P, i64, P, P, P, f64, f64, i32, P, P]),
+            "oracle_trace_grad": (None, [i64, P, P, P, P, i64, P, P, P, f64, f64, f64,
+                                         P, P, P, P, P, P]),
+            "oracle_dir_rays": (None, [i64, P, i32, P, f32, P, i64, P, P, P]),
+            "oracle_philox": (None, [P, P, P]),
+            "oracle_env_rays": (None, [i64, P, i32, i32, P, P, P, u32, i32, f32, P, i64, P, P, P]),
+            "oracle_morton": (None, [i64, P, P, P, P]),
+            "oracle_lbvh": (None, [i64, P, P, P, P, P]),
+            "oracle_leaf_boxes": (None, [i64, P, P, P, P, f64, f64, i32, P]),
+            "oracle_bf16_round": (None, [i64, P, P]),
+            "oracle_mlp_encode": (None, [i64, P, P, P, P, P]),
+            "oracle_mlp_nparam": (i64, []),
+            "oracle_mlp_set_bf16": (None, [i32]),
+            "oracle_mlp_forward": (None, [P, i64, P, P, P]),
+            "oracle_mlp_loss_grad": (f64, [P, i64, P, P, P]),
+            "oracle_adam_step": (None, [i64, P, P, P, P, i64, f64, f64, f64, f64]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(np.asarray(a, dtype=dt))
+
+
+def _scene(sc):
+    """Scene arrays widened to float64 (exact for float32 inputs)."""
+    return (_c(sc["mean"], np.float64), _c(sc["scale"], np.float64),
+            _c(sc["quat"], np.float64), _c(sc["opacity"], np.float64))
+
+
+def rotation(q) -> np.ndarray:
+    q = _c(q, np.float64)
+    R = np.empty(9, np.float64)
+    _load().oracle_rotation(_p(q), _p(R))
+    return R.reshape(3, 3)
+
+
+def trace(scene, ray_o, ray_d, ray_src=None, k_sigma=3.0, alpha_min=1.0 / 255.0,
+          t_min=1e-4, bands=None):
+    """Brute-force visibility.  Returns dict(T, T_exact, hits, flags)."""
+    mean, scale, quat, opac = _scene(scene)
+    ray_o = _c(ray_o, np.float64).reshape(-1, 3)
+    ray_d = _c(ray_d, np.float64).reshape(-1, 3)
+    R = ray_o.shape[0]
+    src = None if ray_src is None else _c(ray_src, np.int32)
+    b = dict(DEFAULT_BANDS)
+    if bands:
+        b.update(bands)
+    T = np.empty(R, np.float64)
+    Te = np.empty(R, np.float64)
+    hits = np.empty(R, np.int32)
+    flags = np.empty(R, np.uint32)
+    _load().oracle_trace(mean.shape[0], _p(mean), _p(scale), _p(quat), _p(opac), R, _p(ray_o),
+                         _p(ray_d), _p(src), k_sigma, alpha_min, t_min, b["band_m2"],
+                         b["band_alpha"], b["band_t"], b["band_T"], _p(T), _p(Te), _p(hits),
+                         _p(flags))
+    return {"T": T, "T_exact": Te, "hits": hits, "flags": flags}
+
+
+def trace_hits(scene, ray_o, ray_d, ray_src=None, k_sigma=3.0, alpha_min=1.0 / 255.0, cap=256):
+    """Accepted Gaussian ids per ray: (ids[R, cap] int32, count[R] int32)."""
+    mean, scale, quat, opac = _scene(scene)
+    ray_o = _c(ray_o, np.float64).reshape(-1, 3)
+    ray_d = _c(ray_d, np.float64).reshape(-1, 3)
+    R = ray_o.shape[0]
+    src = None if ray_src is None else _c(ray_src, np.int32)
+    ids = np.full((R, cap), -1, np.int32)
+    cnt = np.empty(R, np.int32)
+    _load().oracle_trace_hits(mean.shape[0], _p(mean), _p(scale), _p(quat), _p(opac), R,
+                              _p(ray_o), _p(ray_d), _p(src), k_sigma, alpha_min, cap, _p(ids),
+                              _p(cnt))
+    return ids, cnt
+
+
+def trace_grad(scene, ray_o, ray_d, ray_src, dL_dT, k_sigma=3.0, alpha_min=1.0 / 255.0,
+               t_min=0.0, with_origin=False):
+    """Analytic FP64 gradient of L = sum_r dL_dT[r] T[r]."""
+    mean, scale, quat, opac = _scene(scene)
+    ray_o = _c(ray_o, np.float64).reshape(-1, 3)
+    ray_d = _c(ray_d, np.float64).reshape(-1, 3)
+    R = ray_o.shape[0]
+    n = mean.shape[0]
+    src = None if ray_src is None else _c(ray_src, np.int32)
+    g = _c(dL_dT, np.float64)
+    out = {"mean": np.empty((n, 3)), "scale": np.empty((n, 3)), "quat": np.empty((n, 4)),
+           "opacity": np.empty(n)}
+    dro = np.empty((R, 3)) if with_origin else None
+    _load().oracle_trace_grad(n, _p(mean), _p(scale), _p(quat), _p(opac), R, _p(ray_o),
+                              _p(ray_d), _p(src), k_sigma, alpha_min, t_min, _p(g),
+                              _p(out["mean"]), _p(out["scale"]), _p(out["quat"]),
+                              _p(out["opacity"]), _p(dro))
+    if with_origin:
+        out["ray_o"] = dro
+    return out
+
+
+def dir_rays(mean, dirs, ids, eps=1e-4):
+    """Float32 rays (o, d, src) for ray ids r = g*K + k (Sec. 4.2 ray set)."""
+    mean = _c(mean, np.float32)
+    dirs = _c(dirs, np.float32)
+    ids = _c(ids, np.int64)
+    m = ids.shape[0]
+    o = np.empty((m, 3), np.float32)
+    d = np.empty((m, 3), np.float32)
+    s = np.empty(m, np.int32)
+    _load().oracle_dir_rays(mean.shape[0], _p(mean), dirs.shape[0], _p(dirs), eps, _p(ids), m,
+                            _p(o), _p(d), _p(s))
+    return o, d, s
+
+
+def philox(counter, key) -> np.ndarray:
+    """Philox4x64-10 block: 4 uint64 outputs of counter[4], key[2]."""
+    c = _c(counter, np.uint64)
+    k = _c(key, np.uint64)
+    out = np.empty(4, np.uint64)
+    _load().oracle_philox(_p(c), _p(k), _p(out))
+    return out
+
+
+def env_rays(mean, env, seed, samples_per_gaussian, ids, eps=1e-4):
+    """Float32 shadow rays importance-sampled from env (scenes.envmap dict)."""
+    mean = _c(mean, np.float32)
+    rad = _c(env["radiance"], np.float64)
+    sa = _c(env["solid_angle"], np.float64)
+    cor = _c(env["corners"], np.float32)
+    h, w = rad.shape
+    ids = _c(ids, np.int64)
+    m = ids.shape[0]
+    o = np.empty((m, 3), np.float32)
+    d = np.empty((m, 3), np.float32)
+    s = np.empty(m, np.int32)
+    _load().oracle_env_rays(mean.shape[0], _p(mean), h, w, _p(rad), _p(sa), _p(cor), seed,
+                            samples_per_gaussian, eps, _p(ids), m, _p(o), _p(d), _p(s))
+    return o, d, s
+
+
+def morton(mean):
+    mean = _c(mean, np.float32)
+    n = mean.shape[0]
+    codes = np.empty(n, np.uint32)
+    lo = np.empty(3, np.float32)
+    hi = np.empty(3, np.float32)
+    _load().oracle_morton(n, _p(mean), _p(codes), _p(lo), _p(hi))
+    return codes, lo, hi
+
+
+def lbvh(mean):
+    """CPU twin of the LBVH topology: dict(keys, left, right, parent)."""
+    mean = _c(mean, np.float32)
+    n = mean.shape[0]
+    keys = np.empty(max(n, 1), np.uint64)[:n]
+    left = np.empty(max(n - 1, 1), np.int32)[:max(n - 1, 0)]
+    right = np.empty(max(n - 1, 1), np.int32)[:max(n - 1, 0)]
+    parent = np.empty(max(2 * n - 1, 1), np.int32)[:max(2 * n - 1, 0)]
+    _load().oracle_lbvh(n, _p(mean), _p(keys), _p(left), _p(right), _p(parent))
+    return {"keys": keys, "left": left, "right": right, "parent": parent}
+
+
+def leaf_boxes(scene, k_sigma=3.0, alpha_min=1.0 / 255.0, box_mode=0):
+    mean, scale, quat, opac = _scene(scene)
+    n = mean.shape[0]
+    box = np.empty((n, 6), np.float64)
+    _load().oracle_leaf_boxes(n, _p(mean), _p(scale), _p(quat), _p(opac), k_sigma, alpha_min,
+                              box_mode, _p(box))
+    return box
+
+
+def bf16_round(x) -> np.ndarray:
+    x = _c(x, np.float64)
+    y = np.empty_like(x)
+    _load().oracle_bf16_round(x.size, _p(x), _p(y))
+    return y
+
+
+MLP_IN, MLP_H = 80, 128
+
+
+def mlp_set_bf16(on: bool) -> None:
+    """Switch bf16 emulation (default on); off gives an exact FP64 MLP."""
+    _load().oracle_mlp_set_bf16(1 if on else 0)
+
+
+def mlp_nparam() -> int:
+    return int(_load().oracle_mlp_nparam())
+
+
+def mlp_encode(pos, dirs, lo, hi) -> np.ndarray:
+    pos = _c(pos, np.float32).reshape(-1, 3)
+    dirs = _c(dirs, np.float32).reshape(-1, 3)
+    lo = _c(lo, np.float32)
+    hi = _c(hi, np.float32)
+    m = pos.shape[0]
+    feat = np.empty((m, MLP_IN), np.float64)
+    _load().oracle_mlp_encode(m, _p(pos), _p(dirs), _p(lo), _p(hi), _p(feat))
+    return feat
+
+
+def mlp_forward(params, feat):
+    params = _c(params, np.float32)
+    feat = _c(feat, np.float64)
+    m = feat.shape[0]
+    p = np.empty(m)
+    z = np.empty(m)
+    _load().oracle_mlp_forward(_p(params), m, _p(feat), _p(p), _p(z))
+    return p, z
+
+
+def mlp_loss_grad(params, feat, y):
+    params = _c(params, np.float32)
+    feat = _c(feat, np.float64)
+    y = _c(y, np.float64)
+    g = np.empty(params.shape[0], np.float64)
+    loss = _load().oracle_mlp_loss_grad(_p(params), feat.shape[0], _p(feat), _p(y), _p(g))
+    return float(loss), g
+
+
+def adam_step(w, g, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """In-place FP64 Adam step on numpy arrays w, m, v."""
+    g = _c(g, np.float64)
+    _load().oracle_adam_step(w.size, _p(w), _p(g), _p(m), _p(v), t, lr, b1, b2, eps)
