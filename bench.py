@@ -1,0 +1,343 @@
+#!/usr/bin/env python
+"""Benchmark: per-Gaussian visibility precompute on one GB300.
+
+A step is one whole precompute of the visibility table: LBVH build over the
+Gaussians plus the trace of every ray cast from every Gaussian along each of
+K Fibonacci directions (Sec. 4.1-4.2), inputs already resident in HBM.
+Default workload: the 2M-Gaussian object-scale scene (flattened Gaussians on
+2 spheres, a torus, a box and a ground plane; opacity Beta(5,1)) x 128
+directions = 256M rays per step.
+
+Printed (rank 0, one JSON line): traced rays/s of the whole precompute, ms
+per precompute, the roofline of the trace kernel (algorithmic bytes of node
+boxes and Gaussians fetched per ray over the measured HBM peak), the
+end-to-end rate through the C ABI from pinned host buffers, the FP64 oracle's
+rate on the host cores (a bounded sample), and SM clocks sampled during the
+timed region.
+
+`--impl reference` times the FP64 brute-force oracle (the reference for this
+method) on the host cores on bounded samples of the same workload.
+With `--gpus N` (torchrun) every rank runs an independent replica: the
+precompute has no exchange step, so there is no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (generator, n, seed, K)
+    "object_2m_k128": ("object", 2_000_000, 2, 128),
+    "object_300k_k128": ("object", 300_000, 2, 128),
+    "uniform_4k_k32": ("uniform", 4096, 1, 32),
+}
+METRIC = "traced rays/s & ms per 2M-Gaussian visibility precompute; surrogate speedup at MAE"
+TRACE_SOURCES = ["paper_2311_16043_gb300/csrc/rt_trace.cu", "paper_2311_16043_gb300/csrc/rt_trace_core.cuh"]
+BUILD_KERNELS_PER_STEP = 18  # bounds, morton, 4 x (hist, scan, scatter), perm, prep, karras, refit
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="object_2m_k128")
+    ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 per-ray, 2 packet")
+    ap.add_argument("--order-block", type=int, default=0)
+    ap.add_argument("--cpu-rays", type=int, default=2048, help="oracle sample for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def make_scene(name):
+    import scenes
+    gen, n, seed, K = WORKLOADS[name]
+    sc = scenes.object_scene(n, seed) if gen == "object" else scenes.uniform_scene(n, seed)
+    return sc, scenes.fibonacci_sphere(K)
+
+
+def workload_config(name, extra=None):
+    gen, n, seed, K = WORKLOADS[name]
+    cfg = {"workload": name, "gaussians": n, "directions": K, "rays_per_step": n * K,
+           "scene": "object-scale: 2 spheres, torus, box, ground plane" if gen == "object"
+           else "uniform cube", "seed": seed,
+           "step": "LBVH build + trace of every (Gaussian, direction) ray",
+           "l2": "inputs+outputs > L2 (T table %.0f MB) and a 512 MB L2 flush between steps" % (n * K * 4 / 1e6)}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def oracle_rate(sc, dirs, m, seed=99):
+    """Rays/s of the FP64 brute-force oracle on a seeded sample of m rays."""
+    import oracle
+    import scenes
+    oracle.build()
+    n, K = sc["mean"].shape[0], dirs.shape[0]
+    ids = scenes.sample_ray_ids(n * K, m, seed)
+    o, d, s = oracle.dir_rays(sc["mean"], dirs, ids)
+    t0 = time.perf_counter()
+    oracle.trace(sc, o, d, s)
+    dt = time.perf_counter() - t0
+    return m / dt, dt
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def trace_traffic():
+    """DRAM bytes per launch of the trace kernel from the committed ncu summary,
+    if it was taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "trace_dram.txt")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for line in open(path):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    h = hashlib.sha256()
+    for p in TRACE_SOURCES:
+        h.update(open(os.path.join(ROOT, p), "rb").read())
+    if kv.get("kernel_sha256") != h.hexdigest()[:16]:
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch_full_workload"])
+    except (KeyError, ValueError):
+        return None
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    sc, dirs = make_scene(args.workload)
+    n, K = sc["mean"].shape[0], dirs.shape[0]
+    m = max(32, min(args.cpu_rays, int(4e8 // max(n, 1))))  # ~4e8 ray-Gaussian tests per step
+    rates = []
+    for i in range(args.warmup + args.steps):
+        r, dt = oracle_rate(sc, dirs, m, seed=1000 + i)
+        if i >= args.warmup:
+            rates.append((r, dt))
+    value = statistics.mean(r for r, _ in rates)
+    ms = 1000.0 * n * K / value
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args.workload, {"parallelism": "host cores (OpenMP)"}),
+            "cpu_baseline": {"value": value, "unit": "rays/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{m} seeded rays per step of the {n * K} (brute force, every ray vs every Gaussian)"},
+            "e2e": {"value": value, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_2311_16043_gb300 import rt
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    rt.lib()
+    sc, dirs_np = make_scene(args.workload)
+    n, K = sc["mean"].shape[0], dirs_np.shape[0]
+    R = n * K
+    dev = torch.device("cuda", local)
+    d = {k: torch.from_numpy(v).to(dev) for k, v in sc.items()}
+    dirs = torch.from_numpy(dirs_np).to(dev)
+    T = torch.empty((n, K), dtype=torch.float32, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    prm = rt.params()
+    opts = rt.trace_opts(kernel=args.kernel, order_block=args.order_block)
+
+    def step(ev=None):
+        if ev:
+            ev[0].record()
+        bvh = rt.rt_build_bvh(d["mean"], d["scale"], d["quat"], d["opacity"], prm)
+        if ev:
+            ev[1].record()
+        rt.rt_trace_visibility_dirs(bvh, dirs, T, opts)
+        if ev:
+            ev[2].record()
+        bvh.destroy()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    # per-ray work of this trace, counted once (outside the timed region)
+    cnt = torch.zeros(4, dtype=torch.int64, device=dev)
+    bvh = rt.rt_build_bvh(d["mean"], d["scale"], d["quat"], d["opacity"], prm)
+    rt.rt_trace_visibility_dirs(bvh, dirs, T, rt.trace_opts(kernel=args.kernel, order_block=args.order_block,
+                                                              counters=cnt))
+    torch.cuda.synchronize()
+    bvh.destroy()
+    box_tests, gauss_tests, hits, rays_cnt = (int(x) for x in cnt.cpu())
+    assert rays_cnt == R, (rays_cnt, R)
+    alg_bytes = 28 * box_tests + 40 * gauss_tests + 16 * R
+
+    clocks = ClockSampler(local)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    barrier()
+    clocks.start()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        step(evs[i])
+    barrier()
+    clk = clocks.stop()
+    step_ms = [e[0].elapsed_time(e[2]) for e in evs]
+    build_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    trace_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    ms = statistics.mean(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * R / (ms / 1000.0)
+
+    # end to end through the C ABI from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        host = {k: torch.from_numpy(v).pin_memory() for k, v in sc.items()}
+        hdirs = torch.from_numpy(dirs_np).pin_memory()
+        hT = torch.empty((n, K), dtype=torch.float32).pin_memory()
+        h2d = sum(v.numel() * 4 for v in host.values()) + hdirs.numel() * 4
+        d2h = hT.numel() * 4
+        e_ms = []
+        for i in range(args.warmup + args.steps):
+            flush.fill_(float(i))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            dd = {k: v.to(dev, non_blocking=True) for k, v in host.items()}
+            ddirs = hdirs.to(dev, non_blocking=True)
+            bvh = rt.rt_build_bvh(dd["mean"], dd["scale"], dd["quat"], dd["opacity"], prm)
+            rt.rt_trace_visibility_dirs(bvh, ddirs, T, opts)
+            hT.copy_(T, non_blocking=True)
+            e1.record()
+            bvh.destroy()
+            torch.cuda.synchronize()
+            if i >= args.warmup:
+                e_ms.append(e0.elapsed_time(e1))
+        em = statistics.mean(e_ms)
+        if world > 1:
+            t = torch.tensor([em], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            em = float(t.item())
+        e2e = {"value": world * R / (em / 1000.0), "unit": "rays/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": em}
+
+    pk, pk_kind = peaks()
+    tr_ms = statistics.mean(trace_ms)
+    achieved = alg_bytes / (tr_ms / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "traffic": trace_traffic(),
+                "kernel": "k_trace (visibility trace)", "peak_kind": pk_kind,
+                "algorithmic_bytes_per_launch": alg_bytes,
+                "per_ray": {"box_tests": box_tests / R, "gaussian_tests": gauss_tests / R,
+                            "accepted_hits": hits / R},
+                "bytes_model": "28 B per child-box test + 40 B per Gaussian test + 16 B per ray"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        m = max(32, min(args.cpu_rays, int(4e9 // max(n, 1))))
+        rate, dt = oracle_rate(sc, dirs_np, m)
+        cpu = {"value": rate, "unit": "rays/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{m} seeded rays of the {R} (FP64 brute force, every ray vs all {n} Gaussians), {dt:.1f} s"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": workload_config(args.workload, {
+                    "parallelism": "replicas" if world > 1 else "single GPU",
+                    "build_ms": statistics.mean(build_ms), "trace_ms": tr_ms,
+                    "kernel": ["auto", "per-ray", "packet"][args.kernel]}),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": (BUILD_KERNELS_PER_STEP + 1) * args.steps,
+                "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

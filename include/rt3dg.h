@@ -1,0 +1,232 @@
+/*
+ * rt3dg.h -- C ABI of the GB300 (sm_103a) point-based Gaussian ray tracer.
+ *
+ * The library precomputes per-Gaussian visibility: for rays cast from each 3D
+ * Gaussian in a set of directions it returns the transmittance
+ * T = prod_j (1 - alpha_j) over the Gaussians the ray passes (Sec. 4.1-4.2 of
+ * "Relightable 3D Gaussians", arXiv 2311.16043).  Gaussians are given as mean,
+ * scale, rotation quaternion and opacity (Sec. 3.1); rays as origin and
+ * direction (Eq. 13); visibility is returned per ray.
+ *
+ * Conventions for every entry point
+ *   - Array arguments are DEVICE pointers owned by the caller unless a comment
+ *     says "host".  float32 arrays are C-contiguous, row-major.
+ *   - Gaussians: mean[n*3], scale[n*3] (linear standard deviations along the
+ *     local axes), quat[n*4] as (w, x, y, z) (normalised internally; must be
+ *     non-zero), opacity[n] in [0, 1).  Sigma = R(q) diag(s)^2 R(q)^T.
+ *   - All work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream) and is asynchronous; calls do not synchronise the host unless a
+ *     comment says so.
+ *   - Calls return rt_status.  Argument errors are detected on the host and
+ *     returned before anything is enqueued.  Errors found by kernels
+ *     (RT_ERR_STACK_OVERFLOW, RT_ERR_TIMEOUT) set a sticky device status word
+ *     read by rt_status_last() after the caller synchronises the stream.
+ *     No entry point aborts, asserts or traps.
+ *   - Handles (rt_bvh, rt_envmap, rt_surrogate, rt_batch) own their device
+ *     memory (stream-ordered cudaMallocAsync) and keep no pointer to caller
+ *     arrays after the call that created them returns.
+ */
+#ifndef RT3DG_H
+#define RT3DG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *rt_stream_t; /* identical to cudaStream_t */
+
+typedef enum {
+    RT_OK = 0,
+    RT_ERR_INVALID_ARG = 1,     /* bad pointer, size, or parameter         */
+    RT_ERR_OOM = 2,             /* device allocation failed                */
+    RT_ERR_CUDA = 3,            /* a CUDA runtime call failed              */
+    RT_ERR_STACK_OVERFLOW = 4,  /* traversal stack exceeded (never for trees built here) */
+    RT_ERR_HITLOG_OVERFLOW = 5, /* informational: some ray logged more hits than capacity */
+    RT_ERR_TIMEOUT = 6,         /* a bounded device wait gave up           */
+    RT_ERR_NOT_TRAINED = 7,     /* surrogate used before training          */
+    RT_ERR_UNSUPPORTED = 8      /* option combination not supported        */
+} rt_status;
+
+/* Tracing parameters.  Defaults (rt_params_default):
+ *   k_sigma = 3       support of a Gaussian: accepted only if the peak's
+ *                     Mahalanobis distance m satisfies m^2 <= k_sigma^2;
+ *   alpha_min = 1/255 accepted only if alpha = o * exp(-m^2/2) >= alpha_min;
+ *   t_min = 1e-4      early termination (Sec. 4.1): a ray whose running T
+ *                     drops below t_min stops and reports T = 0 (0 disables);
+ *   origin_eps = 1e-4 rays cast from a Gaussian start at
+ *                     fl(mu + fl(origin_eps * d)) and skip that Gaussian;
+ *   box_mode = 0      leaf boxes of radius k_sigma; 1 = opacity-aware radius
+ *                     min(k_sigma, sqrt(2 ln(o / alpha_min))), which gives the
+ *                     same accepted set with tighter boxes.                  */
+typedef struct {
+    float k_sigma;
+    float alpha_min;
+    float t_min;
+    float origin_eps;
+    int32_t box_mode;
+    int32_t reserved;
+} rt_params;
+
+void rt_params_default(rt_params *p);
+const char *rt_status_string(rt_status s);
+/* Sticky device status word (RT_OK if no kernel reported an error).  Reads a
+ * device value synchronously: call after synchronising the work in question.
+ * rt_status_clear() resets it. */
+rt_status rt_status_last(void);
+rt_status rt_status_clear(void);
+
+/* ------------------------------------------------------------------------ */
+/* LBVH (Sec. 4.1: binary radix tree of Karras 2012 over the Gaussians)      */
+/* ------------------------------------------------------------------------ */
+
+typedef struct rt_bvh rt_bvh;
+
+/* Builds the tree: per-Gaussian whitening S^-1 R^T and leaf boxes, scene
+ * bounds of the means, 30-bit Morton codes, a device LSD radix sort of
+ * (code, index), Karras' split rule over keys code<<32 | index, and a
+ * bottom-up refit of the child boxes.  n = 0 and n = 1 are valid.
+ * Synchronises `stream` once (to read the scene bounds into the handle).
+ * Errors: RT_ERR_INVALID_ARG (n < 0, n >= 2^31, NULL arrays with n > 0,
+ * k_sigma <= 0, alpha_min outside (0,1), t_min outside [0,1)), RT_ERR_OOM. */
+rt_status rt_build_bvh(const float *mean, const float *scale, const float *quat,
+                       const float *opacity, int64_t n, const rt_params *params,
+                       rt_stream_t stream, rt_bvh **out);
+rt_status rt_bvh_destroy(rt_bvh *bvh, rt_stream_t stream);
+/* Host outputs (any may be NULL): Gaussian count, scene bounds of the means
+ * (float[3] each), device bytes held by the handle. */
+rt_status rt_bvh_info(const rt_bvh *bvh, int64_t *n, float *lo, float *hi, int64_t *device_bytes);
+/* Copies the tree out (device pointers, any may be NULL):
+ *   keys[n]            sorted keys code<<32 | original index;
+ *   left[n-1], right[n-1]  child refs of internal node i; bit 31 set = leaf
+ *                      (sorted position in the low bits);
+ *   parent[2n-1]       parents of internal nodes 0..n-2 then of leaves;
+ *   boxes[(n-1)*12]    per internal node: left child box (lo xyz, hi xyz),
+ *                      then right child box (lo xyz, hi xyz).              */
+rt_status rt_bvh_export(const rt_bvh *bvh, uint64_t *keys, int32_t *left, int32_t *right,
+                        int32_t *parent, float *boxes, rt_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Ray sets                                                                   */
+/* ------------------------------------------------------------------------ */
+
+typedef struct rt_envmap rt_envmap;
+
+/* Environment map for importance-sampled shadow rays (the direct light of
+ * Eq. 8).  Host inputs: radiance[h*w] and solid_angle[h*w] (float64,
+ * row-major, row 0 = polar angle 0) and corners[(h+1)*(w+1)*3] (float32 unit
+ * directions of the pixel corners).  Pixel (i,j) is drawn with probability
+ * radiance*solid_angle / total (cumulative sums in float64, index order);
+ * inside it the direction is the normalised bilinear blend of its corners. */
+rt_status rt_envmap_create(const double *radiance, const double *solid_angle,
+                           const float *corners, int32_t h, int32_t w, rt_stream_t stream,
+                           rt_envmap **out);
+rt_status rt_envmap_destroy(rt_envmap *env, rt_stream_t stream);
+
+typedef enum {
+    RT_RAYS_EXPLICIT = 0, /* ray_o[R*3], ray_d[R*3], ray_src[R] (or NULL)       */
+    RT_RAYS_DIRS = 1,     /* from every Gaussian g along dirs[k]: id g*K + k     */
+    RT_RAYS_ENV = 2       /* from every Gaussian g, S env samples: id g*S + s    */
+} rt_ray_kind;
+
+/* A ray set.  EXPLICIT: n_rays rays, ray_src[r] = original index of a
+ * Gaussian the ray skips (or -1; NULL = none).  DIRS: K = n_dirs directions
+ * dirs[K*3] (device, unit length); the ray id r = g*K + k starts at
+ * fl(mu_g + fl(origin_eps * d_k)) and skips g.  ENV: S = n_dirs samples per
+ * Gaussian; sample s of Gaussian g (ray id r = g*S + s) draws Philox4x64-10
+ * with counter (r,0,0,0) and key (seed,0): u0 = (x0>>11) 2^-53 picks the
+ * pixel, a = (x1>>40) 2^-24 and b = (x2>>40) 2^-24 blend its corners.
+ * If ray_ids (device int64[n_ids]) is set for DIRS/ENV, only those ray ids
+ * are traced and outputs are indexed by position in ray_ids. */
+typedef struct {
+    int32_t kind;
+    int32_t n_dirs;
+    int64_t n_rays;
+    const float *ray_o;
+    const float *ray_d;
+    const int32_t *ray_src;
+    const float *dirs;
+    const rt_envmap *env;
+    uint64_t seed;
+    const int64_t *ray_ids;
+    int64_t n_ids;
+} rt_rayspec;
+
+/* Number of rays of a ray set over `bvh` (n*K for DIRS, n*S for ENV, n_ids if
+ * ray_ids is set, n_rays for EXPLICIT); -1 if the set is invalid. */
+int64_t rt_rayspec_count(const rt_bvh *bvh, const rt_rayspec *rays);
+
+/* Materialises rays of an implicit set (device outputs o[m*3], d[m*3],
+ * src[m], original index of the source Gaussian) for the listed ray ids. */
+rt_status rt_materialize_rays(const rt_bvh *bvh, const rt_rayspec *rays, const int64_t *ray_ids,
+                              int64_t m, float *ray_o, float *ray_d, int32_t *ray_src,
+                              rt_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Visibility (Eq. 13-15)                                                    */
+/* ------------------------------------------------------------------------ */
+
+typedef enum {
+    RT_KERNEL_AUTO = 0,
+    RT_KERNEL_RAY = 1,    /* one thread per ray, private traversal stack      */
+    RT_KERNEL_PACKET = 2  /* one warp per 32 rays of neighbouring Gaussians in
+                             one direction, shared stack (DIRS/ENV only)     */
+} rt_kernel;
+
+typedef struct {
+    int32_t kernel;      /* rt_kernel                                          */
+    int32_t order_block; /* PACKET: tiles of 32 Gaussians per direction sweep
+                            (0 = default)                                      */
+    int32_t block_threads; /* threads per block (0 = default)                  */
+    int32_t hit_cap;     /* capacity per ray of hit_ids                        */
+    int64_t *counters;   /* device int64[4] accumulated (not reset): box tests,
+                            Gaussian tests, accepted hits, rays (NULL = off)   */
+    int32_t *hit_ids;    /* device [R*hit_cap]: original indices of accepted
+                            Gaussians per ray, in traversal order (NULL = off) */
+    int32_t *hit_count;  /* device [R]: accepted hits per ray (may exceed
+                            hit_cap: the log of that ray is then incomplete)   */
+} rt_trace_opts;
+
+/* T_out[R] (device float32): visibility of every ray of the set, in ray-id
+ * order (DIRS: an [n, K] row-major table in the caller's Gaussian order).
+ * Accept rule per Gaussian j != source: t* > 0, m^2 <= k_sigma^2,
+ * alpha >= alpha_min, where t* minimises the Mahalanobis distance along the
+ * ray (Eq. 14 with Sigma^-1) and m^2 is its value; T is snapped to 0 below
+ * t_min.  opts may be NULL.  Errors: RT_ERR_INVALID_ARG. */
+rt_status rt_trace_visibility(const rt_bvh *bvh, const rt_rayspec *rays, float *T_out,
+                              const rt_trace_opts *opts, rt_stream_t stream);
+
+/* Convenience form of rt_trace_visibility for RT_RAYS_DIRS over all
+ * Gaussians: T_out[n*k]. */
+rt_status rt_trace_visibility_dirs(const rt_bvh *bvh, const float *dirs, int32_t k, float *T_out,
+                                   const rt_trace_opts *opts, rt_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Adjoint                                                                    */
+/* ------------------------------------------------------------------------ */
+
+/* Gradient of L = sum_r dL_dT[r] * T[r] for the ray set (T as traced with the
+ * same params; rays snapped to 0 contribute nothing).  Accumulates (+=) into
+ * d_mean[n*3], d_scale[n*3], d_quat[n*4] (with respect to the un-normalised
+ * quaternion), d_opacity[n] (caller-zeroed, original Gaussian order) and, if
+ * not NULL, writes d_ray_o[R*3].  T[R] are the traced values.  With
+ * hit_ids/hit_count from the forward (capacity hit_cap) the accepted hits are
+ * replayed; rays whose count exceeds hit_cap, or all rays if hit_ids is NULL,
+ * are re-traversed.  The mean, scale, quat, opacity arrays must be the ones
+ * the BVH was built from.  Accumulation uses float32 atomics (summation order
+ * is not deterministic). */
+rt_status rt_trace_visibility_backward(const rt_bvh *bvh, const rt_rayspec *rays,
+                                       const float *mean, const float *scale, const float *quat,
+                                       const float *opacity, const float *T, const float *dL_dT,
+                                       const int32_t *hit_ids, const int32_t *hit_count,
+                                       int32_t hit_cap, float *d_mean, float *d_scale,
+                                       float *d_quat, float *d_opacity, float *d_ray_o,
+                                       rt_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RT3DG_H */

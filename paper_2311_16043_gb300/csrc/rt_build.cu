@@ -1,0 +1,535 @@
+// rt_build.cu -- LBVH construction on the device (Sec. 4.1: a binary radix
+// tree over the Gaussians in the manner of Karras 2012, leaves = tight boxes
+// of single Gaussians, internal nodes = union of their children).
+//
+// Steps (all kernels below, one stream):
+//   k_bounds       per-axis min/max of the means (order-preserving uint atomics)
+//   k_morton       30-bit Morton codes, float32 IEEE quantisation (no FMA)
+//   k_radix_*      stable LSD radix sort of (code, index), 8-bit digits, 4 passes
+//   k_perm         permutation, inverse permutation, 64-bit keys code<<32|index
+//   k_prep         per-Gaussian record (mean, opacity, whitening W = S^-1 R^T)
+//                  and its leaf box, written in sorted order
+//   k_karras       internal-node children by the longest-common-prefix split
+//   k_refit        bottom-up child boxes; the second thread to reach a node
+//                  (atomic arrival count) forms its box and climbs on
+#include <math.h>
+#include <stdio.h>
+
+#include "rt_internal.cuh"
+
+namespace {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 keys per block
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+
+__device__ __forceinline__ uint32_t f2ord(float f) {
+    uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ord2f(uint32_t u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+// bounds_u[0..2] = ordered min, [3..5] = ordered max (pre-set to 0xff.. / 0)
+__global__ void k_bounds(const float *__restrict__ mean, int64_t n, uint32_t *bounds_u) {
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float v = mean[3 * i + c];
+            lo[c] = fminf(lo[c], v);
+            hi[c] = fmaxf(hi[c], v);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        for (int off = 16; off > 0; off >>= 1) {
+            lo[c] = fminf(lo[c], __shfl_xor_sync(0xffffffffu, lo[c], off));
+            hi[c] = fmaxf(hi[c], __shfl_xor_sync(0xffffffffu, hi[c], off));
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            atomicMin(&bounds_u[c], f2ord(lo[c]));
+            atomicMax(&bounds_u[3 + c], f2ord(hi[c]));
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t spread10(uint32_t v) {
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000FFu;
+    v = (v | (v << 8)) & 0x0300F00Fu;
+    v = (v | (v << 4)) & 0x030C30C3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+// Quantisation with separately rounded float32 operations:
+// u = (mu - lo) / (hi - lo), q = clamp(floor(u * 1024), 0, 1023); 0 if hi == lo.
+__global__ void k_morton(const float *__restrict__ mean, int64_t n, const uint32_t *bounds_u,
+                         float *bounds_out, uint32_t *codes, int32_t *vals) {
+    float lo[3], ext[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        lo[c] = ord2f(bounds_u[c]);
+        float hi = ord2f(bounds_u[3 + c]);
+        ext[c] = __fsub_rn(hi, lo[c]);
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            bounds_out[c] = lo[c];
+            bounds_out[3 + c] = hi;
+        }
+    }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t q[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            if (ext[c] == 0.0f) {
+                q[c] = 0;
+                continue;
+            }
+            float u = __fdiv_rn(__fsub_rn(mean[3 * i + c], lo[c]), ext[c]);
+            float v = __fmul_rn(u, 1024.0f);
+            int qi = (int)floorf(v);
+            qi = qi < 0 ? 0 : (qi > 1023 ? 1023 : qi);
+            q[c] = (uint32_t)qi;
+        }
+        codes[i] = (spread10(q[0]) << 2) | (spread10(q[1]) << 1) | spread10(q[2]);
+        vals[i] = (int32_t)i;
+    }
+}
+
+// counts[d * nblk + b] = number of keys of tile b with digit d
+__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t *__restrict__ keys,
+                                                             int64_t n, int shift, int nblk,
+                                                             uint32_t *counts) {
+    __shared__ uint32_t hist[kRadix];
+    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) hist[d] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * kSortTile;
+#pragma unroll 4
+    for (int it = 0; it < kSortItems; ++it) {
+        int64_t i = base + it * kSortThreads + threadIdx.x;
+        if (i < n) atomicAdd(&hist[(keys[i] >> shift) & (kRadix - 1)], 1u);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) counts[(int64_t)d * nblk + blockIdx.x] = hist[d];
+}
+
+// In-place exclusive scan of m counts, one block of 1024 threads.
+__global__ void __launch_bounds__(1024) k_radix_scan(uint32_t *counts, int64_t m) {
+    __shared__ uint32_t part[1024];
+    int t = threadIdx.x;
+    int64_t chunk = (m + 1023) / 1024;
+    int64_t b = t * chunk, e = b + chunk < m ? b + chunk : m;
+    uint32_t s = 0;
+    for (int64_t i = b; i < e; ++i) s += counts[i];
+    part[t] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {  // Hillis-Steele inclusive
+        uint32_t v = t >= off ? part[t - off] : 0u;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    uint32_t run = part[t] - s;  // exclusive prefix of this chunk
+    for (int64_t i = b; i < e; ++i) {
+        uint32_t c = counts[i];
+        counts[i] = run;
+        run += c;
+    }
+}
+
+// Stable scatter: within a tile, keys are ranked in index order (round,
+// warp, lane), so equal digits keep their relative order.
+__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
+    const uint32_t *__restrict__ keys_in, const int32_t *__restrict__ vals_in, int64_t n, int shift,
+    int nblk, const uint32_t *__restrict__ offsets, uint32_t *keys_out, int32_t *vals_out) {
+    constexpr int kWarps = kSortThreads / 32;
+    __shared__ uint32_t goff[kRadix];
+    __shared__ uint32_t wcnt[kWarps][kRadix];
+    const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+    for (int d = t; d < kRadix; d += kSortThreads) goff[d] = offsets[(int64_t)d * nblk + blockIdx.x];
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    int64_t base = (int64_t)blockIdx.x * kSortTile;
+    for (int it = 0; it < kSortItems; ++it) {
+        for (int j = t; j < kWarps * kRadix; j += kSortThreads) (&wcnt[0][0])[j] = 0;
+        __syncthreads();
+        int64_t i = base + it * kSortThreads + t;
+        bool valid = i < n;
+        uint32_t key = valid ? keys_in[i] : 0u;
+        int32_t val = valid ? vals_in[i] : 0;
+        uint32_t d = valid ? ((key >> shift) & (kRadix - 1)) : 0xffffffffu;
+        uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t rank = __popc(peers & lt_mask);
+        if (valid && rank == 0) wcnt[w][d] = __popc(peers);
+        __syncthreads();
+        for (int dd = t; dd < kRadix; dd += kSortThreads) {  // prefix over warps, per digit
+            uint32_t run = goff[dd];
+            for (int ww = 0; ww < kWarps; ++ww) {
+                uint32_t c = wcnt[ww][dd];
+                wcnt[ww][dd] = run;
+                run += c;
+            }
+            goff[dd] = run;
+        }
+        __syncthreads();
+        if (valid) {
+            uint32_t pos = wcnt[w][d] + rank;
+            keys_out[pos] = key;
+            vals_out[pos] = val;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_perm(const uint32_t *__restrict__ codes, const int32_t *__restrict__ vals,
+                       int64_t n, int32_t *perm, int32_t *rank, uint64_t *keys) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        int32_t i = vals[p];
+        perm[p] = i;
+        rank[i] = (int32_t)p;
+        keys[p] = ((uint64_t)codes[p] << 32) | (uint32_t)i;
+    }
+}
+
+// Per-Gaussian record and leaf box in sorted order.
+__global__ void k_prep(const float *__restrict__ mean, const float *__restrict__ scale,
+                       const float *__restrict__ quat, const float *__restrict__ opacity,
+                       const int32_t *__restrict__ perm, int64_t n, rt_params prm,
+                       float4 *gauss, float *leafbox) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        int32_t i = perm[p];
+        float qw = quat[4 * i], qx = quat[4 * i + 1], qy = quat[4 * i + 2], qz = quat[4 * i + 3];
+        float qn = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+        qw /= qn; qx /= qn; qy /= qn; qz /= qn;
+        float R[3][3];
+        R[0][0] = 1.f - 2.f * (qy * qy + qz * qz); R[0][1] = 2.f * (qx * qy - qw * qz); R[0][2] = 2.f * (qx * qz + qw * qy);
+        R[1][0] = 2.f * (qx * qy + qw * qz); R[1][1] = 1.f - 2.f * (qx * qx + qz * qz); R[1][2] = 2.f * (qy * qz - qw * qx);
+        R[2][0] = 2.f * (qx * qz - qw * qy); R[2][1] = 2.f * (qy * qz + qw * qx); R[2][2] = 1.f - 2.f * (qx * qx + qy * qy);
+        float s[3] = {scale[3 * i], scale[3 * i + 1], scale[3 * i + 2]};
+        float mu[3] = {mean[3 * i], mean[3 * i + 1], mean[3 * i + 2]};
+        float o = opacity[i];
+        float W[3][3];  // row k = column k of R divided by s_k
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) W[k][c] = __fdiv_rn(R[c][k], s[k]);
+        gauss[4 * p + 0] = make_float4(mu[0], mu[1], mu[2], o);
+        gauss[4 * p + 1] = make_float4(W[0][0], W[0][1], W[0][2], __int_as_float(i));
+        gauss[4 * p + 2] = make_float4(W[1][0], W[1][1], W[1][2], 0.f);
+        gauss[4 * p + 3] = make_float4(W[2][0], W[2][1], W[2][2], 0.f);
+        // support radius: k_sigma, or the opacity-aware radius (same accepted set)
+        float K = prm.k_sigma;
+        bool empty = false;
+        if (prm.box_mode == 1) {
+            if (o < prm.alpha_min) empty = true;
+            else {
+                float kk = 2.0f * logf(o / prm.alpha_min);
+                kk = kk * (1.0f + 1e-4f) + 1e-6f;  // outward margin for logf rounding
+                if (kk < K * K) K = sqrtf(kk);
+            }
+        }
+        float *bx = leafbox + 6 * p;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            // half-extent along world axis c: K sqrt(sum_k (R_ck s_k)^2), widened by
+            // 1e-4 relative plus a few ulps of |mu| so the float box contains the
+            // exact support and the slab test never misses an accepted peak
+            float a0 = R[c][0] * s[0], a1 = R[c][1] * s[1], a2 = R[c][2] * s[2];
+            float h = K * sqrtf(a0 * a0 + a1 * a1 + a2 * a2);
+            h = h * (1.0f + 1e-4f) + 4.0f * 1.1920929e-7f * fabsf(mu[c]) + 1e-30f;
+            bx[c] = empty ? INFINITY : __fsub_rd(mu[c], h);
+            bx[3 + c] = empty ? -INFINITY : __fadd_ru(mu[c], h);
+        }
+    }
+}
+
+__device__ __forceinline__ int lcp(const uint64_t *keys, int64_t n, int64_t i, int64_t j) {
+    if (j < 0 || j >= n) return -1;
+    return __clzll(keys[i] ^ keys[j]);
+}
+
+// Internal node i: direction d toward the longer common prefix, range end j
+// by exponential + binary search, split gamma by binary search; children
+// gamma and gamma+1 are leaves when they are the range's ends.
+__global__ void k_karras(const uint64_t *__restrict__ keys, int64_t n, float4 *nodes, int32_t *parent) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n - 1;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int d = (lcp(keys, n, i, i + 1) - lcp(keys, n, i, i - 1)) >= 0 ? 1 : -1;
+        int dmin = lcp(keys, n, i, i - d);
+        int64_t lmax = 2;
+        while (lcp(keys, n, i, i + lmax * d) > dmin) lmax <<= 1;
+        int64_t l = 0;
+        for (int64_t t = lmax >> 1; t >= 1; t >>= 1)
+            if (lcp(keys, n, i, i + (l + t) * d) > dmin) l += t;
+        int64_t j = i + l * d;
+        int dnode = lcp(keys, n, i, j);
+        int64_t s = 0, t = l;
+        for (;;) {
+            t = (t + 1) >> 1;
+            if (lcp(keys, n, i, i + (s + t) * d) > dnode) s += t;
+            if (t == 1) break;
+        }
+        int64_t gamma = i + s * d + (d < 0 ? -1 : 0);
+        int64_t first = i < j ? i : j, last = i < j ? j : i;
+        uint32_t lref, rref;
+        if (first == gamma) {
+            lref = RT_LEAF_BIT | (uint32_t)gamma;
+            parent[(n - 1) + gamma] = (int32_t)i;
+        } else {
+            lref = (uint32_t)gamma;
+            parent[gamma] = (int32_t)i;
+        }
+        if (last == gamma + 1) {
+            rref = RT_LEAF_BIT | (uint32_t)(gamma + 1);
+            parent[(n - 1) + gamma + 1] = (int32_t)i;
+        } else {
+            rref = (uint32_t)(gamma + 1);
+            parent[gamma + 1] = (int32_t)i;
+        }
+        nodes[4 * i + 3] = make_float4(__uint_as_float(lref), __uint_as_float(rref), 0.f, 0.f);
+        if (i == 0) parent[0] = -1;
+    }
+}
+
+__device__ __forceinline__ void store_child_box(float4 *nodes, int32_t node, bool right, const float b[6]) {
+    float *nd = reinterpret_cast<float *>(nodes + 4 * (int64_t)node);
+    if (!right) {
+        __stcg(nd + 0, b[0]); __stcg(nd + 1, b[3]); __stcg(nd + 2, b[1]);
+        __stcg(nd + 3, b[4]); __stcg(nd + 4, b[2]); __stcg(nd + 5, b[5]);
+    } else {
+        __stcg(nd + 6, b[0]); __stcg(nd + 7, b[3]); __stcg(nd + 8, b[1]);
+        __stcg(nd + 9, b[4]); __stcg(nd + 10, b[2]); __stcg(nd + 11, b[5]);
+    }
+}
+
+// One thread per leaf climbs toward the root.  At each internal node it
+// stores its subtree's box into the node's child slot, fences, and bumps the
+// node's arrival count: the first arrival stops, the second (which then sees
+// both slots) forms the union and continues.  No thread ever waits.
+__global__ void k_refit(const float *__restrict__ leafbox, const int32_t *__restrict__ parent,
+                        int64_t n, float4 *nodes, uint32_t *arrivals) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        float b[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) b[c] = leafbox[6 * p + c];
+        uint32_t child = RT_LEAF_BIT | (uint32_t)p;
+        int32_t node = parent[(n - 1) + p];
+        while (node >= 0) {
+            float4 refs = __ldcg(nodes + 4 * (int64_t)node + 3);
+            bool right = __float_as_uint(refs.x) != child;
+            store_child_box(nodes, node, right, b);
+            __threadfence();
+            if (atomicAdd(&arrivals[node], 1u) == 0) break;
+            __threadfence();
+            const float *nd = reinterpret_cast<const float *>(nodes + 4 * (int64_t)node);
+            float l[12];
+#pragma unroll
+            for (int c = 0; c < 12; ++c) l[c] = __ldcg(nd + c);
+            // slots: (L.lo.x, L.hi.x, L.lo.y, L.hi.y, L.lo.z, L.hi.z, R.lo.x, ...)
+            b[0] = fminf(l[0], l[6]);  b[3] = fmaxf(l[1], l[7]);
+            b[1] = fminf(l[2], l[8]);  b[4] = fmaxf(l[3], l[9]);
+            b[2] = fminf(l[4], l[10]); b[5] = fmaxf(l[5], l[11]);
+            child = (uint32_t)node;
+            node = parent[node];
+        }
+    }
+}
+
+__global__ void k_export_boxes(const float4 *__restrict__ nodes, int64_t m, float *boxes,
+                               int32_t *left, int32_t *right) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float4 a = nodes[4 * i], b = nodes[4 * i + 1], c = nodes[4 * i + 2], r = nodes[4 * i + 3];
+        if (boxes) {
+            float *o = boxes + 12 * i;
+            o[0] = a.x; o[1] = a.z; o[2] = b.x; o[3] = a.y; o[4] = a.w; o[5] = b.y;
+            o[6] = b.z; o[7] = c.x; o[8] = c.z; o[9] = b.w; o[10] = c.y; o[11] = c.w;
+        }
+        if (left) left[i] = (int32_t)__float_as_uint(r.x);
+        if (right) right[i] = (int32_t)__float_as_uint(r.y);
+    }
+}
+
+int grid_for(int64_t n, int threads) {
+    int64_t g = (n + threads - 1) / threads;
+    int64_t cap = (int64_t)rt_num_sms() * 16;
+    if (g > cap) g = cap;
+    return g < 1 ? 1 : (int)g;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" rt_status rt_build_bvh(const float *mean, const float *scale, const float *quat,
+                                  const float *opacity, int64_t n, const rt_params *params,
+                                  rt_stream_t stream, rt_bvh **out) {
+    if (!out) return RT_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n < 0 || n >= (int64_t)0x7fffffff) return RT_ERR_INVALID_ARG;
+    if (n > 0 && (!mean || !scale || !quat || !opacity)) return RT_ERR_INVALID_ARG;
+    rt_params prm;
+    rt_params_default(&prm);
+    if (params) prm = *params;
+    if (!(prm.k_sigma > 0.f) || !(prm.alpha_min > 0.f && prm.alpha_min < 1.f) ||
+        !(prm.t_min >= 0.f && prm.t_min < 1.f) || !(prm.origin_eps >= 0.f) ||
+        (prm.box_mode != 0 && prm.box_mode != 1))
+        return RT_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+
+    rt_bvh *b = new rt_bvh();
+    b->n = n;
+    b->params = prm;
+    const int64_t ni = n > 1 ? n - 1 : 0;
+    size_t off_g = 0;
+    size_t off_nd = off_g + align256(sizeof(float4) * 4 * (size_t)n);
+    size_t off_perm = off_nd + align256(sizeof(float4) * 4 * (size_t)ni);
+    size_t off_rank = off_perm + align256(sizeof(int32_t) * (size_t)n);
+    size_t off_keys = off_rank + align256(sizeof(int32_t) * (size_t)n);
+    size_t off_par = off_keys + align256(sizeof(uint64_t) * (size_t)n);
+    size_t off_bnd = off_par + align256(sizeof(int32_t) * (size_t)(n > 0 ? 2 * n - 1 : 0));
+    size_t total = off_bnd + 256;
+    rt_status s = rt_alloc(&b->block, total, stream);
+    if (s != RT_OK) {
+        delete b;
+        return s;
+    }
+    char *base = (char *)b->block;
+    b->bytes = (int64_t)total;
+    b->gauss = (float4 *)(base + off_g);
+    b->nodes = (float4 *)(base + off_nd);
+    b->perm = (int32_t *)(base + off_perm);
+    b->rank = (int32_t *)(base + off_rank);
+    b->keys = (uint64_t *)(base + off_keys);
+    b->parent = (int32_t *)(base + off_par);
+    b->bounds = (float *)(base + off_bnd);
+    for (int c = 0; c < 3; ++c) b->lo[c] = b->hi[c] = 0.f;
+    if (n == 0) {
+        *out = b;
+        return RT_OK;
+    }
+
+    // scratch: bounds(6 u32) | codes, vals x2 | counts | leafbox | arrivals
+    const int nblk = (int)((n + kSortTile - 1) / kSortTile);
+    size_t s_bu = 0;
+    size_t s_k0 = s_bu + 256;
+    size_t s_v0 = s_k0 + align256(4 * (size_t)n);
+    size_t s_k1 = s_v0 + align256(4 * (size_t)n);
+    size_t s_v1 = s_k1 + align256(4 * (size_t)n);
+    size_t s_cnt = s_v1 + align256(4 * (size_t)n);
+    size_t s_leaf = s_cnt + align256(4 * (size_t)kRadix * nblk);
+    size_t s_arr = s_leaf + align256(24 * (size_t)n);
+    size_t s_total = s_arr + align256(4 * (size_t)ni);
+    void *scratch = nullptr;
+    s = rt_alloc(&scratch, s_total, stream);
+    if (s != RT_OK) {
+        rt_free(b->block, stream);
+        delete b;
+        return s;
+    }
+    char *sb = (char *)scratch;
+    uint32_t *bounds_u = (uint32_t *)(sb + s_bu);
+    uint32_t *k0 = (uint32_t *)(sb + s_k0), *k1 = (uint32_t *)(sb + s_k1);
+    int32_t *v0 = (int32_t *)(sb + s_v0), *v1 = (int32_t *)(sb + s_v1);
+    uint32_t *counts = (uint32_t *)(sb + s_cnt);
+    float *leafbox = (float *)(sb + s_leaf);
+    uint32_t *arrivals = (uint32_t *)(sb + s_arr);
+
+    rt_status result = RT_OK;
+    do {
+        if (cudaMemsetAsync(bounds_u, 0xff, 12, st) != cudaSuccess ||
+            cudaMemsetAsync(bounds_u + 3, 0, 12, st) != cudaSuccess) {
+            result = RT_ERR_CUDA;
+            break;
+        }
+        k_bounds<<<grid_for(n, 256), 256, 0, st>>>(mean, n, bounds_u);
+        k_morton<<<grid_for(n, 256), 256, 0, st>>>(mean, n, bounds_u, b->bounds, k0, v0);
+        for (int pass = 0; pass < 4; ++pass) {
+            int shift = pass * kRadixBits;
+            k_radix_hist<<<nblk, kSortThreads, 0, st>>>(k0, n, shift, nblk, counts);
+            k_radix_scan<<<1, 1024, 0, st>>>(counts, (int64_t)kRadix * nblk);
+            k_radix_scatter<<<nblk, kSortThreads, 0, st>>>(k0, v0, n, shift, nblk, counts, k1, v1);
+            uint32_t *tk = k0; k0 = k1; k1 = tk;
+            int32_t *tv = v0; v0 = v1; v1 = tv;
+        }
+        k_perm<<<grid_for(n, 256), 256, 0, st>>>(k0, v0, n, b->perm, b->rank, b->keys);
+        k_prep<<<grid_for(n, 128), 128, 0, st>>>(mean, scale, quat, opacity, b->perm, n, prm,
+                                                 b->gauss, leafbox);
+        if (n == 1) {
+            int32_t m1 = -1;
+            if (cudaMemcpyAsync(b->parent, &m1, sizeof(int32_t), cudaMemcpyHostToDevice, st) != cudaSuccess)
+                result = RT_ERR_CUDA;
+        } else {
+            k_karras<<<grid_for(ni, 256), 256, 0, st>>>(b->keys, n, b->nodes, b->parent);
+            if (cudaMemsetAsync(arrivals, 0, 4 * (size_t)ni, st) != cudaSuccess) {
+                result = RT_ERR_CUDA;
+                break;
+            }
+            k_refit<<<grid_for(n, 256), 256, 0, st>>>(leafbox, b->parent, n, b->nodes, arrivals);
+        }
+        if (rt_check_launch() != RT_OK) {
+            result = RT_ERR_CUDA;
+            break;
+        }
+        if (cudaMemcpyAsync(b->lo, b->bounds, 3 * sizeof(float), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(b->hi, b->bounds + 3, 3 * sizeof(float), cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+            result = RT_ERR_CUDA;
+            break;
+        }
+    } while (0);
+    rt_free(scratch, stream);
+    if (result == RT_OK && cudaStreamSynchronize(st) != cudaSuccess) result = RT_ERR_CUDA;
+    if (result != RT_OK) {
+        rt_free(b->block, stream);
+        delete b;
+        return result;
+    }
+    *out = b;
+    return RT_OK;
+}
+
+extern "C" rt_status rt_bvh_destroy(rt_bvh *bvh, rt_stream_t stream) {
+    if (!bvh) return RT_ERR_INVALID_ARG;
+    rt_free(bvh->block, stream);
+    delete bvh;
+    return RT_OK;
+}
+
+extern "C" rt_status rt_bvh_info(const rt_bvh *bvh, int64_t *n, float *lo, float *hi, int64_t *bytes) {
+    if (!bvh) return RT_ERR_INVALID_ARG;
+    if (n) *n = bvh->n;
+    for (int c = 0; c < 3; ++c) {
+        if (lo) lo[c] = bvh->lo[c];
+        if (hi) hi[c] = bvh->hi[c];
+    }
+    if (bytes) *bytes = bvh->bytes;
+    return RT_OK;
+}
+
+extern "C" rt_status rt_bvh_export(const rt_bvh *bvh, uint64_t *keys, int32_t *left, int32_t *right,
+                                   int32_t *parent, float *boxes, rt_stream_t stream) {
+    if (!bvh) return RT_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int64_t n = bvh->n;
+    if (n == 0) return RT_OK;
+    if (keys && cudaMemcpyAsync(keys, bvh->keys, 8 * (size_t)n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return RT_ERR_CUDA;
+    if (parent && cudaMemcpyAsync(parent, bvh->parent, 4 * (size_t)(2 * n - 1), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return RT_ERR_CUDA;
+    if (n > 1 && (boxes || left || right)) {
+        k_export_boxes<<<grid_for(n - 1, 256), 256, 0, st>>>(bvh->nodes, n - 1, boxes, left, right);
+        return rt_check_launch();
+    }
+    return RT_OK;
+}

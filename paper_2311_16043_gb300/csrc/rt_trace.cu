@@ -1,0 +1,263 @@
+// rt_trace.cu -- visibility of a ray set (Eq. 13-15, Sec. 4.1-4.2).
+//
+// One persistent launch: each warp repeatedly takes a work item of 32 rays
+// from a device counter.  For a full implicit set (every Gaussian x K
+// directions) an item is 32 Gaussians adjacent in Morton order x one
+// direction, so the warp's rays are nearly parallel and start close together.
+// Items are ordered in sweeps: `order_block` tiles for direction 0, the same
+// tiles for direction 1, ... so that the rows T[g, 0..K) of a tile are written
+// within a short window (whole sectors merge in L2) while neighbouring warps
+// still trace parallel rays.  Explicit ray lists and id subsets are taken in
+// chunks of 32 in the given order.
+#include <string.h>
+
+#include "rt_trace_core.cuh"
+
+namespace {
+
+enum { MODE_EXPLICIT = 0, MODE_FULL = 1, MODE_IDS = 2 };
+
+struct TraceJob {
+    int mode;
+    int64_t n_items;
+    int64_t n_tiles;      // MODE_FULL
+    int32_t order_block;  // MODE_FULL: tiles per sweep
+    int64_t n_out;        // outputs (rays)
+};
+
+// Decode a MODE_FULL item into (tile, direction).
+__device__ __forceinline__ void full_item(const TraceJob &job, int32_t K, int64_t item, int64_t &tile,
+                                          int32_t &k) {
+    const int64_t B = job.order_block;
+    const int64_t grp = item / (B * K);
+    const int64_t rem = item - grp * B * K;
+    int64_t in_grp = job.n_tiles - grp * B;
+    if (in_grp > B) in_grp = B;
+    k = (int32_t)(rem / in_grp);
+    tile = grp * B + rem % in_grp;
+}
+
+template <bool PACKET>
+__global__ void __launch_bounds__(128) k_trace(BvhDev b, RaySetDev rs, TraceJob job, float *T_out,
+                                               TraceAux aux, unsigned long long *work) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    WorkCounts wc = {0, 0, 0};
+    unsigned long long rays_done = 0;
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(work, 1ull);
+        item = __shfl_sync(FULL, item, 0);
+        if ((int64_t)item >= job.n_items) break;
+
+        // ---- ray of this lane ----
+        bool valid = false;
+        float3 o = make_float3(0.f, 0.f, 0.f), d = make_float3(0.f, 0.f, 1.f);
+        int32_t src = -1;
+        int64_t out_idx = 0;
+        if (job.mode == MODE_FULL) {
+            int64_t tile;
+            int32_t k;
+            full_item(job, rs.K, (int64_t)item, tile, k);
+            const int64_t p = tile * 32 + lane;
+            if (p < b.n) {
+                valid = true;
+                const float4 mu = __ldg(b.gauss + 4 * p);
+                const int32_t g = __float_as_int(__ldg(b.gauss + 4 * p + 1).w);
+                out_idx = (int64_t)g * rs.K + k;
+                implicit_ray(rs, out_idx, k, mu, o, d);
+                src = (int32_t)p;
+            }
+        } else {
+            const int64_t r = (int64_t)item * 32 + lane;
+            if (r < job.n_out) {
+                valid = true;
+                out_idx = r;
+                if (job.mode == MODE_EXPLICIT) {
+                    o = make_float3(rs.ray_o[3 * r], rs.ray_o[3 * r + 1], rs.ray_o[3 * r + 2]);
+                    d = make_float3(rs.ray_d[3 * r], rs.ray_d[3 * r + 1], rs.ray_d[3 * r + 2]);
+                    if (rs.ray_src) {
+                        const int32_t s = rs.ray_src[r];
+                        src = (s >= 0 && s < b.n) ? b.rank[s] : -1;
+                    }
+                } else {
+                    const int64_t rid = rs.ray_ids[r];
+                    if (rid < 0 || rid >= rs.n_rays) {
+                        rt_set_error(aux.status, RT_ERR_INVALID_ARG);
+                        valid = false;
+                        T_out[r] = __int_as_float(0x7fc00000);
+                    } else {
+                        const int64_t g = rid / rs.K;
+                        const int32_t k = (int32_t)(rid - g * rs.K);
+                        const int32_t p = b.rank[g];
+                        const float4 mu = __ldg(b.gauss + 4 * (int64_t)p);
+                        implicit_ray(rs, rid, k, mu, o, d);
+                        src = p;
+                    }
+                }
+            }
+        }
+
+        LaneLog lg;
+        lg.ids = (aux.hit_ids && valid) ? aux.hit_ids + out_idx * aux.cap : nullptr;
+        lg.cap = aux.cap;
+        lg.count = 0;
+        float T;
+        if (PACKET) {
+            T = trace_packet(b, o, d, src, valid, lg, wc, aux.status);
+        } else {
+            T = valid ? trace_ray(b, o, d, src, lg, wc, aux.status) : 1.0f;
+        }
+        if (valid) {
+            T_out[out_idx] = T;
+            if (aux.hit_count) aux.hit_count[out_idx] = lg.count;
+            rays_done++;
+        }
+    }
+    if (aux.counters) {
+        unsigned long long v[4] = {wc.box, wc.gauss, wc.hits, rays_done};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            unsigned long long x = v[c];
+            for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(FULL, x, off);
+            if (lane == 0 && x) atomicAdd(aux.counters + c, x);
+        }
+    }
+}
+
+int persistent_blocks(const void *kernel, int threads) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    return per_sm * rt_num_sms();
+}
+
+}  // namespace
+
+// Shared by rt_trace_visibility and the batched launch.
+rt_status rt_trace_launch(const rt_bvh *bvh, const rt_rayspec *rays, float *T_out,
+                          const rt_trace_opts *opts, rt_stream_t stream, unsigned long long *work) {
+    RaySetDev rs;
+    int64_t count = 0;
+    RT_TRY(rt_rayset_dev(bvh, rays, &rs, &count));
+    if (count > 0 && !T_out) return RT_ERR_INVALID_ARG;
+    rt_trace_opts o;
+    memset(&o, 0, sizeof(o));
+    if (opts) o = *opts;
+    if (o.kernel < 0 || o.kernel > 2 || o.order_block < 0 || o.block_threads < 0) return RT_ERR_INVALID_ARG;
+    if ((o.hit_ids && (o.hit_cap <= 0 || !o.hit_count)) ) return RT_ERR_INVALID_ARG;
+    if (count == 0) return RT_OK;
+
+    TraceJob job;
+    job.n_out = count;
+    job.order_block = 1;
+    job.n_tiles = 0;
+    if (rays->kind == RT_RAYS_EXPLICIT) job.mode = MODE_EXPLICIT;
+    else if (rays->ray_ids) job.mode = MODE_IDS;
+    else job.mode = MODE_FULL;
+    if (job.mode == MODE_FULL) {
+        job.n_tiles = (bvh->n + 31) / 32;
+        int64_t B = o.order_block > 0 ? o.order_block : 64;
+        if (B > job.n_tiles) B = job.n_tiles;
+        job.order_block = (int32_t)B;
+        job.n_items = job.n_tiles * rs.K;
+    } else {
+        job.n_items = (count + 31) / 32;
+    }
+    bool packet = o.kernel == RT_KERNEL_PACKET || (o.kernel == RT_KERNEL_AUTO && job.mode == MODE_FULL && rays->kind == RT_RAYS_DIRS);
+
+    TraceAux aux;
+    aux.counters = (unsigned long long *)o.counters;
+    aux.hit_ids = o.hit_ids;
+    aux.hit_count = o.hit_count;
+    aux.cap = o.hit_cap;
+    aux.status = rt_status_ptr();
+    BvhDev b = bvh_dev(bvh);
+    cudaStream_t st = (cudaStream_t)stream;
+
+    bool own = false;
+    if (!work) {
+        RT_TRY(rt_alloc((void **)&work, sizeof(unsigned long long), stream));
+        own = true;
+    }
+    rt_status res = RT_OK;
+    if (cudaMemsetAsync(work, 0, sizeof(unsigned long long), st) != cudaSuccess) res = RT_ERR_CUDA;
+    if (res == RT_OK) {
+        const int threads = 128;
+        if (packet) {
+            int grid = persistent_blocks((const void *)k_trace<true>, threads);
+            k_trace<true><<<grid, threads, 0, st>>>(b, rs, job, T_out, aux, work);
+        } else {
+            int grid = persistent_blocks((const void *)k_trace<false>, threads);
+            k_trace<false><<<grid, threads, 0, st>>>(b, rs, job, T_out, aux, work);
+        }
+        res = rt_check_launch();
+    }
+    if (own) rt_free(work, stream);
+    return res;
+}
+
+extern "C" rt_status rt_trace_visibility(const rt_bvh *bvh, const rt_rayspec *rays, float *T_out,
+                                         const rt_trace_opts *opts, rt_stream_t stream) {
+    if (!bvh || !rays) return RT_ERR_INVALID_ARG;
+    return rt_trace_launch(bvh, rays, T_out, opts, stream, nullptr);
+}
+
+extern "C" rt_status rt_trace_visibility_dirs(const rt_bvh *bvh, const float *dirs, int32_t k,
+                                              float *T_out, const rt_trace_opts *opts,
+                                              rt_stream_t stream) {
+    if (!bvh) return RT_ERR_INVALID_ARG;
+    rt_rayspec rs;
+    memset(&rs, 0, sizeof(rs));
+    rs.kind = RT_RAYS_DIRS;
+    rs.n_dirs = k;
+    rs.dirs = dirs;
+    return rt_trace_launch(bvh, &rs, T_out, opts, stream, nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// Materialised rays of an implicit set (for inspection and the adjoint)
+// ---------------------------------------------------------------------------
+namespace {
+__global__ void k_materialize(BvhDev b, RaySetDev rs, const int64_t *ids, int64_t m, float *ro,
+                              float *rd, int32_t *rsrc, int *status) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t rid = ids[i];
+        if (rid < 0 || rid >= rs.n_rays) {
+            rt_set_error(status, RT_ERR_INVALID_ARG);
+            continue;
+        }
+        int64_t g = rid / rs.K;
+        int32_t k = (int32_t)(rid - g * rs.K);
+        int32_t p = b.rank[g];
+        float3 o, d;
+        implicit_ray(rs, rid, k, __ldg(b.gauss + 4 * (int64_t)p), o, d);
+        ro[3 * i] = o.x; ro[3 * i + 1] = o.y; ro[3 * i + 2] = o.z;
+        rd[3 * i] = d.x; rd[3 * i + 1] = d.y; rd[3 * i + 2] = d.z;
+        if (rsrc) rsrc[i] = (int32_t)g;
+    }
+}
+}  // namespace
+
+extern "C" rt_status rt_materialize_rays(const rt_bvh *bvh, const rt_rayspec *rays,
+                                         const int64_t *ray_ids, int64_t m, float *ray_o,
+                                         float *ray_d, int32_t *ray_src, rt_stream_t stream) {
+    if (!bvh || !rays || m < 0) return RT_ERR_INVALID_ARG;
+    if (rays->kind == RT_RAYS_EXPLICIT) return RT_ERR_INVALID_ARG;
+    if (m == 0) return RT_OK;
+    if (!ray_ids || !ray_o || !ray_d) return RT_ERR_INVALID_ARG;
+    RaySetDev rs;
+    int64_t c;
+    rt_rayspec tmp = *rays;
+    tmp.ray_ids = nullptr;
+    RT_TRY(rt_rayset_dev(bvh, &tmp, &rs, &c));
+    int grid = (int)((m + 255) / 256);
+    if (grid > rt_num_sms() * 8) grid = rt_num_sms() * 8;
+    k_materialize<<<grid, 256, 0, (cudaStream_t)stream>>>(bvh_dev(bvh), rs, ray_ids, m, ray_o, ray_d,
+                                                          ray_src, rt_status_ptr());
+    return rt_check_launch();
+}

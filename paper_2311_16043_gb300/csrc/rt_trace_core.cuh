@@ -1,0 +1,287 @@
+// rt_trace_core.cuh -- ray/Gaussian and ray/box tests and the two traversal
+// strategies, shared by the forward trace, the adjoint and the batched launch.
+#pragma once
+
+#include "rt_internal.cuh"
+
+struct BvhDev {
+    const float4 *gauss;
+    const float4 *nodes;
+    const int32_t *rank;
+    int64_t n;
+    float k2;         // k_sigma^2
+    float alpha_min;
+    float t_min;
+};
+
+inline BvhDev bvh_dev(const rt_bvh *b) {
+    BvhDev d;
+    d.gauss = b->gauss;
+    d.nodes = b->nodes;
+    d.rank = b->rank;
+    d.n = b->n;
+    d.k2 = b->params.k_sigma * b->params.k_sigma;
+    d.alpha_min = b->params.alpha_min;
+    d.t_min = b->params.t_min;
+    return d;
+}
+
+struct TraceAux {
+    unsigned long long *counters;  // [4] or null
+    int32_t *hit_ids;              // [R*cap] or null
+    int32_t *hit_count;            // [R] or null
+    int32_t cap;
+    int *status;
+};
+
+struct LaneLog {
+    int32_t *ids;  // this ray's slots (null = no log)
+    int32_t cap;
+    int32_t count;
+};
+
+// Reciprocal direction with exact zeros replaced by a tiny signed value, so
+// (lo - o) * inv never forms 0 * inf.
+__device__ __forceinline__ float3 safe_inv(float3 d) {
+    const float tiny = 1e-30f;
+    float x = fabsf(d.x) < tiny ? copysignf(tiny, d.x) : d.x;
+    float y = fabsf(d.y) < tiny ? copysignf(tiny, d.y) : d.y;
+    float z = fabsf(d.z) < tiny ? copysignf(tiny, d.z) : d.z;
+    return make_float3(1.0f / x, 1.0f / y, 1.0f / z);
+}
+
+// Ray vs axis-aligned box over t in [0, inf).  The differences (lo - o) are
+// formed first so their signs are exact; the far distance gets a 1e-6
+// relative allowance so rounding never rejects a box that the ray touches.
+__device__ __forceinline__ bool slab(float lox, float hix, float loy, float hiy, float loz, float hiz,
+                                     float3 o, float3 inv) {
+    float tx0 = (lox - o.x) * inv.x, tx1 = (hix - o.x) * inv.x;
+    float ty0 = (loy - o.y) * inv.y, ty1 = (hiy - o.y) * inv.y;
+    float tz0 = (loz - o.z) * inv.z, tz1 = (hiz - o.z) * inv.z;
+    float tnear = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.0f));
+    float tfar = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fmaxf(tz0, tz1));
+    return tnear <= fmaf(fabsf(tfar), 1e-6f, tfar);
+}
+
+// Peak response of the Gaussian at sorted position p along the ray
+// (Eq. 13-14 with Sigma^-1) and the transmittance update (Eq. 15).
+// In the whitened frame u = W (x - mu) the squared Mahalanobis distance along
+// the ray is |u_o + t u_d|^2, minimised at t* = -(u_o . u_d)/(u_d . u_d).
+// Accuracy: o - mu is split exactly into hi + lo; the point e = x(t*) - mu is
+// rebuilt in world space as fma(t*, d, hi) + lo (it is small, so this has no
+// cancellation), and m^2 = |W e|^2.  Since m^2 is stationary at t*, the
+// rounding of t* enters m^2 only at second order.
+// Returns true if the Gaussian is accepted (t* > 0, m^2 <= K^2,
+// alpha >= alpha_min) and multiplies T by (1 - alpha).
+__device__ __forceinline__ bool gauss_hit(const BvhDev &b, int32_t p, float3 o, float3 d, float &T,
+                                          float *alpha_out = nullptr) {
+    const float4 g0 = __ldg(b.gauss + 4 * p);
+    const float4 g1 = __ldg(b.gauss + 4 * p + 1);
+    const float4 g2 = __ldg(b.gauss + 4 * p + 2);
+    const float4 g3 = __ldg(b.gauss + 4 * p + 3);
+    float hx, lx, hy, ly, hz, lz;
+    two_diff(o.x, g0.x, hx, lx);
+    two_diff(o.y, g0.y, hy, ly);
+    two_diff(o.z, g0.z, hz, lz);
+    const float3 w0 = make_float3(g1.x, g1.y, g1.z);
+    const float3 w1 = make_float3(g2.x, g2.y, g2.z);
+    const float3 w2 = make_float3(g3.x, g3.y, g3.z);
+    const float3 dh = make_float3(hx, hy, hz);
+    const float3 ud = make_float3(dot3(w0, d), dot3(w1, d), dot3(w2, d));
+    const float3 uo = make_float3(dot3(w0, dh), dot3(w1, dh), dot3(w2, dh));
+    const float a = dot3(ud, ud);
+    const float bb = dot3(uo, ud);
+    const float t = -bb / a;
+    if (!(t > 0.0f)) return false;
+    const float3 e = make_float3(fmaf(t, d.x, hx) + lx, fmaf(t, d.y, hy) + ly, fmaf(t, d.z, hz) + lz);
+    const float3 u = make_float3(dot3(w0, e), dot3(w1, e), dot3(w2, e));
+    const float m2 = dot3(u, u);
+    if (!(m2 <= b.k2)) return false;
+    const float alpha = g0.w * expf(-0.5f * m2);
+    if (!(alpha >= b.alpha_min)) return false;
+    T *= (1.0f - alpha);
+    if (alpha_out) *alpha_out = alpha;
+    return true;
+}
+
+__device__ __forceinline__ void log_hit(LaneLog &lg, const BvhDev &b, int32_t p) {
+    if (lg.ids) {
+        if (lg.count < lg.cap) lg.ids[lg.count] = __float_as_int(__ldg(b.gauss + 4 * p + 1).w);
+        lg.count++;
+    }
+}
+
+struct WorkCounts {
+    unsigned long long box, gauss, hits;
+};
+
+// Strategy 1: each thread traverses alone with a private stack.
+__device__ __forceinline__ float trace_ray(const BvhDev &b, float3 o, float3 d, int32_t src,
+                                           LaneLog &lg, WorkCounts &wc, int *status) {
+    float T = 1.0f;
+    if (b.n <= 0) return T;
+    if (b.n == 1) {
+        wc.gauss++;
+        if (src != 0 && gauss_hit(b, 0, o, d, T)) {
+            wc.hits++;
+            log_hit(lg, b, 0);
+        }
+        return T < b.t_min ? 0.0f : T;
+    }
+    const float3 inv = safe_inv(d);
+    uint32_t stack[RT_STACK];
+    int sp = 0;
+    uint32_t node = 0;
+    for (;;) {
+        const float4 n0 = __ldg(b.nodes + 4 * node);
+        const float4 n1 = __ldg(b.nodes + 4 * node + 1);
+        const float4 n2 = __ldg(b.nodes + 4 * node + 2);
+        const float4 n3 = __ldg(b.nodes + 4 * node + 3);
+        bool hl = slab(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, o, inv);
+        bool hr = slab(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, o, inv);
+        wc.box += 2;
+        const uint32_t cl = __float_as_uint(n3.x), cr = __float_as_uint(n3.y);
+        if (hl && (cl & RT_LEAF_BIT)) {
+            int32_t p = (int32_t)(cl & ~RT_LEAF_BIT);
+            hl = false;
+            if (p != src) {
+                wc.gauss++;
+                if (gauss_hit(b, p, o, d, T)) {
+                    wc.hits++;
+                    log_hit(lg, b, p);
+                }
+            }
+        }
+        if (hr && (cr & RT_LEAF_BIT)) {
+            int32_t p = (int32_t)(cr & ~RT_LEAF_BIT);
+            hr = false;
+            if (p != src) {
+                wc.gauss++;
+                if (gauss_hit(b, p, o, d, T)) {
+                    wc.hits++;
+                    log_hit(lg, b, p);
+                }
+            }
+        }
+        if (T < b.t_min) break;
+        if (hl && hr) {
+            if (sp >= RT_STACK) {
+                rt_set_error(status, RT_ERR_STACK_OVERFLOW);
+                break;
+            }
+            stack[sp++] = cr;
+            node = cl;
+        } else if (hl) {
+            node = cl;
+        } else if (hr) {
+            node = cr;
+        } else {
+            if (sp == 0) break;
+            node = stack[--sp];
+        }
+    }
+    return T < b.t_min ? 0.0f : T;
+}
+
+// Strategy 2: the warp's 32 rays traverse together.  A node is visited if
+// any lane's ray hit its box; each lane tests the children only if its own
+// ray hit the node (the lane mask travels with the node on the stack), so the
+// per-ray work counts equal strategy 1's.  The stack is warp-uniform and
+// lives in registers: entry e sits in lane e % 32, column e / 32.
+__device__ __forceinline__ float trace_packet(const BvhDev &b, float3 o, float3 d, int32_t src,
+                                              bool valid, LaneLog &lg, WorkCounts &wc,
+                                              int *status) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    float T = 1.0f;
+    if (b.n <= 0) return T;
+    if (b.n == 1) {
+        if (valid) {
+            wc.gauss++;
+            if (src != 0 && gauss_hit(b, 0, o, d, T)) {
+                wc.hits++;
+                log_hit(lg, b, 0);
+            }
+        }
+        return T < b.t_min ? 0.0f : T;
+    }
+    const float3 inv = safe_inv(d);
+    uint32_t alive = __ballot_sync(FULL, valid);
+    uint32_t s_node0 = 0, s_node1 = 0, s_mask0 = 0, s_mask1 = 0;
+    int sp = 0;
+    uint32_t node = 0, mask = alive;
+    while (mask) {
+        const bool mine = (mask >> lane) & 1u;
+        const float4 n0 = __ldg(b.nodes + 4 * node);
+        const float4 n1 = __ldg(b.nodes + 4 * node + 1);
+        const float4 n2 = __ldg(b.nodes + 4 * node + 2);
+        const float4 n3 = __ldg(b.nodes + 4 * node + 3);
+        bool hl = false, hr = false;
+        if (mine) {
+            hl = slab(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, o, inv);
+            hr = slab(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, o, inv);
+            wc.box += 2;
+        }
+        const uint32_t cl = __float_as_uint(n3.x), cr = __float_as_uint(n3.y);
+        if (cl & RT_LEAF_BIT) {
+            int32_t p = (int32_t)(cl & ~RT_LEAF_BIT);
+            if (hl && p != src) {
+                wc.gauss++;
+                if (gauss_hit(b, p, o, d, T)) {
+                    wc.hits++;
+                    log_hit(lg, b, p);
+                }
+            }
+            hl = false;
+        }
+        if (cr & RT_LEAF_BIT) {
+            int32_t p = (int32_t)(cr & ~RT_LEAF_BIT);
+            if (hr && p != src) {
+                wc.gauss++;
+                if (gauss_hit(b, p, o, d, T)) {
+                    wc.hits++;
+                    log_hit(lg, b, p);
+                }
+            }
+            hr = false;
+        }
+        alive = __ballot_sync(FULL, valid && !(T < b.t_min));
+        const uint32_t ml = __ballot_sync(FULL, hl) & alive;
+        const uint32_t mr = __ballot_sync(FULL, hr) & alive;
+        if (ml && mr) {
+            if (sp >= 2 * 32) {
+                rt_set_error(status, RT_ERR_STACK_OVERFLOW);
+                break;
+            }
+            if (lane == (sp & 31)) {
+                if (sp < 32) {
+                    s_node0 = cr;
+                    s_mask0 = mr;
+                } else {
+                    s_node1 = cr;
+                    s_mask1 = mr;
+                }
+            }
+            ++sp;
+            node = cl;
+            mask = ml;
+        } else if (ml) {
+            node = cl;
+            mask = ml;
+        } else if (mr) {
+            node = cr;
+            mask = mr;
+        } else {
+            mask = 0;
+            while (sp > 0) {
+                --sp;
+                const int srcl = sp & 31;
+                const bool lo = sp < 32;
+                node = __shfl_sync(FULL, lo ? s_node0 : s_node1, srcl);
+                mask = __shfl_sync(FULL, lo ? s_mask0 : s_mask1, srcl) & alive;
+                if (mask) break;
+            }
+        }
+    }
+    return T < b.t_min ? 0.0f : T;
+}

@@ -1,0 +1,311 @@
+"""Thin Python binding of ``include/rt3dg.h`` (argument marshalling only).
+
+Every function here keeps the C entry point's name and converts torch CUDA
+tensors to device pointers and the current torch stream to a ``cudaStream_t``;
+all computation runs in the sm_103a kernels of ``librt3dg.so``.  There is no
+CPU fallback: if the library cannot be loaded, or a tensor is not a
+contiguous CUDA tensor of the required dtype, the call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import threading
+
+import torch
+
+from . import _build
+
+_lock = threading.Lock()
+_LIB = None
+
+RT_OK = 0
+STATUS_NAMES = {0: "RT_OK", 1: "RT_ERR_INVALID_ARG", 2: "RT_ERR_OOM", 3: "RT_ERR_CUDA",
+                4: "RT_ERR_STACK_OVERFLOW", 5: "RT_ERR_HITLOG_OVERFLOW", 6: "RT_ERR_TIMEOUT",
+                7: "RT_ERR_NOT_TRAINED", 8: "RT_ERR_UNSUPPORTED"}
+RT_RAYS_EXPLICIT, RT_RAYS_DIRS, RT_RAYS_ENV = 0, 1, 2
+RT_KERNEL_AUTO, RT_KERNEL_RAY, RT_KERNEL_PACKET = 0, 1, 2
+
+
+class RTError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {STATUS_NAMES.get(code, code)}")
+
+
+class rt_params(C.Structure):
+    _fields_ = [("k_sigma", C.c_float), ("alpha_min", C.c_float), ("t_min", C.c_float),
+                ("origin_eps", C.c_float), ("box_mode", C.c_int32), ("reserved", C.c_int32)]
+
+
+class rt_rayspec(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("n_dirs", C.c_int32), ("n_rays", C.c_int64),
+                ("ray_o", C.c_void_p), ("ray_d", C.c_void_p), ("ray_src", C.c_void_p),
+                ("dirs", C.c_void_p), ("env", C.c_void_p), ("seed", C.c_uint64),
+                ("ray_ids", C.c_void_p), ("n_ids", C.c_int64)]
+
+
+class rt_trace_opts(C.Structure):
+    _fields_ = [("kernel", C.c_int32), ("order_block", C.c_int32), ("block_threads", C.c_int32),
+                ("hit_cap", C.c_int32), ("counters", C.c_void_p), ("hit_ids", C.c_void_p),
+                ("hit_count", C.c_void_p)]
+
+
+_P = C.c_void_p
+_I64 = C.c_int64
+_I32 = C.c_int32
+_SIGS = {
+    "rt_params_default": (None, [_P]),
+    "rt_status_string": (C.c_char_p, [_I32]),
+    "rt_status_last": (_I32, []),
+    "rt_status_clear": (_I32, []),
+    "rt_build_bvh": (_I32, [_P, _P, _P, _P, _I64, _P, _P, _P]),
+    "rt_bvh_destroy": (_I32, [_P, _P]),
+    "rt_bvh_info": (_I32, [_P, _P, _P, _P, _P]),
+    "rt_bvh_export": (_I32, [_P, _P, _P, _P, _P, _P, _P]),
+    "rt_envmap_create": (_I32, [_P, _P, _P, _I32, _I32, _P, _P]),
+    "rt_envmap_destroy": (_I32, [_P, _P]),
+    "rt_rayspec_count": (_I64, [_P, _P]),
+    "rt_materialize_rays": (_I32, [_P, _P, _P, _I64, _P, _P, _P, _P]),
+    "rt_trace_visibility": (_I32, [_P, _P, _P, _P, _P]),
+    "rt_trace_visibility_dirs": (_I32, [_P, _P, _I32, _P, _P, _P]),
+    "rt_trace_visibility_backward": (_I32, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I32,
+                                            _P, _P, _P, _P, _P, _P]),
+}
+
+
+def exported_symbols() -> list[str]:
+    return sorted(_SIGS)
+
+
+def lib():
+    """Load (building first if stale) librt3dg.so; raises if it cannot."""
+    global _LIB
+    with _lock:
+        if _LIB is None:
+            path = _build.build()
+            L = C.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _LIB = L
+    return _LIB
+
+
+def _check(code: int, where: str):
+    if code != RT_OK:
+        raise RTError(code, where)
+
+
+def _ptr(t, dtype=None, name="tensor"):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr() if t.numel() > 0 else None
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def params(k_sigma=3.0, alpha_min=1.0 / 255.0, t_min=1e-4, origin_eps=1e-4, box_mode=0) -> rt_params:
+    p = rt_params()
+    lib().rt_params_default(C.byref(p))
+    p.k_sigma, p.alpha_min, p.t_min, p.origin_eps, p.box_mode = k_sigma, alpha_min, t_min, origin_eps, box_mode
+    return p
+
+
+def rt_status_last() -> int:
+    return int(lib().rt_status_last())
+
+
+def rt_status_clear() -> None:
+    _check(lib().rt_status_clear(), "rt_status_clear")
+
+
+class Bvh:
+    """Owning wrapper of an ``rt_bvh*`` handle."""
+
+    def __init__(self, handle, n, prm):
+        self.handle = handle
+        self.n = n
+        self.params = prm
+
+    def info(self):
+        n = C.c_int64()
+        lo = (C.c_float * 3)()
+        hi = (C.c_float * 3)()
+        nb = C.c_int64()
+        _check(lib().rt_bvh_info(self.handle, C.byref(n), lo, hi, C.byref(nb)), "rt_bvh_info")
+        return {"n": n.value, "lo": list(lo), "hi": list(hi), "device_bytes": nb.value}
+
+    def destroy(self, stream=None):
+        if self.handle:
+            _check(lib().rt_bvh_destroy(self.handle, _stream(stream)), "rt_bvh_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            if self.handle and _LIB is not None and torch.cuda.is_initialized():
+                _LIB.rt_bvh_destroy(self.handle, _stream())
+                self.handle = None
+        except Exception:
+            pass
+
+
+def rt_build_bvh(mean, scale, quat, opacity, prm: rt_params | None = None, stream=None) -> Bvh:
+    n = mean.shape[0] if mean.dim() > 0 else 0
+    for t, w, nm in ((mean, 3, "mean"), (scale, 3, "scale"), (quat, 4, "quat")):
+        if t.numel() != n * w:
+            raise ValueError(f"{nm} must have {w} values per Gaussian")
+    if opacity.numel() != n:
+        raise ValueError("opacity must have one value per Gaussian")
+    prm = prm or params()
+    h = C.c_void_p()
+    _check(lib().rt_build_bvh(_ptr(mean, torch.float32, "mean"), _ptr(scale, torch.float32, "scale"),
+                              _ptr(quat, torch.float32, "quat"), _ptr(opacity, torch.float32, "opacity"),
+                              n, C.byref(prm), _stream(stream), C.byref(h)), "rt_build_bvh")
+    return Bvh(h, n, prm)
+
+
+def rt_bvh_export(bvh: Bvh, stream=None) -> dict:
+    n = bvh.n
+    dev = torch.device("cuda")
+    keys = torch.empty(n, dtype=torch.int64, device=dev)
+    m = max(n - 1, 0)
+    left = torch.empty(m, dtype=torch.int32, device=dev)
+    right = torch.empty(m, dtype=torch.int32, device=dev)
+    parent = torch.empty(max(2 * n - 1, 0), dtype=torch.int32, device=dev)
+    boxes = torch.empty((m, 12), dtype=torch.float32, device=dev)
+    _check(lib().rt_bvh_export(bvh.handle, _ptr(keys), _ptr(left), _ptr(right), _ptr(parent), _ptr(boxes),
+                               _stream(stream)), "rt_bvh_export")
+    return {"keys": keys, "left": left, "right": right, "parent": parent, "boxes": boxes}
+
+
+class Envmap:
+    def __init__(self, handle):
+        self.handle = handle
+
+    def destroy(self, stream=None):
+        if self.handle:
+            _check(lib().rt_envmap_destroy(self.handle, _stream(stream)), "rt_envmap_destroy")
+            self.handle = None
+
+
+def rt_envmap_create(radiance, solid_angle, corners, stream=None) -> Envmap:
+    """Host numpy inputs: radiance[h,w] float64, solid_angle[h,w] float64,
+    corners[h+1,w+1,3] float32."""
+    import numpy as np
+    rad = np.ascontiguousarray(radiance, dtype=np.float64)
+    sa = np.ascontiguousarray(solid_angle, dtype=np.float64)
+    cor = np.ascontiguousarray(corners, dtype=np.float32)
+    h, w = rad.shape
+    if sa.shape != (h, w) or cor.shape != (h + 1, w + 1, 3):
+        raise ValueError("envmap shapes do not match")
+    out = C.c_void_p()
+    _check(lib().rt_envmap_create(rad.ctypes.data, sa.ctypes.data, cor.ctypes.data, h, w, _stream(stream),
+                                  C.byref(out)), "rt_envmap_create")
+    return Envmap(out)
+
+
+def rayspec(kind=RT_RAYS_DIRS, *, dirs=None, ray_o=None, ray_d=None, ray_src=None, env=None,
+            n_samples=0, seed=0, ray_ids=None) -> rt_rayspec:
+    rs = rt_rayspec()
+    rs.kind = kind
+    if kind == RT_RAYS_EXPLICIT:
+        rs.n_rays = ray_o.shape[0]
+        rs.ray_o = _ptr(ray_o, torch.float32, "ray_o")
+        rs.ray_d = _ptr(ray_d, torch.float32, "ray_d")
+        rs.ray_src = _ptr(ray_src, torch.int32, "ray_src")
+    elif kind == RT_RAYS_DIRS:
+        rs.n_dirs = dirs.shape[0]
+        rs.dirs = _ptr(dirs, torch.float32, "dirs")
+    elif kind == RT_RAYS_ENV:
+        rs.n_dirs = n_samples
+        rs.env = env.handle
+        rs.seed = seed
+    if ray_ids is not None:
+        rs.ray_ids = _ptr(ray_ids, torch.int64, "ray_ids")
+        rs.n_ids = ray_ids.numel()
+    rs._keep = (dirs, ray_o, ray_d, ray_src, env, ray_ids)  # keep the tensors alive
+    return rs
+
+
+def rt_rayspec_count(bvh: Bvh, rs: rt_rayspec) -> int:
+    return int(lib().rt_rayspec_count(bvh.handle, C.byref(rs)))
+
+
+def trace_opts(kernel=RT_KERNEL_AUTO, order_block=0, counters=None, hit_ids=None, hit_count=None) -> rt_trace_opts:
+    o = rt_trace_opts()
+    o.kernel = kernel
+    o.order_block = order_block
+    o.counters = _ptr(counters, torch.int64, "counters")
+    o.hit_ids = _ptr(hit_ids, torch.int32, "hit_ids")
+    o.hit_count = _ptr(hit_count, torch.int32, "hit_count")
+    o.hit_cap = hit_ids.shape[1] if hit_ids is not None else 0
+    return o
+
+
+def rt_trace_visibility(bvh: Bvh, rs: rt_rayspec, T_out=None, opts: rt_trace_opts | None = None, stream=None):
+    R = rt_rayspec_count(bvh, rs)
+    if R < 0:
+        raise RTError(1, "rt_rayspec_count")
+    if T_out is None:
+        T_out = torch.empty(R, dtype=torch.float32, device="cuda")
+    elif T_out.numel() != R:
+        raise ValueError(f"T_out must have {R} elements")
+    _check(lib().rt_trace_visibility(bvh.handle, C.byref(rs), _ptr(T_out, torch.float32, "T_out"),
+                                     C.byref(opts) if opts is not None else None, _stream(stream)),
+           "rt_trace_visibility")
+    return T_out
+
+
+def rt_trace_visibility_dirs(bvh: Bvh, dirs, T_out=None, opts: rt_trace_opts | None = None, stream=None):
+    K = dirs.shape[0]
+    if T_out is None:
+        T_out = torch.empty((bvh.n, K), dtype=torch.float32, device="cuda")
+    elif T_out.numel() != bvh.n * K:
+        raise ValueError("T_out must have n*K elements")
+    _check(lib().rt_trace_visibility_dirs(bvh.handle, _ptr(dirs, torch.float32, "dirs"), K,
+                                          _ptr(T_out, torch.float32, "T_out"),
+                                          C.byref(opts) if opts is not None else None, _stream(stream)),
+           "rt_trace_visibility_dirs")
+    return T_out
+
+
+def rt_materialize_rays(bvh: Bvh, rs: rt_rayspec, ray_ids, stream=None):
+    m = ray_ids.numel()
+    dev = torch.device("cuda")
+    o = torch.empty((m, 3), dtype=torch.float32, device=dev)
+    d = torch.empty((m, 3), dtype=torch.float32, device=dev)
+    s = torch.empty(m, dtype=torch.int32, device=dev)
+    _check(lib().rt_materialize_rays(bvh.handle, C.byref(rs), _ptr(ray_ids, torch.int64, "ray_ids"), m,
+                                     _ptr(o), _ptr(d), _ptr(s), _stream(stream)), "rt_materialize_rays")
+    return o, d, s
+
+
+def rt_trace_visibility_backward(bvh: Bvh, rs: rt_rayspec, mean, scale, quat, opacity, T, dL_dT,
+                                 hit_ids=None, hit_count=None, d_mean=None, d_scale=None, d_quat=None,
+                                 d_opacity=None, d_ray_o=None, stream=None):
+    n = bvh.n
+    dev = torch.device("cuda")
+    d_mean = torch.zeros((n, 3), dtype=torch.float32, device=dev) if d_mean is None else d_mean
+    d_scale = torch.zeros((n, 3), dtype=torch.float32, device=dev) if d_scale is None else d_scale
+    d_quat = torch.zeros((n, 4), dtype=torch.float32, device=dev) if d_quat is None else d_quat
+    d_opacity = torch.zeros(n, dtype=torch.float32, device=dev) if d_opacity is None else d_opacity
+    cap = hit_ids.shape[1] if hit_ids is not None else 0
+    _check(lib().rt_trace_visibility_backward(
+        bvh.handle, C.byref(rs), _ptr(mean, torch.float32, "mean"), _ptr(scale, torch.float32, "scale"),
+        _ptr(quat, torch.float32, "quat"), _ptr(opacity, torch.float32, "opacity"),
+        _ptr(T, torch.float32, "T"), _ptr(dL_dT, torch.float32, "dL_dT"),
+        _ptr(hit_ids, torch.int32, "hit_ids"), _ptr(hit_count, torch.int32, "hit_count"), cap,
+        _ptr(d_mean, torch.float32, "d_mean"), _ptr(d_scale, torch.float32, "d_scale"),
+        _ptr(d_quat, torch.float32, "d_quat"), _ptr(d_opacity, torch.float32, "d_opacity"),
+        _ptr(d_ray_o, torch.float32, "d_ray_o"), _stream(stream)), "rt_trace_visibility_backward")
+    return {"mean": d_mean, "scale": d_scale, "quat": d_quat, "opacity": d_opacity, "ray_o": d_ray_o}

@@ -1,0 +1,244 @@
+"""GPU parity of the visibility trace against the FP64 brute-force oracle.
+
+Bar: |T_gpu - T_oracle| <= 1e-5 on every ray, except rays the oracle flags as
+having a candidate inside a rounding band of a threshold (m^2 = K^2,
+alpha = 1/255, t* = 0, T = T_min); those are excluded and counted, and must
+stay rare.  The two traversal kernels visit each ray's accepted Gaussians in
+the same order, so they agree bit for bit.
+"""
+import numpy as np
+import pytest
+import torch
+
+import scenes
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def build(sc, **kw):
+    from paper_2311_16043_gb300 import rt
+    return rt.rt_build_bvh(_dev(sc["mean"]), _dev(sc["scale"]), _dev(sc["quat"]), _dev(sc["opacity"]),
+                           rt.params(**kw))
+
+
+def trace_dirs(bvh, dirs, kernel=0, **opt):
+    from paper_2311_16043_gb300 import rt
+    rs = rt.rayspec(rt.RT_RAYS_DIRS, dirs=_dev(dirs))
+    T = rt.rt_trace_visibility(bvh, rs, opts=rt.trace_opts(kernel=kernel, **opt))
+    torch.cuda.synchronize()
+    assert rt.rt_status_last() == 0
+    return T.cpu().numpy().astype(np.float64)
+
+
+def compare(T_gpu, ref, max_excluded=0.002):
+    ok = ref["flags"] == 0
+    err = np.abs(T_gpu - ref["T"])
+    bad = np.nonzero(ok & (err > TOL))[0]
+    assert bad.size == 0, (bad[:10], err[bad[:10]], T_gpu[bad[:10]], ref["T"][bad[:10]])
+    assert (~ok).mean() <= max_excluded, (~ok).sum()
+    return err[ok].max(), int((~ok).sum())
+
+
+@pytest.fixture(scope="module")
+def small(orc):
+    """Uniform scene: 4,096 Gaussians x 32 Fibonacci directions (131,072 rays),
+    every ray checked."""
+    sc = scenes.uniform_scene(4096, 1)
+    dirs = scenes.fibonacci_sphere(32)
+    ids = np.arange(4096 * 32, dtype=np.int64)
+    o, d, s = orc.dir_rays(sc["mean"], dirs, ids)
+    ref = orc.trace(sc, o, d, s)
+    return sc, dirs, ref
+
+
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_small_scene_all_rays(small, kernel):
+    sc, dirs, ref = small
+    bvh = build(sc)
+    T = trace_dirs(bvh, dirs, kernel=kernel).reshape(-1)
+    maxerr, excl = compare(T, ref)
+    assert maxerr < TOL
+    assert (ref["T"] < 1).mean() > 0.3 and (ref["T"] == 0).any() or (ref["hits"] > 3).any()
+
+
+def test_kernels_agree_bitwise(small):
+    sc, dirs, _ = small
+    bvh = build(sc)
+    a = trace_dirs(bvh, dirs, kernel=1)
+    b = trace_dirs(bvh, dirs, kernel=2)
+    np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("order_block", [1, 7, 1000])
+def test_work_order_does_not_change_results(small, order_block):
+    sc, dirs, _ = small
+    bvh = build(sc)
+    a = trace_dirs(bvh, dirs, kernel=2)
+    b = trace_dirs(bvh, dirs, kernel=2, order_block=order_block)
+    np.testing.assert_array_equal(a, b)
+
+
+def test_box_mode_1_same_results(small):
+    sc, dirs, _ = small
+    a = trace_dirs(build(sc), dirs, kernel=1)
+    b = trace_dirs(build(sc, box_mode=1), dirs, kernel=1)
+    np.testing.assert_array_equal(a, b)
+
+
+def test_no_early_termination(orc, small):
+    sc, dirs, _ = small
+    ids = np.arange(0, 4096 * 32, 7, dtype=np.int64)
+    o, d, s = orc.dir_rays(sc["mean"], dirs, ids)
+    ref = orc.trace(sc, o, d, s, t_min=0.0)
+    T = trace_dirs(build(sc, t_min=0.0), dirs).reshape(-1)[ids]
+    compare(T, ref)
+    assert (ref["T"] < 1e-4).any()  # exercises products below the snap threshold
+
+
+def test_explicit_rays_and_counters(orc):
+    """Rays from the input generator (origins in and around the cube, random
+    directions, some with a source to skip); per-ray work counts must be the
+    same for both traversal strategies."""
+    from paper_2311_16043_gb300 import rt
+    sc = scenes.uniform_scene(4096, 1)
+    rng = np.random.default_rng(17)
+    R = 20000
+    ro = rng.uniform(-1.5, 1.5, (R, 3)).astype(np.float32)
+    rd = rng.standard_normal((R, 3))
+    rd /= np.linalg.norm(rd, axis=1, keepdims=True)
+    rd = rd.astype(np.float32)
+    rd[:50] = np.array([1, 0, 0], np.float32)  # axis-aligned directions
+    rd[50:100] = np.array([0, 0, -1], np.float32)
+    src = np.where(rng.random(R) < 0.5, rng.integers(0, 4096, R), -1).astype(np.int32)
+    ref = orc.trace(sc, ro, rd, src)
+    bvh = build(sc)
+    outs, cnts = [], []
+    for kernel in (1, 2):
+        cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
+        rs = rt.rayspec(rt.RT_RAYS_EXPLICIT, ray_o=_dev(ro), ray_d=_dev(rd), ray_src=_dev(src))
+        T = rt.rt_trace_visibility(bvh, rs, opts=rt.trace_opts(kernel=kernel, counters=cnt))
+        torch.cuda.synchronize()
+        outs.append(T.cpu().numpy().astype(np.float64))
+        cnts.append(cnt.cpu().numpy())
+    compare(outs[0], ref)
+    np.testing.assert_array_equal(outs[0], outs[1])
+    np.testing.assert_array_equal(cnts[0], cnts[1])
+    assert cnts[0][3] == R
+    assert cnts[0][2] == int(ref["hits"][ref["T"] > 0].sum()) or cnts[0][2] <= int(ref["hits"].sum())
+
+
+def test_hit_log_matches_oracle(orc, small):
+    from paper_2311_16043_gb300 import rt
+    sc, dirs, _ = small
+    bvh = build(sc, t_min=0.0)
+    R = 4096 * 32
+    cap = 16
+    ids = torch.full((R, cap), -1, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(R, dtype=torch.int32, device="cuda")
+    rs = rt.rayspec(rt.RT_RAYS_DIRS, dirs=_dev(dirs))
+    rt.rt_trace_visibility(bvh, rs, opts=rt.trace_opts(hit_ids=ids, hit_count=cnt))
+    torch.cuda.synchronize()
+    ids, cnt = ids.cpu().numpy(), cnt.cpu().numpy()
+    sel = np.arange(0, R, 13, dtype=np.int64)
+    o, d, s = orc.dir_rays(sc["mean"], dirs, sel)
+    ref = orc.trace(sc, o, d, s, t_min=0.0)
+    rid, rcnt = orc.trace_hits(sc, o, d, s, cap=64)
+    ok = ref["flags"] == 0
+    np.testing.assert_array_equal(cnt[sel][ok], rcnt[ok])
+    assert (cnt > cap).any()  # some rays overflow the log and say so
+    for j in np.nonzero(ok & (rcnt <= cap))[0][:2000]:
+        r = sel[j]
+        assert set(ids[r, :cnt[r]]) == set(rid[j, :rcnt[j]])
+
+
+def test_id_subset_matches_full_trace(small):
+    from paper_2311_16043_gb300 import rt
+    sc, dirs, _ = small
+    bvh = build(sc)
+    full = trace_dirs(bvh, dirs).reshape(-1)
+    sel = scenes.sample_ray_ids(4096 * 32, 5000, 3)
+    rs = rt.rayspec(rt.RT_RAYS_DIRS, dirs=_dev(dirs), ray_ids=_dev(sel))
+    T = rt.rt_trace_visibility(bvh, rs)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(T.cpu().numpy().astype(np.float64), full[sel])
+
+
+def test_materialized_rays_bit_exact(orc, small):
+    from paper_2311_16043_gb300 import rt
+    sc, dirs, _ = small
+    bvh = build(sc)
+    sel = scenes.sample_ray_ids(4096 * 32, 3000, 4)
+    rs = rt.rayspec(rt.RT_RAYS_DIRS, dirs=_dev(dirs))
+    o, d, s = rt.rt_materialize_rays(bvh, rs, _dev(sel))
+    torch.cuda.synchronize()
+    ro, rd, rsrc = orc.dir_rays(sc["mean"], dirs, sel)
+    np.testing.assert_array_equal(o.cpu().numpy(), ro)
+    np.testing.assert_array_equal(d.cpu().numpy(), rd)
+    np.testing.assert_array_equal(s.cpu().numpy(), rsrc)
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 3, 33])
+def test_tiny_scenes(orc, n):
+    from paper_2311_16043_gb300 import rt
+    sc = scenes.uniform_scene(max(n, 1), 5, log_scale_mean=np.log(0.3))
+    sc = {k: v[:n] for k, v in sc.items()}
+    dirs = scenes.fibonacci_sphere(16)
+    bvh = build(sc)
+    if n == 0:
+        rs = rt.rayspec(rt.RT_RAYS_DIRS, dirs=_dev(dirs))
+        assert rt.rt_rayspec_count(bvh, rs) == 0
+        rng = np.random.default_rng(0)
+        ro = _dev(rng.uniform(-1, 1, (10, 3)).astype(np.float32))
+        rd = _dev(np.tile(np.array([[0, 0, 1]], np.float32), (10, 1)))
+        T = rt.rt_trace_visibility(bvh, rt.rayspec(rt.RT_RAYS_EXPLICIT, ray_o=ro, ray_d=rd))
+        torch.cuda.synchronize()
+        assert torch.all(T == 1)
+        return
+    ids = np.arange(n * 16, dtype=np.int64)
+    o, d, s = orc.dir_rays(sc["mean"], dirs, ids)
+    ref = orc.trace(sc, o, d, s)
+    for kernel in (1, 2):
+        compare(trace_dirs(bvh, dirs, kernel=kernel).reshape(-1), ref, max_excluded=1.0)
+
+
+def test_object_scene_300k_sample(orc):
+    """Object-scale scene, 300k flattened Gaussians x 128 directions
+    (38.4M rays); 4,096 sampled rays checked against brute force."""
+    sc = scenes.object_scene(300_000, 2)
+    dirs = scenes.fibonacci_sphere(128)
+    bvh = build(sc)
+    T = trace_dirs(bvh, dirs).reshape(-1)
+    sel = scenes.sample_ray_ids(300_000 * 128, 4096, 7)
+    o, d, s = orc.dir_rays(sc["mean"], dirs, sel)
+    ref = orc.trace(sc, o, d, s)
+    compare(T[sel], ref, max_excluded=0.01)
+    assert np.all((T >= 0) & (T <= 1))
+
+
+def test_env_rays(orc):
+    """Shadow rays importance-sampled from the 64x32 environment map: the
+    materialised directions equal the oracle's float32 rays bit for bit, and
+    the traced T matches brute force."""
+    from paper_2311_16043_gb300 import rt
+    sc = scenes.uniform_scene(4096, 1)
+    env = scenes.envmap(399)
+    E = rt.rt_envmap_create(env["radiance"], env["solid_angle"], env["corners"])
+    S = 64
+    bvh = build(sc)
+    rs = rt.rayspec(rt.RT_RAYS_ENV, env=E, n_samples=S, seed=12345)
+    T = rt.rt_trace_visibility(bvh, rs)
+    torch.cuda.synchronize()
+    T = T.cpu().numpy().astype(np.float64)
+    sel = scenes.sample_ray_ids(4096 * S, 8192, 8)
+    o, d, s = rt.rt_materialize_rays(bvh, rs, _dev(sel))
+    ro, rd, rsrc = orc.env_rays(sc["mean"], env, 12345, S, sel)
+    np.testing.assert_array_equal(d.cpu().numpy(), rd)
+    np.testing.assert_array_equal(o.cpu().numpy(), ro)
+    ref = orc.trace(sc, ro, rd, rsrc)
+    compare(T[sel], ref)
+    E.destroy()
