@@ -225,6 +225,124 @@ rt_status rt_trace_visibility_backward(const rt_bvh *bvh, const rt_rayspec *rays
                                        float *d_quat, float *d_opacity, float *d_ray_o,
                                        rt_stream_t stream);
 
+
+/* ------------------------------------------------------------------------ */
+/* Learned visibility surrogate (not in the paper)                            */
+/* ------------------------------------------------------------------------ */
+/*
+ * A small MLP predicts T from a ray's origin and direction; rays whose
+ * prediction is uncertain fall back to the tracer.  The paper precomputes
+ * visibility by tracing only (Sec. 4.2); this is an addition.
+ *
+ * Network: six scalars (origin normalised to [-1,1] by the scene bounds
+ * lo/hi, p_n = 2 (p - lo)/(hi - lo) - 1, then the direction), each expanded
+ * to [x, sin(2^k pi x), cos(2^k pi x), k = 0..5] -> 78 features + 2 zeros =
+ * 80 inputs; four hidden layers of 128 with ReLU; one sigmoid output.
+ * Weights and activations are bf16 on the tensor cores with float32
+ * accumulation; biases, the output layer and the master copy of all weights
+ * are float32.  Loss: mean binary cross-entropy against soft targets T;
+ * optimiser: Adam.
+ *
+ * Parameter block (float32, rt_surrogate_param_count() = 60033 values):
+ *   W1[128][80], b1[128], W2[128][128], b2[128], W3[128][128], b3[128],
+ *   W4[128][128], b4[128], w5[128], b5.
+ */
+typedef struct rt_surrogate rt_surrogate;
+
+typedef struct {
+    float lr;      /* Adam step size (1e-3)                       */
+    float beta1;   /* 0.9                                         */
+    float beta2;   /* 0.999                                       */
+    float eps;     /* 1e-8                                        */
+    int32_t batch; /* samples per training step (262144)          */
+    int32_t reserved;
+} rt_mlp_cfg;
+
+void rt_mlp_cfg_default(rt_mlp_cfg *cfg);
+int64_t rt_surrogate_param_count(void);
+
+/* Creates a surrogate with He-uniform weights drawn from Philox4x64-10 keyed
+ * by `seed` (zero biases), Adam state zeroed, scene bounds (-1,-1,-1)..(1,1,1).
+ * Synchronises `stream`. */
+rt_status rt_surrogate_create(const rt_mlp_cfg *cfg, uint64_t seed, rt_stream_t stream,
+                              rt_surrogate **out);
+rt_status rt_surrogate_destroy(rt_surrogate *s, rt_stream_t stream);
+/* Parameter block in/out (device float32[60033]); set resets the Adam state. */
+rt_status rt_surrogate_set_params(rt_surrogate *s, const float *params, rt_stream_t stream);
+rt_status rt_surrogate_get_params(const rt_surrogate *s, float *params, rt_stream_t stream);
+/* Full training state (device float32[3*60033 + 1]): parameters, Adam first
+ * and second moments, then the step count; for checkpoint / resume. */
+rt_status rt_surrogate_get_state(const rt_surrogate *s, float *state, rt_stream_t stream);
+rt_status rt_surrogate_set_state(rt_surrogate *s, const float *state, rt_stream_t stream);
+/* Scene bounds (host float[3] each) used to normalise origins. */
+rt_status rt_surrogate_set_bounds(rt_surrogate *s, const float *lo, const float *hi);
+
+/* p_out[m] = network output for explicit rays (device pos[m*3], dir[m*3]). */
+rt_status rt_surrogate_forward(const rt_surrogate *s, const float *pos, const float *dir, int64_t m,
+                               float *p_out, rt_stream_t stream);
+/* Mean BCE over m explicit samples (targets y[m]) and its gradient with
+ * respect to the parameter block: grad_out[60033] and loss_out[1] (device). */
+rt_status rt_surrogate_loss_grad(const rt_surrogate *s, const float *pos, const float *dir,
+                                 const float *y, int64_t m, float *grad_out, float *loss_out,
+                                 rt_stream_t stream);
+/* `steps` Adam steps on samples of an implicit ray set over `bvh` (DIRS):
+ * each step draws cfg.batch ray ids r uniformly (Philox4x64-10, counter
+ * (i, step, 0, 0), key (seed, 1)), builds the ray as the tracer does and uses
+ * T_target[r] (the traced visibility of the whole set) as the target.  Sets
+ * the scene bounds from `bvh`.  loss_curve (device float32[steps], may be
+ * NULL) receives each step's mean loss. */
+rt_status rt_surrogate_train(rt_surrogate *s, const rt_bvh *bvh, const rt_rayspec *samples,
+                             const float *T_target, int32_t steps, uint64_t seed,
+                             float *loss_curve, rt_stream_t stream);
+/* Visibility of an implicit ray set over `bvh` (DIRS or ENV, optionally a
+ * ray_ids subset) from the surrogate: T_out[i] = p.  If band > 0, rays with
+ * |p - 0.5| < band are traced on `bvh` instead (the fallback) and T_out holds
+ * the traced value; n_fallback (device int64[1], may be NULL) receives their
+ * number.  The scene bounds used to normalise origins are the surrogate's.
+ * Errors: RT_ERR_INVALID_ARG. */
+rt_status rt_surrogate_infer(const rt_surrogate *s, const rt_bvh *bvh, const rt_rayspec *rays,
+                             float band, float *T_out, int64_t *n_fallback, rt_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Autotuning and multi-scene batches (not in the paper)                      */
+/* ------------------------------------------------------------------------ */
+
+/* Picks the traversal strategy (rt_kernel) and the work order (order_block)
+ * for a full implicit ray set (DIRS or ENV, no ray_ids) over `bvh`: each
+ * candidate traces the same contiguous block of up to 1024 tiles of 32
+ * Gaussians (all directions), timed with CUDA events; the fastest is written
+ * into opts->kernel and opts->order_block (other fields untouched).  Results
+ * are cached in-process per (device, log2 n, ray kind, K).  T_scratch must
+ * hold rt_rayspec_count(bvh, rays) floats.  Synchronises `stream`. */
+rt_status rt_trace_autotune(const rt_bvh *bvh, const rt_rayspec *rays, float *T_scratch,
+                            rt_trace_opts *opts, rt_stream_t stream);
+
+typedef struct rt_batch rt_batch;
+
+/* One scene of a batch: its tree, a full implicit ray set over it (DIRS or
+ * ENV, no ray_ids), and the output T_out[rt_rayspec_count(bvh, &rays)]. */
+typedef struct {
+    const rt_bvh *bvh;
+    rt_rayspec rays;
+    float *T_out;
+} rt_batch_job;
+
+/* Prepares one persistent launch over all jobs: a device work queue of
+ * 32-ray items ordered scene by scene, largest estimated cost first; each
+ * job's strategy and work order from rt_trace_autotune (autotune != 0) or the
+ * defaults.  The queue reset and the launch are captured once into a CUDA
+ * graph.  Jobs' trees, ray sets and outputs must stay alive until
+ * rt_batch_destroy.  At most 4096 jobs.  Synchronises `stream`. */
+rt_status rt_batch_create(const rt_batch_job *jobs, int32_t n_jobs, int32_t autotune, rt_stream_t stream,
+                          rt_batch **out);
+/* Replays the captured graph on `stream`: every job's T_out is written. */
+rt_status rt_batch_run(rt_batch *batch, rt_stream_t stream);
+/* Host outputs (may be NULL): total rays, total work items, and per job the
+ * chosen kernel and order_block (arrays of n_jobs, in job order). */
+rt_status rt_batch_info(const rt_batch *batch, int64_t *n_rays, int64_t *n_items, int32_t *kernel,
+                        int32_t *order_block);
+rt_status rt_batch_destroy(rt_batch *batch, rt_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

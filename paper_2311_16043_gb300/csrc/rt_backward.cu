@@ -148,6 +148,7 @@ __global__ void __launch_bounds__(128) k_backward(BvhDev b, RaySetDev rs, int64_
                     hit_grad(G, __float_as_int(__ldg(b.gauss + 1).w), gT, Tr, alpha, e, d_origin);
             } else if (b.n > 1) {
                 const float3 inv = safe_inv(d);
+                const float3 oi = make_float3(o.x * inv.x, o.y * inv.y, o.z * inv.z);
                 uint32_t stack[RT_STACK];
                 int sp = 0;
                 uint32_t node = 0;
@@ -156,8 +157,8 @@ __global__ void __launch_bounds__(128) k_backward(BvhDev b, RaySetDev rs, int64_
                     const float4 n1 = __ldg(b.nodes + 4 * node + 1);
                     const float4 n2 = __ldg(b.nodes + 4 * node + 2);
                     const float4 n3 = __ldg(b.nodes + 4 * node + 3);
-                    bool hl = slab(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, o, inv);
-                    bool hr = slab(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, o, inv);
+                    bool hl = slab(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, oi, inv);
+                    bool hr = slab(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, oi, inv);
                     const uint32_t ch[2] = {__float_as_uint(n3.x), __float_as_uint(n3.y)};
                     bool hit2[2] = {hl, hr};
 #pragma unroll

@@ -1,0 +1,316 @@
+// rt_batch.cu -- autotuning of the trace launch shape and batches of many
+// scenes in one persistent, graph-captured launch (neither is in the paper;
+// Sec. 4.3 re-traces the visibility of composed scenes, which is what a batch
+// of scenes serves).
+//
+// Autotuner: for a full implicit ray set it times each candidate (traversal
+// strategy: one thread per ray or one warp per 32 rays; work order: tiles per
+// direction sweep) on the same contiguous block of tiles and keeps the
+// fastest.
+//
+// Batch: the work items (32 rays each) of all jobs form one virtual queue,
+// job after job in decreasing estimated cost (rays x log2 n), consumed
+// through one device counter by a persistent grid; each warp finds its job by
+// binary search over the jobs' first item and runs that job's strategy.  The
+// counter reset and the launch are captured into a CUDA graph at creation.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "rt_trace_core.cuh"
+
+rt_status rt_trace_launch_job(const BvhDev &b, const RaySetDev &rs, const TraceJob &job, float *T_out,
+                              bool packet, rt_stream_t stream, unsigned long long *work);
+
+namespace {
+
+struct TuneKey {
+    int dev, log2n, kind, K;
+    bool operator<(const TuneKey &o) const {
+        return std::tie(dev, log2n, kind, K) < std::tie(o.dev, o.log2n, o.kind, o.K);
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int>> g_tune_cache;
+
+TraceJob full_job(const rt_bvh *bvh, int32_t K, int32_t order_block) {
+    TraceJob job;
+    memset(&job, 0, sizeof(job));
+    job.mode = MODE_FULL;
+    job.n_tiles = (bvh->n + 31) / 32;
+    int64_t B = order_block > 0 ? order_block : 64;
+    if (B > job.n_tiles) B = job.n_tiles;
+    if (B < 1) B = 1;
+    job.order_block = (int32_t)B;
+    job.n_items = job.n_tiles * K;
+    job.n_out = bvh->n * K;
+    job.tile_base = 0;
+    return job;
+}
+
+struct BatchJobDev {
+    BvhDev b;
+    RaySetDev rs;
+    TraceJob job;
+    float *T_out;
+    int32_t packet;
+    int64_t item_begin;
+};
+
+__global__ void __launch_bounds__(128) k_trace_batch(const BatchJobDev *__restrict__ jobs, int n_jobs,
+                                                     int64_t total_items, int *status,
+                                                     unsigned long long *work) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    WorkCounts wc = {0, 0, 0};
+    unsigned long long rays_done = 0;
+    TraceAux aux;
+    aux.counters = nullptr;
+    aux.hit_ids = nullptr;
+    aux.hit_count = nullptr;
+    aux.cap = 0;
+    aux.status = status;
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(work, 1ull);
+        item = __shfl_sync(FULL, item, 0);
+        if ((int64_t)item >= total_items) break;
+        int lo = 0, hi = n_jobs - 1;  // last job with item_begin <= item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (jobs[mid].item_begin <= (int64_t)item) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchJobDev &J = jobs[lo];
+        const int64_t local = (int64_t)item - J.item_begin;
+        if (J.packet) trace_item<true, false>(J.b, J.rs, J.job, J.T_out, aux, local, J.job.n_out, wc, rays_done);
+        else trace_item<false, false>(J.b, J.rs, J.job, J.T_out, aux, local, J.job.n_out, wc, rays_done);
+    }
+}
+
+int persistent_grid() {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_batch, 128, 0) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    return per_sm * rt_num_sms();
+}
+
+}  // namespace
+
+extern "C" rt_status rt_trace_autotune(const rt_bvh *bvh, const rt_rayspec *rays, float *T_scratch,
+                                       rt_trace_opts *opts, rt_stream_t stream) {
+    if (!bvh || !rays || !opts || !T_scratch) return RT_ERR_INVALID_ARG;
+    if (rays->kind == RT_RAYS_EXPLICIT || rays->ray_ids) return RT_ERR_UNSUPPORTED;
+    RaySetDev rs;
+    int64_t count = 0;
+    RT_TRY(rt_rayset_dev(bvh, rays, &rs, &count));
+    if (count == 0) return RT_OK;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int log2n = 0;
+    while ((1ll << (log2n + 1)) <= bvh->n) ++log2n;
+    const TuneKey key{dev, log2n, rays->kind, rs.K};
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            opts->kernel = it->second.first;
+            opts->order_block = it->second.second;
+            return RT_OK;
+        }
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned long long *work = nullptr;
+    RT_TRY(rt_alloc((void **)&work, 8, stream));
+    const BvhDev b = bvh_dev(bvh);
+    const int64_t ntiles = (bvh->n + 31) / 32;
+    const int64_t S = ntiles < 1024 ? ntiles : 1024;
+    const int64_t base = (ntiles - S) / 2;
+    const int blocks[] = {1, 16, 128, 1024};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int best_k = RT_KERNEL_PACKET, best_b = 64;
+    rt_status res = RT_OK;
+    for (int kernel = RT_KERNEL_RAY; kernel <= RT_KERNEL_PACKET && res == RT_OK; ++kernel) {
+        for (int bi = 0; bi < 4 && res == RT_OK; ++bi) {
+            TraceJob job = full_job(bvh, rs.K, blocks[bi]);
+            job.n_tiles = S;
+            job.tile_base = base;
+            if (job.order_block > S) job.order_block = (int32_t)S;
+            job.n_items = S * rs.K;
+            float ms = 0.f;
+            for (int rep = 0; rep < 2 && res == RT_OK; ++rep) {  // first run warms caches
+                cudaEventRecord(e0, st);
+                res = rt_trace_launch_job(b, rs, job, T_scratch, kernel == RT_KERNEL_PACKET, stream, work);
+                cudaEventRecord(e1, st);
+                if (cudaEventSynchronize(e1) != cudaSuccess) res = RT_ERR_CUDA;
+                cudaEventElapsedTime(&ms, e0, e1);
+            }
+            if (res == RT_OK && ms < best) {
+                best = ms;
+                best_k = kernel;
+                best_b = blocks[bi];
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    rt_free(work, stream);
+    if (res != RT_OK) return res;
+    opts->kernel = best_k;
+    opts->order_block = best_b;
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tune_cache[key] = {best_k, best_b};
+    return RT_OK;
+}
+
+struct rt_batch {
+    int n_jobs;
+    int64_t n_rays, n_items;
+    std::vector<int32_t> kernel, order_block;  // per job, in the caller's order
+    void *table;                                // BatchJobDev[n_jobs] + work counter
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+extern "C" rt_status rt_batch_create(const rt_batch_job *jobs, int32_t n_jobs, int32_t autotune,
+                                     rt_stream_t stream, rt_batch **out) {
+    if (!out || !jobs || n_jobs <= 0 || n_jobs > 4096) return RT_ERR_INVALID_ARG;
+    *out = nullptr;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<BatchJobDev> host(n_jobs);
+    std::vector<double> cost(n_jobs);
+    rt_batch *bt = new rt_batch();
+    bt->n_jobs = n_jobs;
+    bt->kernel.assign(n_jobs, 0);
+    bt->order_block.assign(n_jobs, 0);
+    bt->table = nullptr;
+    bt->graph = nullptr;
+    bt->exec = nullptr;
+    for (int j = 0; j < n_jobs; ++j) {
+        const rt_batch_job &J = jobs[j];
+        int64_t count = 0;
+        RaySetDev rs;
+        rt_status r = (J.bvh && (J.rays.kind == RT_RAYS_DIRS || J.rays.kind == RT_RAYS_ENV) && !J.rays.ray_ids)
+                          ? rt_rayset_dev(J.bvh, &J.rays, &rs, &count)
+                          : RT_ERR_INVALID_ARG;
+        if (r == RT_OK && count > 0 && !J.T_out) r = RT_ERR_INVALID_ARG;
+        if (r != RT_OK) {
+            delete bt;
+            return r;
+        }
+        rt_trace_opts o;
+        memset(&o, 0, sizeof(o));
+        o.kernel = J.rays.kind == RT_RAYS_DIRS ? RT_KERNEL_PACKET : RT_KERNEL_RAY;
+        o.order_block = 64;
+        if (autotune && count > 0) {
+            r = rt_trace_autotune(J.bvh, &J.rays, J.T_out, &o, stream);
+            if (r != RT_OK) {
+                delete bt;
+                return r;
+            }
+        }
+        bt->kernel[j] = o.kernel;
+        bt->order_block[j] = o.order_block;
+        BatchJobDev &H = host[j];
+        memset(&H, 0, sizeof(H));
+        H.b = bvh_dev(J.bvh);
+        H.rs = rs;
+        H.job = full_job(J.bvh, rs.K, o.order_block);
+        H.T_out = J.T_out;
+        H.packet = o.kernel == RT_KERNEL_PACKET;
+        cost[j] = (double)count * log2((double)(J.bvh->n > 1 ? J.bvh->n : 2));
+    }
+    // largest estimated cost first
+    std::vector<int> order(n_jobs);
+    for (int j = 0; j < n_jobs; ++j) order[j] = j;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    std::vector<BatchJobDev> queue(n_jobs);
+    int64_t items = 0, rays = 0;
+    for (int q = 0; q < n_jobs; ++q) {
+        queue[q] = host[order[q]];
+        queue[q].item_begin = items;
+        items += queue[q].job.n_items;
+        rays += queue[q].job.n_out;
+    }
+    bt->n_items = items;
+    bt->n_rays = rays;
+    const size_t tbytes = ((sizeof(BatchJobDev) * n_jobs + 255) & ~(size_t)255);
+    rt_status r = rt_alloc(&bt->table, tbytes + 256, stream);
+    if (r != RT_OK) {
+        delete bt;
+        return r;
+    }
+    BatchJobDev *dtab = (BatchJobDev *)bt->table;
+    unsigned long long *work = (unsigned long long *)((char *)bt->table + tbytes);
+    if (cudaMemcpyAsync(dtab, queue.data(), sizeof(BatchJobDev) * n_jobs, cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        rt_free(bt->table, stream);
+        delete bt;
+        return RT_ERR_CUDA;
+    }
+    // capture: reset the queue counter, one persistent launch
+    cudaStream_t cap;
+    if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
+        rt_free(bt->table, stream);
+        delete bt;
+        return RT_ERR_CUDA;
+    }
+    const int grid = persistent_grid();
+    int *status = rt_status_ptr();
+    bool ok = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        cudaMemsetAsync(work, 0, 8, cap);
+        k_trace_batch<<<grid, 128, 0, cap>>>(dtab, n_jobs, items, status, work);
+        ok = cudaStreamEndCapture(cap, &bt->graph) == cudaSuccess;
+    }
+    if (ok) ok = cudaGraphInstantiate(&bt->exec, bt->graph, 0) == cudaSuccess;
+    cudaStreamDestroy(cap);
+    if (!ok) {
+        cudaGetLastError();
+        if (bt->exec) cudaGraphExecDestroy(bt->exec);
+        if (bt->graph) cudaGraphDestroy(bt->graph);
+        rt_free(bt->table, stream);
+        delete bt;
+        return RT_ERR_CUDA;
+    }
+    *out = bt;
+    return RT_OK;
+}
+
+extern "C" rt_status rt_batch_run(rt_batch *bt, rt_stream_t stream) {
+    if (!bt) return RT_ERR_INVALID_ARG;
+    return cudaGraphLaunch(bt->exec, (cudaStream_t)stream) == cudaSuccess ? RT_OK : RT_ERR_CUDA;
+}
+
+extern "C" rt_status rt_batch_info(const rt_batch *bt, int64_t *n_rays, int64_t *n_items, int32_t *kernel,
+                                   int32_t *order_block) {
+    if (!bt) return RT_ERR_INVALID_ARG;
+    if (n_rays) *n_rays = bt->n_rays;
+    if (n_items) *n_items = bt->n_items;
+    for (int j = 0; j < bt->n_jobs; ++j) {
+        if (kernel) kernel[j] = bt->kernel[j];
+        if (order_block) order_block[j] = bt->order_block[j];
+    }
+    return RT_OK;
+}
+
+extern "C" rt_status rt_batch_destroy(rt_batch *bt, rt_stream_t stream) {
+    if (!bt) return RT_ERR_INVALID_ARG;
+    cudaStreamSynchronize((cudaStream_t)stream);
+    if (bt->exec) cudaGraphExecDestroy(bt->exec);
+    if (bt->graph) cudaGraphDestroy(bt->graph);
+    rt_free(bt->table, stream);
+    delete bt;
+    return RT_OK;
+}

@@ -204,7 +204,15 @@ __global__ void k_perm(const uint32_t *__restrict__ codes, const int32_t *__rest
 __global__ void k_prep(const float *__restrict__ mean, const float *__restrict__ scale,
                        const float *__restrict__ quat, const float *__restrict__ opacity,
                        const int32_t *__restrict__ perm, int64_t n, rt_params prm,
-                       float4 *gauss, float *leafbox) {
+                       const uint32_t *bounds_u, float4 *gauss, float *leafbox) {
+    // absolute box margin: 1e-6 of the scene's coordinate scale
+    float L = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float lo = ord2f(bounds_u[c]), hi = ord2f(bounds_u[3 + c]);
+        L = fmaxf(L, fmaxf(fabsf(lo), fmaxf(fabsf(hi), hi - lo)));
+    }
+    const float margin = 1e-6f * L;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
         int32_t i = perm[p];
@@ -246,7 +254,7 @@ __global__ void k_prep(const float *__restrict__ mean, const float *__restrict__
             // exact support and the slab test never misses an accepted peak
             float a0 = R[c][0] * s[0], a1 = R[c][1] * s[1], a2 = R[c][2] * s[2];
             float h = K * sqrtf(a0 * a0 + a1 * a1 + a2 * a2);
-            h = h * (1.0f + 1e-4f) + 4.0f * 1.1920929e-7f * fabsf(mu[c]) + 1e-30f;
+            h = h * (1.0f + 1e-4f) + 4.0f * 1.1920929e-7f * fabsf(mu[c]) + margin + 1e-30f;
             bx[c] = empty ? INFINITY : __fsub_rd(mu[c], h);
             bx[3 + c] = empty ? -INFINITY : __fadd_ru(mu[c], h);
         }
@@ -464,7 +472,7 @@ extern "C" rt_status rt_build_bvh(const float *mean, const float *scale, const f
             int32_t *tv = v0; v0 = v1; v1 = tv;
         }
         k_perm<<<grid_for(n, 256), 256, 0, st>>>(k0, v0, n, b->perm, b->rank, b->keys);
-        k_prep<<<grid_for(n, 128), 128, 0, st>>>(mean, scale, quat, opacity, b->perm, n, prm,
+        k_prep<<<grid_for(n, 128), 128, 0, st>>>(mean, scale, quat, opacity, b->perm, n, prm, bounds_u,
                                                  b->gauss, leafbox);
         if (n == 1) {
             int32_t m1 = -1;

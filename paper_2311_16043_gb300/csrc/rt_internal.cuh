@@ -178,3 +178,10 @@ rt_status rt_rayset_dev(const rt_bvh *bvh, const rt_rayspec *rays, RaySetDev *ou
 // caller-provided device counter (8 bytes); NULL allocates one per call.
 rt_status rt_trace_launch(const rt_bvh *bvh, const rt_rayspec *rays, float *T_out,
                           const rt_trace_opts *opts, rt_stream_t stream, unsigned long long *work);
+
+// Host: trace the rays listed in ray_ids[0 .. *count) of an implicit set
+// (count is a device value, at most max_count) writing T_out[out_index[i]].
+// `work` is a device counter (8 bytes) owned by the caller.
+rt_status rt_trace_launch_list(const rt_bvh *bvh, const rt_rayspec *rays, const int64_t *ray_ids,
+                               const int64_t *out_index, const unsigned long long *count, int64_t max_count,
+                               float *T_out, rt_stream_t stream, unsigned long long *work);

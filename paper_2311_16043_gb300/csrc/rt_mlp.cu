@@ -1,0 +1,948 @@
+// rt_mlp.cu -- learned visibility surrogate on the 5th-generation tensor
+// cores (not in the paper; the paper precomputes visibility by tracing).
+//
+// Network: frequency encoding of (origin, direction) -> 80 inputs ->
+// 4 x 128 ReLU -> 1 sigmoid.  bf16 weights and activations, f32 accumulation
+// in TMEM.  One CTA of 128 threads per SM; thread r owns sample row r of a
+// 128-sample tile (= TMEM lane r of the accumulator).
+//
+// Inference (k_mlp_infer): the four weight images stay in shared memory; per
+// tile the encoding is written to shared memory, each layer is one chain of
+// tcgen05.mma (M=128, N=128, K=80/128) into TMEM, and the epilogue (bias,
+// ReLU, bf16) writes the next layer's operand back to shared memory; the last
+// epilogue does the 128->1 layer and the sigmoid on the CUDA cores.  Rays
+// whose prediction is within `band` of 0.5 are appended (warp-aggregated
+// atomics) to a fallback list that the tracer then resolves.
+//
+// Training (k_mlp_train): per tile, forward (activations kept in shared
+// memory), then backward with the same operands read K-major or MN-major:
+//   dW_l += dz_l^T x_{l-1}   (M = units, N = inputs, K = samples; TMEM-resident
+//                             across the CTA's tiles for l = 2..4)
+//   dX_{l-1} = dz_l W_l      (M = samples, N = inputs, K = units)
+// Bias gradients are column sums of dz (warp transpose-reductions).  Each CTA
+// writes one partial gradient; k_mlp_reduce_adam sums the partials in a fixed
+// order (deterministic), applies Adam to the f32 master weights and re-packs
+// the bf16 weight images.
+#include <cuda_bf16.h>
+#include <math.h>
+#include <string.h>
+
+#include "rt_tc.cuh"
+#include "rt_trace_core.cuh"
+
+namespace {
+
+constexpr int H = 128;
+constexpr int IN = 80;
+constexpr int OFF_W1 = 0, OFF_B1 = 10240, OFF_W2 = 10368, OFF_B2 = 26752, OFF_W3 = 26880, OFF_B3 = 43264,
+              OFF_W4 = 43392, OFF_B4 = 59776, OFF_W5 = 59904, OFF_B5 = 60032, NPARAM = 60033;
+constexpr int IMG_W1 = 0, IMG_W2 = 20480, IMG_W3 = 53248, IMG_W4 = 86016, IMG_BYTES = 118784;
+constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
+constexpr unsigned FULL = 0xffffffffu;
+
+__host__ __device__ __forceinline__ uint32_t img_off(int r, int c, int kdim) {
+    return (uint32_t)((r >> 3) * (kdim / 8 * 128) + (c >> 3) * 128 + (r & 7) * 16 + (c & 7) * 2);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+__device__ __forceinline__ float bf16_round(float a) { return __bfloat162float(__float2bfloat16_rn(a)); }
+__device__ __forceinline__ float bf16_lo(uint32_t u) { return __uint_as_float(u << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t u) { return __uint_as_float(u & 0xffff0000u); }
+
+// Frequency encoding of one ray into 80 floats (rounded to bf16 at store).
+// The origin is normalised in float64, x = 2 (p - lo)/(hi - lo) - 1 (IEEE
+// operations, so the same value as a float64 host computation), and the
+// argument 2^k x of sin/cos(pi 2^k x) is reduced modulo 2 in float64 (both
+// steps exact) before the float32 sincospif: the feature is then within a
+// few 1e-7 of its exact value, so its bf16 rounding rarely differs from that
+// of an exact evaluation.
+__device__ __forceinline__ void sincospi_k(double x, int k, float &s, float &c) {
+    const double t = ldexp(x, k);             // exact
+    const double r = t - 2.0 * rint(0.5 * t);  // exact, in [-1, 1]
+    sincospif((float)r, &s, &c);
+}
+
+__device__ __forceinline__ void encode(float3 p, float3 d, const double *lo, const double *ext, float (&f)[IN]) {
+    double x[6];
+    x[0] = ext[0] > 0.0 ? 2.0 * ((double)p.x - lo[0]) / ext[0] - 1.0 : 0.0;
+    x[1] = ext[1] > 0.0 ? 2.0 * ((double)p.y - lo[1]) / ext[1] - 1.0 : 0.0;
+    x[2] = ext[2] > 0.0 ? 2.0 * ((double)p.z - lo[2]) / ext[2] - 1.0 : 0.0;
+    x[3] = d.x;
+    x[4] = d.y;
+    x[5] = d.z;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        f[13 * c] = (float)x[c];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            float s, co;
+            sincospi_k(x[c], k, s, co);
+            f[13 * c + 1 + 2 * k] = s;
+            f[13 * c + 2 + 2 * k] = co;
+        }
+    }
+    f[78] = 0.0f;
+    f[79] = 0.0f;
+}
+
+__device__ __forceinline__ void store_row_x0(uint8_t *x0, int r, const float (&f)[IN]) {
+#pragma unroll
+    for (int q = 0; q < IN / 8; ++q) {
+        uint4 v;
+        v.x = pack_bf16(f[8 * q + 0], f[8 * q + 1]);
+        v.y = pack_bf16(f[8 * q + 2], f[8 * q + 3]);
+        v.z = pack_bf16(f[8 * q + 4], f[8 * q + 5]);
+        v.w = pack_bf16(f[8 * q + 6], f[8 * q + 7]);
+        *reinterpret_cast<uint4 *>(x0 + img_off(r, 8 * q, IN)) = v;
+    }
+}
+
+// 32 values of row r, columns c0..c0+31, to a K-major bf16 image (kdim 128).
+__device__ __forceinline__ void store_chunk(uint8_t *img, int r, int c0, const float (&v)[32]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        uint4 u;
+        u.x = pack_bf16(v[8 * q + 0], v[8 * q + 1]);
+        u.y = pack_bf16(v[8 * q + 2], v[8 * q + 3]);
+        u.z = pack_bf16(v[8 * q + 4], v[8 * q + 5]);
+        u.w = pack_bf16(v[8 * q + 6], v[8 * q + 7]);
+        *reinterpret_cast<uint4 *>(img + img_off(r, c0 + 8 * q, H)) = u;
+    }
+}
+
+__device__ __forceinline__ void load_chunk(const uint8_t *img, int r, int c0, float (&v)[32]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        uint4 u = *reinterpret_cast<const uint4 *>(img + img_off(r, c0 + 8 * q, H));
+        v[8 * q + 0] = bf16_lo(u.x); v[8 * q + 1] = bf16_hi(u.x);
+        v[8 * q + 2] = bf16_lo(u.y); v[8 * q + 3] = bf16_hi(u.y);
+        v[8 * q + 4] = bf16_lo(u.z); v[8 * q + 5] = bf16_hi(u.z);
+        v[8 * q + 6] = bf16_lo(u.w); v[8 * q + 7] = bf16_hi(u.w);
+    }
+}
+
+// Warp transpose-reduction: afterwards lane l holds sum over the warp's
+// lanes of v[l] (31 shuffles for 32 columns).  Destroys v.
+template <int S>
+__device__ __forceinline__ void tr_step(float (&v)[32], int lane) {
+    const bool upper = (lane & S) != 0;
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+        float keep = upper ? v[i + S] : v[i];
+        float send = upper ? v[i] : v[i + S];
+        v[i] = keep + __shfl_xor_sync(FULL, send, S);
+    }
+}
+__device__ __forceinline__ float transpose_reduce32(float (&v)[32], int lane) {
+    tr_step<16>(v, lane);
+    tr_step<8>(v, lane);
+    tr_step<4>(v, lane);
+    tr_step<2>(v, lane);
+    tr_step<1>(v, lane);
+    return v[0];
+}
+
+// Chain of MMAs D (+)= A * B^T over K in steps of 16.
+__device__ __forceinline__ void issue_mma(uint32_t tmem_d, uint32_t a, uint32_t a_lbo, uint32_t a_sbo,
+                                          uint32_t a_kstep, uint32_t b, uint32_t b_lbo, uint32_t b_sbo,
+                                          uint32_t b_kstep, uint32_t idesc, int K, bool acc_first) {
+    for (int kk = 0; kk < K / 16; ++kk) {
+        tc_mma(tmem_d, tc_smem_desc(a + kk * a_kstep, a_lbo, a_sbo), tc_smem_desc(b + kk * b_kstep, b_lbo, b_sbo),
+               idesc, (kk > 0 || acc_first) ? 1u : 0u);
+    }
+}
+
+// Sample sources
+struct SampleSrc {
+    int mode;  // 0 explicit pos/dir(/y); 1 implicit set (rays); 2 implicit, Philox-drawn training ids
+    const float *pos, *dir, *y;
+    BvhDev b;
+    RaySetDev rs;
+    const float *T_target;
+    uint64_t seed;
+    int64_t step;
+    int64_t R;  // rays in the implicit set
+};
+
+__device__ __forceinline__ bool get_sample(const SampleSrc &S, int64_t i, int64_t m, float3 &p, float3 &d,
+                                           float &y, int64_t &rid) {
+    if (i >= m) return false;
+    if (S.mode == 0) {
+        p = make_float3(S.pos[3 * i], S.pos[3 * i + 1], S.pos[3 * i + 2]);
+        d = make_float3(S.dir[3 * i], S.dir[3 * i + 1], S.dir[3 * i + 2]);
+        y = S.y ? S.y[i] : 0.0f;
+        rid = i;
+        return true;
+    }
+    if (S.mode == 1) {
+        rid = S.rs.ray_ids ? S.rs.ray_ids[i] : i;
+    } else {
+        uint64_t c[4] = {(uint64_t)i, (uint64_t)S.step, 0ull, 0ull};
+        philox4x64_10(c, S.seed, 1ull);
+        rid = (int64_t)(c[0] % (uint64_t)S.R);
+    }
+    if (rid < 0 || rid >= S.R) return false;  // reported by the caller's status check
+    const int64_t g = rid / S.rs.K;
+    const int32_t k = (int32_t)(rid - g * S.rs.K);
+    const int32_t ps = S.b.rank[g];
+    implicit_ray(S.rs, rid, k, __ldg(S.b.gauss + 4 * (int64_t)ps), p, d);
+    y = S.T_target ? S.T_target[rid] : 0.0f;
+    return true;
+}
+
+struct MlpDev {
+    const float *params;  // f32 master
+    const uint8_t *img;   // bf16 images
+    double lo[3], ext[3]; // origin normalisation: x = 2 (p - lo) / ext - 1
+};
+
+// ---------------------------------------------------------------------------
+// Inference
+// ---------------------------------------------------------------------------
+constexpr int INF_SMEM_ACT = IMG_BYTES;                   // 32768
+constexpr int INF_SMEM_B = INF_SMEM_ACT + 32768;          // b1..b4, w5: 5*128 floats
+constexpr int INF_SMEM_BAR = INF_SMEM_B + 5 * 128 * 4;    // mbarrier + tmem slot
+constexpr int INF_SMEM_TOTAL = INF_SMEM_BAR + 64;
+
+__global__ void __launch_bounds__(128, 1) k_mlp_infer(MlpDev net, SampleSrc S, int64_t m, float *out, float band,
+                                                      int64_t *fb_rid, int64_t *fb_pos,
+                                                      unsigned long long *fb_count, int *status) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t *wimg = smem;
+    uint8_t *act = smem + INF_SMEM_ACT;
+    float *bias = reinterpret_cast<float *>(smem + INF_SMEM_B);  // [4][128], then w5[128]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + INF_SMEM_BAR);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + INF_SMEM_BAR + 8);
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+
+    for (int i = t; i < IMG_BYTES / 16; i += 128)
+        reinterpret_cast<uint4 *>(wimg)[i] = __ldg(reinterpret_cast<const uint4 *>(net.img) + i);
+    for (int i = t; i < 128; i += 128) {
+        bias[i] = net.params[OFF_B1 + i];
+        bias[128 + i] = net.params[OFF_B2 + i];
+        bias[256 + i] = net.params[OFF_B3 + i];
+        bias[384 + i] = net.params[OFF_B4 + i];
+        bias[512 + i] = net.params[OFF_W5 + i];
+    }
+    const float b5 = net.params[OFF_B5];
+    if (t == 0) mbar_init(bar, 1);
+    if (warp == 0) tmem_alloc(tslot, 128);
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t a_addr = smem_u32(act);
+    const uint32_t w_addr = smem_u32(wimg);
+    const uint32_t idesc = tc_idesc_bf16(128, 128, false, false);
+    uint32_t phase = 0;
+    bool ok = true;
+    const int64_t ntiles = (m + 127) / 128;
+
+    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const int64_t i = tile * 128 + t;
+        float3 p = make_float3(0.f, 0.f, 0.f), d = make_float3(0.f, 0.f, 1.f);
+        float y;
+        int64_t rid = -1;
+        const bool valid = get_sample(S, i, m, p, d, y, rid);
+        {
+            float f[IN];
+            if (valid) encode(p, d, net.lo, net.ext, f);
+            else
+#pragma unroll
+                for (int k = 0; k < IN; ++k) f[k] = 0.0f;
+            store_row_x0(act, t, f);
+        }
+        float z5 = b5;
+        for (int l = 0; l < 4; ++l) {
+            fence_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            if (t == 0) {
+                tc_fence_after();
+                const int K = l == 0 ? IN : H;
+                const uint32_t sbo = (uint32_t)(K / 8 * 128);
+                const uint32_t wb = w_addr + (l == 0 ? IMG_W1 : l == 1 ? IMG_W2 : l == 2 ? IMG_W3 : IMG_W4);
+                issue_mma(tmem, a_addr, 128, sbo, 256, wb, 128, sbo, 256, idesc, K, false);
+                tc_commit(bar);
+            }
+            if (!mbar_wait(bar, phase, WAIT_CYCLES)) {
+                rt_set_error(status, RT_ERR_TIMEOUT);
+                ok = false;
+            }
+            phase ^= 1u;
+            tc_fence_after();
+            if (!ok) break;
+            const float *bl = bias + 128 * l;
+#pragma unroll 1
+            for (int cc = 0; cc < 4; ++cc) {
+                float v[32];
+                tmem_ld32(lane_addr + 32 * cc, v);
+#pragma unroll
+                for (int k = 0; k < 32; ++k) v[k] = fmaxf(v[k] + bl[32 * cc + k], 0.0f);
+                if (l < 3) {
+                    store_chunk(act, t, 32 * cc, v);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) z5 = fmaf(bias[512 + 32 * cc + k], bf16_round(v[k]), z5);
+                }
+            }
+        }
+        if (!ok) break;
+        if (valid) {
+            const float pr = 1.0f / (1.0f + expf(-z5));
+            out[i] = pr;
+            const bool fb = band > 0.0f && fabsf(pr - 0.5f) < band;
+            const uint32_t mask = __ballot_sync(__activemask(), fb);
+            if (fb) {
+                const int leader = __ffs(mask) - 1;
+                unsigned long long base = 0;
+                if (lane == leader) base = atomicAdd(fb_count, (unsigned long long)__popc(mask));
+                base = __shfl_sync(mask, base, leader);
+                const unsigned long long slot = base + __popc(mask & ((1u << lane) - 1u));
+                fb_rid[slot] = rid;
+                fb_pos[slot] = i;
+            }
+        }
+        tc_fence_before();
+        __syncthreads();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, 128);
+}
+
+// ---------------------------------------------------------------------------
+// Training: forward + backward of a minibatch, per-CTA partial gradients
+// ---------------------------------------------------------------------------
+constexpr int TR_WBUF = 0;                       // 32768: one weight image
+constexpr int TR_X0 = TR_WBUF + 32768;           // 20480
+constexpr int TR_H1 = TR_X0 + 20480;             // 32768 each
+constexpr int TR_H2 = TR_H1 + 32768;
+constexpr int TR_H3 = TR_H2 + 32768;
+constexpr int TR_DZ = TR_H3 + 32768;
+constexpr int TR_F = TR_DZ + 32768;              // floats: b[4][128], w5[128], db[4][128], dw5[128], misc
+constexpr int TR_BAR = TR_F + (4 * 128 + 128 + 4 * 128 + 128 + 8) * 4;
+constexpr int TR_SMEM_TOTAL = TR_BAR + 64;
+
+__device__ __forceinline__ void copy_img(uint8_t *dst, const uint8_t *src, int bytes, int t) {
+    for (int i = t; i < bytes / 16; i += 128)
+        reinterpret_cast<uint4 *>(dst)[i] = __ldg(reinterpret_cast<const uint4 *>(src) + i);
+}
+
+__global__ void __launch_bounds__(128, 1) k_mlp_train(MlpDev net, SampleSrc S, int64_t m, float inv_batch,
+                                                      float *partial, int *status) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t *wbuf = smem + TR_WBUF;
+    uint8_t *x0 = smem + TR_X0;
+    uint8_t *hb[3] = {smem + TR_H1, smem + TR_H2, smem + TR_H3};
+    uint8_t *dz = smem + TR_DZ;
+    float *fb = reinterpret_cast<float *>(smem + TR_F);
+    float *bias = fb;             // [4][128]
+    float *w5 = fb + 512;         // [128]
+    float *dbias = fb + 640;      // [4][128]
+    float *dw5 = fb + 1152;       // [128]
+    float *misc = fb + 1280;      // [0] db5, [1] loss
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + TR_BAR);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + TR_BAR + 8);
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    float *part = partial + (int64_t)blockIdx.x * (NPARAM + 1);
+
+    for (int i = t; i < 128; i += 128) {
+        bias[i] = net.params[OFF_B1 + i];
+        bias[128 + i] = net.params[OFF_B2 + i];
+        bias[256 + i] = net.params[OFF_B3 + i];
+        bias[384 + i] = net.params[OFF_B4 + i];
+        w5[i] = net.params[OFF_W5 + i];
+        dw5[i] = 0.0f;
+#pragma unroll
+        for (int l = 0; l < 4; ++l) dbias[128 * l + i] = 0.0f;
+    }
+    if (t < 8) misc[t] = 0.0f;
+    for (int i = t; i < H * IN; i += 128) part[OFF_W1 + i] = 0.0f;
+    const float b5 = net.params[OFF_B5];
+    if (t == 0) mbar_init(bar, 1);
+    if (warp == 0) tmem_alloc(tslot, 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t tm_work = tmem, tm_dw[3] = {tmem + 128, tmem + 256, tmem + 384};  // dW2, dW3, dW4
+    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+    const uint32_t s_wbuf = smem_u32(wbuf), s_x0 = smem_u32(x0), s_dz = smem_u32(dz);
+    const uint32_t s_h[3] = {smem_u32(hb[0]), smem_u32(hb[1]), smem_u32(hb[2])};
+    const uint32_t id_fwd = tc_idesc_bf16(128, 128, false, false);
+    const uint32_t id_dw = tc_idesc_bf16(128, 128, true, true);
+    const uint32_t id_dw1 = tc_idesc_bf16(128, IN, true, true);
+    const uint32_t id_dx = tc_idesc_bf16(128, 128, false, true);
+    const int img_off_l[4] = {IMG_W1, IMG_W2, IMG_W3, IMG_W4};
+    uint32_t phase = 0;
+    bool ok = true;
+
+    const int64_t ntiles = (m + 127) / 128;
+    const int64_t per = (ntiles + gridDim.x - 1) / gridDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * per;
+    const int64_t t1 = t0 + per < ntiles ? t0 + per : ntiles;
+
+    auto sync_mma = [&]() {
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+    };
+    auto wait_mma = [&]() {
+        if (!mbar_wait(bar, phase, WAIT_CYCLES)) {
+            rt_set_error(status, RT_ERR_TIMEOUT);
+            ok = false;
+        }
+        phase ^= 1u;
+        tc_fence_after();
+    };
+
+    for (int64_t tile = t0; tile < t1 && ok; ++tile) {
+        const bool first = tile == t0;
+        const int64_t i = tile * 128 + t;
+        float3 p = make_float3(0.f, 0.f, 0.f), d = make_float3(0.f, 0.f, 1.f);
+        float y = 0.0f;
+        int64_t rid;
+        const bool valid = get_sample(S, i, m, p, d, y, rid);
+        {
+            float f[IN];
+            if (valid) encode(p, d, net.lo, net.ext, f);
+            else
+#pragma unroll
+                for (int k = 0; k < IN; ++k) f[k] = 0.0f;
+            store_row_x0(x0, t, f);
+        }
+        // ---- forward ----
+        float z5 = b5;
+        for (int l = 0; l < 4; ++l) {
+            copy_img(wbuf, net.img + img_off_l[l], l == 0 ? 20480 : 32768, t);
+            sync_mma();
+            if (t == 0) {
+                tc_fence_after();
+                const int K = l == 0 ? IN : H;
+                const uint32_t sbo = (uint32_t)(K / 8 * 128);
+                const uint32_t a = l == 0 ? s_x0 : s_h[l - 1];
+                issue_mma(tm_work, a, 128, sbo, 256, s_wbuf, 128, sbo, 256, id_fwd, K, false);
+                tc_commit(bar);
+            }
+            wait_mma();
+            if (!ok) break;
+            const float *bl = bias + 128 * l;
+            if (l < 3) {
+#pragma unroll 1
+                for (int cc = 0; cc < 4; ++cc) {
+                    float v[32];
+                    tmem_ld32(tm_work + lane_off + 32 * cc, v);
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) v[k] = fmaxf(v[k] + bl[32 * cc + k], 0.0f);
+                    store_chunk(hb[l], t, 32 * cc, v);
+                }
+            } else {
+#pragma unroll 1
+                for (int cc = 0; cc < 4; ++cc) {
+                    float v[32];
+                    tmem_ld32(tm_work + lane_off + 32 * cc, v);
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) z5 = fmaf(w5[32 * cc + k], bf16_round(fmaxf(v[k] + bl[32 * cc + k], 0.0f)), z5);
+                }
+            }
+        }
+        if (!ok) break;
+        // ---- loss and output layer ----
+        const float pr = 1.0f / (1.0f + expf(-z5));
+        const float dz5 = valid ? (pr - y) * inv_batch : 0.0f;
+        {
+            float lv = valid ? (y * (fmaxf(-z5, 0.0f) + log1pf(expf(-fabsf(z5)))) +
+                                (1.0f - y) * (fmaxf(z5, 0.0f) + log1pf(expf(-fabsf(z5))))) * inv_batch
+                             : 0.0f;
+            float db5 = dz5;
+            for (int off = 16; off > 0; off >>= 1) {
+                lv += __shfl_xor_sync(FULL, lv, off);
+                db5 += __shfl_xor_sync(FULL, db5, off);
+            }
+            if (lane == 0) {
+                atomicAdd(misc + 1, lv);
+                atomicAdd(misc + 0, db5);
+            }
+        }
+        // dz4 = bf16(dz5 * w5 * [h4 > 0]); dw5 += dz5 * h4; db4 += dz4
+#pragma unroll 1
+        for (int cc = 0; cc < 4; ++cc) {
+            float v[32], g[32], h4[32];
+            tmem_ld32(tm_work + lane_off + 32 * cc, v);
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+                h4[k] = bf16_round(fmaxf(v[k] + bias[384 + 32 * cc + k], 0.0f));
+                g[k] = h4[k] > 0.0f ? bf16_round(dz5 * w5[32 * cc + k]) : 0.0f;
+                h4[k] *= dz5;
+            }
+            store_chunk(dz, t, 32 * cc, g);
+            atomicAdd(dw5 + 32 * cc + lane, transpose_reduce32(h4, lane));
+            atomicAdd(dbias + 384 + 32 * cc + lane, transpose_reduce32(g, lane));
+        }
+        // ---- backward through layers 4, 3, 2 ----
+        for (int l = 3; l >= 1; --l) {
+            // W_{l+1} is in wbuf (l == 3: still loaded from the forward)
+            if (l < 3) copy_img(wbuf, net.img + img_off_l[l], 32768, t);
+            sync_mma();
+            if (t == 0) {
+                tc_fence_after();
+                const uint32_t s_dzl = l == 3 ? s_dz : s_h[l];  // dz_{l+1} lives in h_{l+1}'s buffer below layer 4
+                // dW_{l+1} += dz^T x_l : A = dz (MN-major), B = h_l (MN-major), K = samples
+                issue_mma(tm_dw[l - 1], s_dzl, 2048, 128, 4096, s_h[l - 1], 2048, 128, 4096, id_dw, 128,
+                          !first);
+                // dX_l = dz W_{l+1} : A = dz (K-major), B = W (MN-major), K = units
+                issue_mma(tm_work, s_dzl, 128, 2048, 256, s_wbuf, 2048, 128, 4096, id_dx, 128, false);
+                tc_commit(bar);
+            }
+            wait_mma();
+            if (!ok) break;
+            // dz_l = bf16(dX_l * [h_l > 0]) written over h_l; db_l += dz_l
+            uint8_t *hl = hb[l - 1];
+#pragma unroll 1
+            for (int cc = 0; cc < 4; ++cc) {
+                float v[32], h[32];
+                tmem_ld32(tm_work + lane_off + 32 * cc, v);
+                load_chunk(hl, t, 32 * cc, h);
+#pragma unroll
+                for (int k = 0; k < 32; ++k) v[k] = h[k] > 0.0f ? bf16_round(v[k]) : 0.0f;
+                store_chunk(hl, t, 32 * cc, v);
+                atomicAdd(dbias + 128 * (l - 1) + 32 * cc + lane, transpose_reduce32(v, lane));
+            }
+        }
+        if (!ok) break;
+        // ---- dW1 = dz1^T x0 (per tile, added to this CTA's partial) ----
+        sync_mma();
+        if (t == 0) {
+            tc_fence_after();
+            issue_mma(tm_work, s_h[0], 2048, 128, 4096, s_x0, 1280, 128, 2560, id_dw1, 128, false);
+            tc_commit(bar);
+        }
+        wait_mma();
+        if (!ok) break;
+        {
+            float v[32];
+            float *row = part + OFF_W1 + (int64_t)t * IN;
+#pragma unroll 1
+            for (int cc = 0; cc < 2; ++cc) {
+                tmem_ld32(tm_work + lane_off + 32 * cc, v);
+#pragma unroll
+                for (int k = 0; k < 32; ++k) row[32 * cc + k] += v[k];
+            }
+            float w[16];
+            tmem_ld16(tm_work + lane_off + 64, w);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) row[64 + k] += w[k];
+        }
+        tc_fence_before();
+        __syncthreads();
+    }
+    // ---- flush this CTA's partial gradient ----
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const bool any = t1 > t0 && ok;
+    const int offW[3] = {OFF_W2, OFF_W3, OFF_W4};
+#pragma unroll 1
+    for (int l = 0; l < 3; ++l) {
+        float *row = part + offW[l] + (int64_t)t * H;
+#pragma unroll 1
+        for (int cc = 0; cc < 4; ++cc) {
+            float v[32];
+            tmem_ld32(tm_dw[l] + lane_off + 32 * cc, v);
+#pragma unroll
+            for (int k = 0; k < 32; ++k) row[32 * cc + k] = any ? v[k] : 0.0f;
+        }
+    }
+    __syncthreads();
+    part[OFF_B1 + t] = dbias[t];
+    part[OFF_B2 + t] = dbias[128 + t];
+    part[OFF_B3 + t] = dbias[256 + t];
+    part[OFF_B4 + t] = dbias[384 + t];
+    part[OFF_W5 + t] = dw5[t];
+    if (t == 0) {
+        part[OFF_B5] = misc[0];
+        part[NPARAM] = misc[1];
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, 512);
+}
+
+// Sum the CTA partials in a fixed order; either write the gradient or take
+// an Adam step on the f32 master weights and re-pack the bf16 images.
+__global__ void k_mlp_reduce_adam(const float *partial, int nparts, float *grad_out, float *loss_out,
+                                  float *params, float *mo, float *vo, uint8_t *img, float lr, float b1,
+                                  float b2, float eps, float c1, float c2, int adam) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q <= NPARAM; q += gridDim.x * blockDim.x) {
+        float g = 0.0f;
+        for (int c = 0; c < nparts; ++c) g += partial[(int64_t)c * (NPARAM + 1) + q];
+        if (q == NPARAM) {
+            if (loss_out) *loss_out = g;
+            continue;
+        }
+        if (!adam) {
+            grad_out[q] = g;
+            continue;
+        }
+        const float m = b1 * mo[q] + (1.0f - b1) * g;
+        const float v = b2 * vo[q] + (1.0f - b2) * g * g;
+        mo[q] = m;
+        vo[q] = v;
+        const float w = params[q] - lr * (m / c1) / (sqrtf(v / c2) + eps);
+        params[q] = w;
+        // re-pack the bf16 image of weight matrices
+        int base = -1, kin = 0, ioff = 0;
+        if (q < OFF_B1) { base = OFF_W1; kin = IN; ioff = IMG_W1; }
+        else if (q >= OFF_W2 && q < OFF_B2) { base = OFF_W2; kin = H; ioff = IMG_W2; }
+        else if (q >= OFF_W3 && q < OFF_B3) { base = OFF_W3; kin = H; ioff = IMG_W3; }
+        else if (q >= OFF_W4 && q < OFF_B4) { base = OFF_W4; kin = H; ioff = IMG_W4; }
+        if (base >= 0) {
+            const int e = q - base, r = e / kin, c = e % kin;
+            *reinterpret_cast<__nv_bfloat16 *>(img + ioff + img_off(r, c, kin)) = __float2bfloat16_rn(w);
+        }
+    }
+}
+
+__global__ void k_mlp_pack(const float *params, uint8_t *img) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < OFF_B4; q += gridDim.x * blockDim.x) {
+        int base = -1, kin = 0, ioff = 0;
+        if (q < OFF_B1) { base = OFF_W1; kin = IN; ioff = IMG_W1; }
+        else if (q >= OFF_W2 && q < OFF_B2) { base = OFF_W2; kin = H; ioff = IMG_W2; }
+        else if (q >= OFF_W3 && q < OFF_B3) { base = OFF_W3; kin = H; ioff = IMG_W3; }
+        else if (q >= OFF_W4 && q < OFF_B4) { base = OFF_W4; kin = H; ioff = IMG_W4; }
+        if (base >= 0) {
+            const int e = q - base, r = e / kin, c = e % kin;
+            *reinterpret_cast<__nv_bfloat16 *>(img + ioff + img_off(r, c, kin)) = __float2bfloat16_rn(params[q]);
+        }
+    }
+}
+
+// He-uniform weights from Philox4x64-10 (counter (q,0,0,0), key (seed, 2)),
+// zero biases; output layer uniform in +-sqrt(1/128).
+__global__ void k_mlp_init(float *params, uint64_t seed) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < NPARAM; q += gridDim.x * blockDim.x) {
+        uint64_t c[4] = {(uint64_t)q, 0ull, 0ull, 0ull};
+        philox4x64_10(c, seed, 2ull);
+        const float u = (float)(c[0] >> 40) * (1.0f / 16777216.0f) * 2.0f - 1.0f;
+        float w = 0.0f;
+        if (q < OFF_B1) w = u * sqrtf(6.0f / IN);
+        else if ((q >= OFF_W2 && q < OFF_B2) || (q >= OFF_W3 && q < OFF_B3) || (q >= OFF_W4 && q < OFF_B4))
+            w = u * sqrtf(6.0f / H);
+        else if (q >= OFF_W5 && q < OFF_B5) w = u * sqrtf(1.0f / H);
+        params[q] = w;
+    }
+}
+
+__global__ void k_fill(float *p, int64_t n, float v) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+}  // namespace
+
+struct rt_surrogate {
+    rt_mlp_cfg cfg;
+    int64_t step;
+    float lo[3], hi[3];
+    void *block;
+    float *params, *adam_m, *adam_v;
+    uint8_t *img;
+    float *partial;  // [nparts][NPARAM+1]
+    int nparts;
+    float *scratch;  // [NPARAM+1] misc device scratch
+};
+
+namespace {
+
+MlpDev mlp_dev(const rt_surrogate *s) {
+    MlpDev n;
+    n.params = s->params;
+    n.img = s->img;
+    for (int c = 0; c < 3; ++c) {
+        n.lo[c] = (double)s->lo[c];
+        n.ext[c] = (double)s->hi[c] - (double)s->lo[c];
+    }
+    return n;
+}
+
+bool g_attr_done = false;
+rt_status set_smem_attrs() {
+    if (g_attr_done) return RT_OK;
+    if (cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, INF_SMEM_TOTAL) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, TR_SMEM_TOTAL) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        return RT_ERR_CUDA;
+    }
+    g_attr_done = true;
+    return RT_OK;
+}
+
+rt_status train_launch(const rt_surrogate *s, const SampleSrc &S, int64_t m, float inv_batch, cudaStream_t st) {
+    RT_TRY(set_smem_attrs());
+    int64_t ntiles = (m + 127) / 128;
+    int grid = (int)(ntiles < s->nparts ? ntiles : s->nparts);
+    if (grid < 1) grid = 1;
+    k_mlp_train<<<grid, 128, TR_SMEM_TOTAL, st>>>(mlp_dev(s), S, m, inv_batch, s->partial, rt_status_ptr());
+    RT_TRY(rt_check_launch());
+    return RT_OK;
+}
+
+}  // namespace
+
+extern "C" void rt_mlp_cfg_default(rt_mlp_cfg *c) {
+    if (!c) return;
+    c->lr = 1e-3f;
+    c->beta1 = 0.9f;
+    c->beta2 = 0.999f;
+    c->eps = 1e-8f;
+    c->batch = 262144;
+    c->reserved = 0;
+}
+
+extern "C" int64_t rt_surrogate_param_count(void) { return NPARAM; }
+
+extern "C" rt_status rt_surrogate_create(const rt_mlp_cfg *cfg, uint64_t seed, rt_stream_t stream,
+                                         rt_surrogate **out) {
+    if (!out) return RT_ERR_INVALID_ARG;
+    *out = nullptr;
+    rt_mlp_cfg c;
+    rt_mlp_cfg_default(&c);
+    if (cfg) c = *cfg;
+    if (!(c.lr > 0.f) || !(c.beta1 >= 0.f && c.beta1 < 1.f) || !(c.beta2 >= 0.f && c.beta2 < 1.f) ||
+        !(c.eps > 0.f) || c.batch <= 0)
+        return RT_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    rt_surrogate *s = new rt_surrogate();
+    s->cfg = c;
+    s->step = 0;
+    for (int k = 0; k < 3; ++k) {
+        s->lo[k] = -1.f;
+        s->hi[k] = 1.f;
+    }
+    s->nparts = rt_num_sms();
+    const size_t pbytes = ((size_t)(NPARAM + 1) * 4 + 255) & ~(size_t)255;
+    const size_t total = 3 * pbytes + IMG_BYTES + (size_t)s->nparts * pbytes + pbytes;
+    rt_status r = rt_alloc(&s->block, total, stream);
+    if (r != RT_OK) {
+        delete s;
+        return r;
+    }
+    char *b = (char *)s->block;
+    s->params = (float *)b;
+    s->adam_m = (float *)(b + pbytes);
+    s->adam_v = (float *)(b + 2 * pbytes);
+    s->img = (uint8_t *)(b + 3 * pbytes);
+    s->partial = (float *)(b + 3 * pbytes + IMG_BYTES);
+    s->scratch = (float *)(b + 3 * pbytes + IMG_BYTES + (size_t)s->nparts * pbytes);
+    // partial rows are NPARAM+1 floats apart
+    k_mlp_init<<<64, 256, 0, st>>>(s->params, seed);
+    k_fill<<<64, 256, 0, st>>>(s->adam_m, NPARAM, 0.f);
+    k_fill<<<64, 256, 0, st>>>(s->adam_v, NPARAM, 0.f);
+    k_mlp_pack<<<64, 256, 0, st>>>(s->params, s->img);
+    if (rt_check_launch() != RT_OK || cudaStreamSynchronize(st) != cudaSuccess) {
+        rt_free(s->block, stream);
+        delete s;
+        return RT_ERR_CUDA;
+    }
+    *out = s;
+    return RT_OK;
+}
+
+extern "C" rt_status rt_surrogate_destroy(rt_surrogate *s, rt_stream_t stream) {
+    if (!s) return RT_ERR_INVALID_ARG;
+    rt_free(s->block, stream);
+    delete s;
+    return RT_OK;
+}
+
+extern "C" rt_status rt_surrogate_set_params(rt_surrogate *s, const float *params, rt_stream_t stream) {
+    if (!s || !params) return RT_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(s->params, params, NPARAM * 4, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return RT_ERR_CUDA;
+    k_fill<<<64, 256, 0, st>>>(s->adam_m, NPARAM, 0.f);
+    k_fill<<<64, 256, 0, st>>>(s->adam_v, NPARAM, 0.f);
+    k_mlp_pack<<<64, 256, 0, st>>>(s->params, s->img);
+    s->step = 0;
+    return rt_check_launch();
+}
+
+extern "C" rt_status rt_surrogate_get_params(const rt_surrogate *s, float *params, rt_stream_t stream) {
+    if (!s || !params) return RT_ERR_INVALID_ARG;
+    return cudaMemcpyAsync(params, s->params, NPARAM * 4, cudaMemcpyDeviceToDevice, (cudaStream_t)stream) ==
+                   cudaSuccess
+               ? RT_OK
+               : RT_ERR_CUDA;
+}
+
+extern "C" rt_status rt_surrogate_get_state(const rt_surrogate *s, float *state, rt_stream_t stream) {
+    if (!s || !state) return RT_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    float stepf = (float)s->step;
+    if (cudaMemcpyAsync(state, s->params, NPARAM * 4, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(state + NPARAM, s->adam_m, NPARAM * 4, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(state + 2 * NPARAM, s->adam_v, NPARAM * 4, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(state + 3 * NPARAM, &stepf, 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return RT_ERR_CUDA;
+    return RT_OK;
+}
+
+extern "C" rt_status rt_surrogate_set_state(rt_surrogate *s, const float *state, rt_stream_t stream) {
+    if (!s || !state) return RT_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    float stepf = 0.f;
+    if (cudaMemcpyAsync(s->params, state, NPARAM * 4, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(s->adam_m, state + NPARAM, NPARAM * 4, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(s->adam_v, state + 2 * NPARAM, NPARAM * 4, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(&stepf, state + 3 * NPARAM, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return RT_ERR_CUDA;
+    if (!(stepf >= 0.f)) return RT_ERR_INVALID_ARG;
+    s->step = (int64_t)stepf;
+    k_mlp_pack<<<64, 256, 0, st>>>(s->params, s->img);
+    return rt_check_launch();
+}
+
+extern "C" rt_status rt_surrogate_set_bounds(rt_surrogate *s, const float *lo, const float *hi) {
+    if (!s || !lo || !hi) return RT_ERR_INVALID_ARG;
+    for (int c = 0; c < 3; ++c) {
+        if (!(hi[c] >= lo[c])) return RT_ERR_INVALID_ARG;
+        s->lo[c] = lo[c];
+        s->hi[c] = hi[c];
+    }
+    return RT_OK;
+}
+
+extern "C" rt_status rt_surrogate_forward(const rt_surrogate *s, const float *pos, const float *dir, int64_t m,
+                                          float *p_out, rt_stream_t stream) {
+    if (!s || m < 0) return RT_ERR_INVALID_ARG;
+    if (m == 0) return RT_OK;
+    if (!pos || !dir || !p_out) return RT_ERR_INVALID_ARG;
+    RT_TRY(set_smem_attrs());
+    SampleSrc S;
+    memset(&S, 0, sizeof(S));
+    S.mode = 0;
+    S.pos = pos;
+    S.dir = dir;
+    int64_t ntiles = (m + 127) / 128;
+    int grid = (int)(ntiles < rt_num_sms() ? ntiles : rt_num_sms());
+    k_mlp_infer<<<grid, 128, INF_SMEM_TOTAL, (cudaStream_t)stream>>>(mlp_dev(s), S, m, p_out, 0.f, nullptr,
+                                                                     nullptr, nullptr, rt_status_ptr());
+    return rt_check_launch();
+}
+
+extern "C" rt_status rt_surrogate_loss_grad(const rt_surrogate *s, const float *pos, const float *dir,
+                                            const float *y, int64_t m, float *grad_out, float *loss_out,
+                                            rt_stream_t stream) {
+    if (!s || m <= 0 || !pos || !dir || !y || !grad_out) return RT_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    SampleSrc S;
+    memset(&S, 0, sizeof(S));
+    S.mode = 0;
+    S.pos = pos;
+    S.dir = dir;
+    S.y = y;
+    RT_TRY(train_launch(s, S, m, 1.0f / (float)m, st));
+    int64_t ntiles = (m + 127) / 128;
+    int nparts = (int)(ntiles < s->nparts ? ntiles : s->nparts);
+    k_mlp_reduce_adam<<<(NPARAM + 256) / 256, 256, 0, st>>>(s->partial, nparts, grad_out, loss_out, nullptr,
+                                                           nullptr, nullptr, nullptr, 0.f, 0.f, 0.f, 0.f, 1.f,
+                                                           1.f, 0);
+    return rt_check_launch();
+}
+
+extern "C" rt_status rt_surrogate_train(rt_surrogate *s, const rt_bvh *bvh, const rt_rayspec *samples,
+                                        const float *T_target, int32_t steps, uint64_t seed, float *loss_curve,
+                                        rt_stream_t stream) {
+    if (!s || !bvh || !samples || !T_target || steps < 0) return RT_ERR_INVALID_ARG;
+    if (samples->kind == RT_RAYS_EXPLICIT || samples->ray_ids) return RT_ERR_UNSUPPORTED;
+    RaySetDev rs;
+    int64_t R = 0;
+    RT_TRY(rt_rayset_dev(bvh, samples, &rs, &R));
+    if (R <= 0) return RT_ERR_INVALID_ARG;
+    RT_TRY(rt_surrogate_set_bounds(s, bvh->lo, bvh->hi));
+    cudaStream_t st = (cudaStream_t)stream;
+    SampleSrc S;
+    memset(&S, 0, sizeof(S));
+    S.mode = 2;
+    S.b = bvh_dev(bvh);
+    S.rs = rs;
+    S.T_target = T_target;
+    S.seed = seed;
+    S.R = R;
+    const int64_t B = s->cfg.batch;
+    const int64_t ntiles = (B + 127) / 128;
+    const int nparts = (int)(ntiles < s->nparts ? ntiles : s->nparts);
+    for (int32_t k = 0; k < steps; ++k) {
+        S.step = s->step;
+        RT_TRY(train_launch(s, S, B, 1.0f / (float)B, st));
+        s->step += 1;
+        const double c1 = 1.0 - pow((double)s->cfg.beta1, (double)s->step);
+        const double c2 = 1.0 - pow((double)s->cfg.beta2, (double)s->step);
+        k_mlp_reduce_adam<<<(NPARAM + 256) / 256, 256, 0, st>>>(
+            s->partial, nparts, nullptr, loss_curve ? loss_curve + k : nullptr, s->params, s->adam_m, s->adam_v,
+            s->img, s->cfg.lr, s->cfg.beta1, s->cfg.beta2, s->cfg.eps, (float)c1, (float)c2, 1);
+        RT_TRY(rt_check_launch());
+    }
+    return RT_OK;
+}
+
+extern "C" rt_status rt_surrogate_infer(const rt_surrogate *s, const rt_bvh *bvh, const rt_rayspec *rays,
+                                        float band, float *T_out, int64_t *n_fallback, rt_stream_t stream) {
+    if (!s || !bvh || !rays || !(band >= 0.f && band <= 0.5f)) return RT_ERR_INVALID_ARG;
+    if (rays->kind == RT_RAYS_EXPLICIT) return RT_ERR_UNSUPPORTED;
+    RaySetDev rs;
+    int64_t m = 0;
+    RT_TRY(rt_rayset_dev(bvh, rays, &rs, &m));
+    if (m == 0) return RT_OK;
+    if (!T_out) return RT_ERR_INVALID_ARG;
+    RT_TRY(set_smem_attrs());
+    cudaStream_t st = (cudaStream_t)stream;
+    SampleSrc S;
+    memset(&S, 0, sizeof(S));
+    S.mode = 1;
+    S.b = bvh_dev(bvh);
+    S.rs = rs;
+    S.R = rs.n_rays;
+    void *fb = nullptr;
+    const bool use_fb = band > 0.f;
+    int64_t *fb_rid = nullptr, *fb_pos = nullptr;
+    unsigned long long *fb_count = nullptr, *work = nullptr;
+    if (use_fb) {
+        RT_TRY(rt_alloc(&fb, 16 * (size_t)m + 512, stream));
+        fb_rid = (int64_t *)fb;
+        fb_pos = fb_rid + m;
+        fb_count = (unsigned long long *)(fb_pos + m);
+        work = fb_count + 4;
+        if (cudaMemsetAsync(fb_count, 0, 8, st) != cudaSuccess) {
+            rt_free(fb, stream);
+            return RT_ERR_CUDA;
+        }
+    }
+    int64_t ntiles = (m + 127) / 128;
+    int grid = (int)(ntiles < rt_num_sms() ? ntiles : rt_num_sms());
+    k_mlp_infer<<<grid, 128, INF_SMEM_TOTAL, st>>>(mlp_dev(s), S, m, T_out, band, fb_rid, fb_pos, fb_count,
+                                                   rt_status_ptr());
+    rt_status r = rt_check_launch();
+    if (r == RT_OK && use_fb) {
+        r = rt_trace_launch_list(bvh, rays, fb_rid, fb_pos, fb_count, m, T_out, stream, work);
+        if (r == RT_OK && n_fallback &&
+            cudaMemcpyAsync(n_fallback, fb_count, 8, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            r = RT_ERR_CUDA;
+    } else if (r == RT_OK && n_fallback) {
+        if (cudaMemsetAsync(n_fallback, 0, 8, st) != cudaSuccess) r = RT_ERR_CUDA;
+    }
+    if (fb) rt_free(fb, stream);
+    return r;
+}

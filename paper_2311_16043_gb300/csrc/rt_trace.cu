@@ -15,29 +15,7 @@
 
 namespace {
 
-enum { MODE_EXPLICIT = 0, MODE_FULL = 1, MODE_IDS = 2 };
-
-struct TraceJob {
-    int mode;
-    int64_t n_items;
-    int64_t n_tiles;      // MODE_FULL
-    int32_t order_block;  // MODE_FULL: tiles per sweep
-    int64_t n_out;        // outputs (rays)
-};
-
-// Decode a MODE_FULL item into (tile, direction).
-__device__ __forceinline__ void full_item(const TraceJob &job, int32_t K, int64_t item, int64_t &tile,
-                                          int32_t &k) {
-    const int64_t B = job.order_block;
-    const int64_t grp = item / (B * K);
-    const int64_t rem = item - grp * B * K;
-    int64_t in_grp = job.n_tiles - grp * B;
-    if (in_grp > B) in_grp = B;
-    k = (int32_t)(rem / in_grp);
-    tile = grp * B + rem % in_grp;
-}
-
-template <bool PACKET>
+template <bool PACKET, bool COUNT>
 __global__ void __launch_bounds__(128) k_trace(BvhDev b, RaySetDev rs, TraceJob job, float *T_out,
                                                TraceAux aux, unsigned long long *work) {
     const unsigned FULL = 0xffffffffu;
@@ -49,80 +27,15 @@ __global__ void __launch_bounds__(128) k_trace(BvhDev b, RaySetDev rs, TraceJob 
         if (lane == 0) item = atomicAdd(work, 1ull);
         item = __shfl_sync(FULL, item, 0);
         if ((int64_t)item >= job.n_items) break;
-
-        // ---- ray of this lane ----
-        bool valid = false;
-        float3 o = make_float3(0.f, 0.f, 0.f), d = make_float3(0.f, 0.f, 1.f);
-        int32_t src = -1;
-        int64_t out_idx = 0;
-        if (job.mode == MODE_FULL) {
-            int64_t tile;
-            int32_t k;
-            full_item(job, rs.K, (int64_t)item, tile, k);
-            const int64_t p = tile * 32 + lane;
-            if (p < b.n) {
-                valid = true;
-                const float4 mu = __ldg(b.gauss + 4 * p);
-                const int32_t g = __float_as_int(__ldg(b.gauss + 4 * p + 1).w);
-                out_idx = (int64_t)g * rs.K + k;
-                implicit_ray(rs, out_idx, k, mu, o, d);
-                src = (int32_t)p;
-            }
-        } else {
-            const int64_t r = (int64_t)item * 32 + lane;
-            if (r < job.n_out) {
-                valid = true;
-                out_idx = r;
-                if (job.mode == MODE_EXPLICIT) {
-                    o = make_float3(rs.ray_o[3 * r], rs.ray_o[3 * r + 1], rs.ray_o[3 * r + 2]);
-                    d = make_float3(rs.ray_d[3 * r], rs.ray_d[3 * r + 1], rs.ray_d[3 * r + 2]);
-                    if (rs.ray_src) {
-                        const int32_t s = rs.ray_src[r];
-                        src = (s >= 0 && s < b.n) ? b.rank[s] : -1;
-                    }
-                } else {
-                    const int64_t rid = rs.ray_ids[r];
-                    if (rid < 0 || rid >= rs.n_rays) {
-                        rt_set_error(aux.status, RT_ERR_INVALID_ARG);
-                        valid = false;
-                        T_out[r] = __int_as_float(0x7fc00000);
-                    } else {
-                        const int64_t g = rid / rs.K;
-                        const int32_t k = (int32_t)(rid - g * rs.K);
-                        const int32_t p = b.rank[g];
-                        const float4 mu = __ldg(b.gauss + 4 * (int64_t)p);
-                        implicit_ray(rs, rid, k, mu, o, d);
-                        src = p;
-                    }
-                }
-            }
+        int64_t n_out = job.n_out;
+        if (job.dyn_count) {
+            const int64_t c = (int64_t)*job.dyn_count;
+            n_out = c < n_out ? c : n_out;
+            if ((int64_t)item * 32 >= n_out) break;
         }
-
-        LaneLog lg;
-        lg.ids = (aux.hit_ids && valid) ? aux.hit_ids + out_idx * aux.cap : nullptr;
-        lg.cap = aux.cap;
-        lg.count = 0;
-        float T;
-        if (PACKET) {
-            T = trace_packet(b, o, d, src, valid, lg, wc, aux.status);
-        } else {
-            T = valid ? trace_ray(b, o, d, src, lg, wc, aux.status) : 1.0f;
-        }
-        if (valid) {
-            T_out[out_idx] = T;
-            if (aux.hit_count) aux.hit_count[out_idx] = lg.count;
-            rays_done++;
-        }
+        trace_item<PACKET, COUNT>(b, rs, job, T_out, aux, (int64_t)item, n_out, wc, rays_done);
     }
-    if (aux.counters) {
-        unsigned long long v[4] = {wc.box, wc.gauss, wc.hits, rays_done};
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            unsigned long long x = v[c];
-            for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(FULL, x, off);
-            if (lane == 0 && x) atomicAdd(aux.counters + c, x);
-        }
-    }
+    flush_counts<COUNT>(aux, wc, rays_done);
 }
 
 int persistent_blocks(const void *kernel, int threads) {
@@ -136,6 +49,25 @@ int persistent_blocks(const void *kernel, int threads) {
 }
 
 }  // namespace
+
+// Launch the single-scene kernel on an explicit job (used by the autotuner).
+rt_status rt_trace_launch_job(const BvhDev &b, const RaySetDev &rs, const TraceJob &job, float *T_out,
+                              bool packet, rt_stream_t stream, unsigned long long *work) {
+    TraceAux aux;
+    memset(&aux, 0, sizeof(aux));
+    aux.status = rt_status_ptr();
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(work, 0, sizeof(unsigned long long), st) != cudaSuccess) return RT_ERR_CUDA;
+    const int threads = 128;
+    if (packet) {
+        int grid = persistent_blocks((const void *)k_trace<true, false>, threads);
+        k_trace<true, false><<<grid, threads, 0, st>>>(b, rs, job, T_out, aux, work);
+    } else {
+        int grid = persistent_blocks((const void *)k_trace<false, false>, threads);
+        k_trace<false, false><<<grid, threads, 0, st>>>(b, rs, job, T_out, aux, work);
+    }
+    return rt_check_launch();
+}
 
 // Shared by rt_trace_visibility and the batched launch.
 rt_status rt_trace_launch(const rt_bvh *bvh, const rt_rayspec *rays, float *T_out,
@@ -152,9 +84,12 @@ rt_status rt_trace_launch(const rt_bvh *bvh, const rt_rayspec *rays, float *T_ou
     if (count == 0) return RT_OK;
 
     TraceJob job;
+    job.out_index = nullptr;
+    job.dyn_count = nullptr;
     job.n_out = count;
     job.order_block = 1;
     job.n_tiles = 0;
+    job.tile_base = 0;
     if (rays->kind == RT_RAYS_EXPLICIT) job.mode = MODE_EXPLICIT;
     else if (rays->ray_ids) job.mode = MODE_IDS;
     else job.mode = MODE_FULL;
@@ -187,17 +122,51 @@ rt_status rt_trace_launch(const rt_bvh *bvh, const rt_rayspec *rays, float *T_ou
     if (cudaMemsetAsync(work, 0, sizeof(unsigned long long), st) != cudaSuccess) res = RT_ERR_CUDA;
     if (res == RT_OK) {
         const int threads = 128;
-        if (packet) {
-            int grid = persistent_blocks((const void *)k_trace<true>, threads);
-            k_trace<true><<<grid, threads, 0, st>>>(b, rs, job, T_out, aux, work);
-        } else {
-            int grid = persistent_blocks((const void *)k_trace<false>, threads);
-            k_trace<false><<<grid, threads, 0, st>>>(b, rs, job, T_out, aux, work);
-        }
+        const bool count = aux.counters != nullptr;
+        const void *kern = packet ? (count ? (const void *)k_trace<true, true> : (const void *)k_trace<true, false>)
+                                  : (count ? (const void *)k_trace<false, true> : (const void *)k_trace<false, false>);
+        int grid = persistent_blocks(kern, threads);
+        if (packet && count) k_trace<true, true><<<grid, threads, 0, st>>>(b, rs, job, T_out, aux, work);
+        else if (packet) k_trace<true, false><<<grid, threads, 0, st>>>(b, rs, job, T_out, aux, work);
+        else if (count) k_trace<false, true><<<grid, threads, 0, st>>>(b, rs, job, T_out, aux, work);
+        else k_trace<false, false><<<grid, threads, 0, st>>>(b, rs, job, T_out, aux, work);
         res = rt_check_launch();
     }
     if (own) rt_free(work, stream);
     return res;
+}
+
+// Trace the rays listed in ray_ids[0 .. *count) (device count, at most
+// max_count) of an implicit set and write T_out[out_index[i]].
+rt_status rt_trace_launch_list(const rt_bvh *bvh, const rt_rayspec *rays, const int64_t *ray_ids,
+                               const int64_t *out_index, const unsigned long long *count, int64_t max_count,
+                               float *T_out, rt_stream_t stream, unsigned long long *work) {
+    if (rays->kind == RT_RAYS_EXPLICIT || !ray_ids || !out_index || !count || !work) return RT_ERR_INVALID_ARG;
+    RaySetDev rs;
+    int64_t c = 0;
+    rt_rayspec tmp = *rays;
+    tmp.ray_ids = nullptr;
+    RT_TRY(rt_rayset_dev(bvh, &tmp, &rs, &c));
+    rs.ray_ids = ray_ids;
+    if (max_count <= 0) return RT_OK;
+    TraceJob job;
+    job.mode = MODE_IDS;
+    job.out_index = out_index;
+    job.dyn_count = count;
+    job.n_out = max_count;
+    job.n_tiles = 0;
+    job.tile_base = 0;
+    job.order_block = 1;
+    job.n_items = (max_count + 31) / 32;
+    TraceAux aux;
+    memset(&aux, 0, sizeof(aux));
+    aux.status = rt_status_ptr();
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(work, 0, sizeof(unsigned long long), st) != cudaSuccess) return RT_ERR_CUDA;
+    const int threads = 128;
+    int grid = persistent_blocks((const void *)k_trace<false, false>, threads);
+    k_trace<false, false><<<grid, threads, 0, st>>>(bvh_dev(bvh), rs, job, T_out, aux, work);
+    return rt_check_launch();
 }
 
 extern "C" rt_status rt_trace_visibility(const rt_bvh *bvh, const rt_rayspec *rays, float *T_out,

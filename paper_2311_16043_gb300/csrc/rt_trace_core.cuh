@@ -50,14 +50,16 @@ __device__ __forceinline__ float3 safe_inv(float3 d) {
     return make_float3(1.0f / x, 1.0f / y, 1.0f / z);
 }
 
-// Ray vs axis-aligned box over t in [0, inf).  The differences (lo - o) are
-// formed first so their signs are exact; the far distance gets a 1e-6
-// relative allowance so rounding never rejects a box that the ray touches.
+// Ray vs axis-aligned box over t in [0, inf), t = lo * inv - o * inv (one
+// FMA per plane, oi = o * inv precomputed).  The rounding of oi is absorbed
+// by the boxes' absolute margin (1e-6 of the scene extent) and the far
+// distance gets a 1e-6 relative allowance, so rounding never rejects a box
+// that an accepted peak lies in.
 __device__ __forceinline__ bool slab(float lox, float hix, float loy, float hiy, float loz, float hiz,
-                                     float3 o, float3 inv) {
-    float tx0 = (lox - o.x) * inv.x, tx1 = (hix - o.x) * inv.x;
-    float ty0 = (loy - o.y) * inv.y, ty1 = (hiy - o.y) * inv.y;
-    float tz0 = (loz - o.z) * inv.z, tz1 = (hiz - o.z) * inv.z;
+                                     float3 oi, float3 inv) {
+    float tx0 = fmaf(lox, inv.x, -oi.x), tx1 = fmaf(hix, inv.x, -oi.x);
+    float ty0 = fmaf(loy, inv.y, -oi.y), ty1 = fmaf(hiy, inv.y, -oi.y);
+    float tz0 = fmaf(loz, inv.z, -oi.z), tz1 = fmaf(hiz, inv.z, -oi.z);
     float tnear = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.0f));
     float tfar = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fmaxf(tz0, tz1));
     return tnear <= fmaf(fabsf(tfar), 1e-6f, tfar);
@@ -116,19 +118,21 @@ struct WorkCounts {
 };
 
 // Strategy 1: each thread traverses alone with a private stack.
+template <bool COUNT>
 __device__ __forceinline__ float trace_ray(const BvhDev &b, float3 o, float3 d, int32_t src,
                                            LaneLog &lg, WorkCounts &wc, int *status) {
     float T = 1.0f;
     if (b.n <= 0) return T;
     if (b.n == 1) {
-        wc.gauss++;
+        if (COUNT) wc.gauss++;
         if (src != 0 && gauss_hit(b, 0, o, d, T)) {
-            wc.hits++;
+            if (COUNT) wc.hits++;
             log_hit(lg, b, 0);
         }
         return T < b.t_min ? 0.0f : T;
     }
     const float3 inv = safe_inv(d);
+    const float3 oi = make_float3(o.x * inv.x, o.y * inv.y, o.z * inv.z);
     uint32_t stack[RT_STACK];
     int sp = 0;
     uint32_t node = 0;
@@ -137,17 +141,17 @@ __device__ __forceinline__ float trace_ray(const BvhDev &b, float3 o, float3 d, 
         const float4 n1 = __ldg(b.nodes + 4 * node + 1);
         const float4 n2 = __ldg(b.nodes + 4 * node + 2);
         const float4 n3 = __ldg(b.nodes + 4 * node + 3);
-        bool hl = slab(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, o, inv);
-        bool hr = slab(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, o, inv);
-        wc.box += 2;
+        bool hl = slab(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, oi, inv);
+        bool hr = slab(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, oi, inv);
+        if (COUNT) wc.box += 2;
         const uint32_t cl = __float_as_uint(n3.x), cr = __float_as_uint(n3.y);
         if (hl && (cl & RT_LEAF_BIT)) {
             int32_t p = (int32_t)(cl & ~RT_LEAF_BIT);
             hl = false;
             if (p != src) {
-                wc.gauss++;
+                if (COUNT) wc.gauss++;
                 if (gauss_hit(b, p, o, d, T)) {
-                    wc.hits++;
+                    if (COUNT) wc.hits++;
                     log_hit(lg, b, p);
                 }
             }
@@ -156,9 +160,9 @@ __device__ __forceinline__ float trace_ray(const BvhDev &b, float3 o, float3 d, 
             int32_t p = (int32_t)(cr & ~RT_LEAF_BIT);
             hr = false;
             if (p != src) {
-                wc.gauss++;
+                if (COUNT) wc.gauss++;
                 if (gauss_hit(b, p, o, d, T)) {
-                    wc.hits++;
+                    if (COUNT) wc.hits++;
                     log_hit(lg, b, p);
                 }
             }
@@ -188,6 +192,7 @@ __device__ __forceinline__ float trace_ray(const BvhDev &b, float3 o, float3 d, 
 // ray hit the node (the lane mask travels with the node on the stack), so the
 // per-ray work counts equal strategy 1's.  The stack is warp-uniform and
 // lives in registers: entry e sits in lane e % 32, column e / 32.
+template <bool COUNT>
 __device__ __forceinline__ float trace_packet(const BvhDev &b, float3 o, float3 d, int32_t src,
                                               bool valid, LaneLog &lg, WorkCounts &wc,
                                               int *status) {
@@ -197,15 +202,16 @@ __device__ __forceinline__ float trace_packet(const BvhDev &b, float3 o, float3 
     if (b.n <= 0) return T;
     if (b.n == 1) {
         if (valid) {
-            wc.gauss++;
+            if (COUNT) wc.gauss++;
             if (src != 0 && gauss_hit(b, 0, o, d, T)) {
-                wc.hits++;
+                if (COUNT) wc.hits++;
                 log_hit(lg, b, 0);
             }
         }
         return T < b.t_min ? 0.0f : T;
     }
     const float3 inv = safe_inv(d);
+    const float3 oi = make_float3(o.x * inv.x, o.y * inv.y, o.z * inv.z);
     uint32_t alive = __ballot_sync(FULL, valid);
     uint32_t s_node0 = 0, s_node1 = 0, s_mask0 = 0, s_mask1 = 0;
     int sp = 0;
@@ -218,17 +224,17 @@ __device__ __forceinline__ float trace_packet(const BvhDev &b, float3 o, float3 
         const float4 n3 = __ldg(b.nodes + 4 * node + 3);
         bool hl = false, hr = false;
         if (mine) {
-            hl = slab(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, o, inv);
-            hr = slab(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, o, inv);
-            wc.box += 2;
+            hl = slab(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, oi, inv);
+            hr = slab(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, oi, inv);
+            if (COUNT) wc.box += 2;
         }
         const uint32_t cl = __float_as_uint(n3.x), cr = __float_as_uint(n3.y);
         if (cl & RT_LEAF_BIT) {
             int32_t p = (int32_t)(cl & ~RT_LEAF_BIT);
             if (hl && p != src) {
-                wc.gauss++;
+                if (COUNT) wc.gauss++;
                 if (gauss_hit(b, p, o, d, T)) {
-                    wc.hits++;
+                    if (COUNT) wc.hits++;
                     log_hit(lg, b, p);
                 }
             }
@@ -237,9 +243,9 @@ __device__ __forceinline__ float trace_packet(const BvhDev &b, float3 o, float3 
         if (cr & RT_LEAF_BIT) {
             int32_t p = (int32_t)(cr & ~RT_LEAF_BIT);
             if (hr && p != src) {
-                wc.gauss++;
+                if (COUNT) wc.gauss++;
                 if (gauss_hit(b, p, o, d, T)) {
-                    wc.hits++;
+                    if (COUNT) wc.hits++;
                     log_hit(lg, b, p);
                 }
             }
@@ -285,3 +291,117 @@ __device__ __forceinline__ float trace_packet(const BvhDev &b, float3 o, float3 
     }
     return T < b.t_min ? 0.0f : T;
 }
+
+// ---------------------------------------------------------------------------
+// Work items of a trace job
+// ---------------------------------------------------------------------------
+enum { MODE_EXPLICIT = 0, MODE_FULL = 1, MODE_IDS = 2 };
+
+struct TraceJob {
+    int mode;
+    const int64_t *out_index;                // MODE_IDS: output position of entry r (null = r)
+    const unsigned long long *dyn_count;     // MODE_IDS: device-side entry count (null = n_out)
+    int64_t n_items;
+    int64_t n_tiles;      // MODE_FULL
+    int32_t order_block;  // MODE_FULL: tiles per sweep
+    int64_t n_out;        // outputs (rays)
+    int64_t tile_base;    // MODE_FULL: first tile (a sample starts elsewhere than 0)
+};
+
+// Decode a MODE_FULL item into (tile, direction).
+__device__ __forceinline__ void full_item(const TraceJob &job, int32_t K, int64_t item, int64_t &tile,
+                                          int32_t &k) {
+    const int64_t B = job.order_block;
+    const int64_t grp = item / (B * K);
+    const int64_t rem = item - grp * B * K;
+    int64_t in_grp = job.n_tiles - grp * B;
+    if (in_grp > B) in_grp = B;
+    k = (int32_t)(rem / in_grp);
+    tile = job.tile_base + grp * B + rem % in_grp;
+}
+
+
+// One work item (32 rays) of a trace job: build each lane's ray, traverse,
+// write T (and the hit log).  Shared by the single-scene and batched kernels.
+template <bool PACKET, bool COUNT>
+__device__ __forceinline__ void trace_item(const BvhDev &b, const RaySetDev &rs, const TraceJob &job,
+                                           float *T_out, const TraceAux &aux, int64_t item, int64_t n_out,
+                                           WorkCounts &wc, unsigned long long &rays_done) {
+    const int lane = threadIdx.x & 31;
+    bool valid = false;
+    float3 o = make_float3(0.f, 0.f, 0.f), d = make_float3(0.f, 0.f, 1.f);
+    int32_t src = -1;
+    int64_t out_idx = 0;
+    if (job.mode == MODE_FULL) {
+        int64_t tile;
+        int32_t k;
+        full_item(job, rs.K, item, tile, k);
+        const int64_t p = tile * 32 + lane;
+        if (p < b.n) {
+            valid = true;
+            const float4 mu = __ldg(b.gauss + 4 * p);
+            const int32_t g = __float_as_int(__ldg(b.gauss + 4 * p + 1).w);
+            out_idx = (int64_t)g * rs.K + k;
+            implicit_ray(rs, out_idx, k, mu, o, d);
+            src = (int32_t)p;
+        }
+    } else {
+        const int64_t r = item * 32 + lane;
+        if (r < n_out) {
+            valid = true;
+            out_idx = job.out_index ? job.out_index[r] : r;
+            if (job.mode == MODE_EXPLICIT) {
+                o = make_float3(rs.ray_o[3 * r], rs.ray_o[3 * r + 1], rs.ray_o[3 * r + 2]);
+                d = make_float3(rs.ray_d[3 * r], rs.ray_d[3 * r + 1], rs.ray_d[3 * r + 2]);
+                if (rs.ray_src) {
+                    const int32_t s = rs.ray_src[r];
+                    src = (s >= 0 && s < b.n) ? b.rank[s] : -1;
+                }
+            } else {
+                const int64_t rid = rs.ray_ids[r];
+                if (rid < 0 || rid >= rs.n_rays) {
+                    rt_set_error(aux.status, RT_ERR_INVALID_ARG);
+                    valid = false;
+                    T_out[out_idx] = __int_as_float(0x7fc00000);
+                } else {
+                    const int64_t g = rid / rs.K;
+                    const int32_t k = (int32_t)(rid - g * rs.K);
+                    const int32_t p = b.rank[g];
+                    const float4 mu = __ldg(b.gauss + 4 * (int64_t)p);
+                    implicit_ray(rs, rid, k, mu, o, d);
+                    src = p;
+                }
+            }
+        }
+    }
+    LaneLog lg;
+    lg.ids = (aux.hit_ids && valid) ? aux.hit_ids + out_idx * aux.cap : nullptr;
+    lg.cap = aux.cap;
+    lg.count = 0;
+    float T;
+    if (PACKET) {
+        T = trace_packet<COUNT>(b, o, d, src, valid, lg, wc, aux.status);
+    } else {
+        T = valid ? trace_ray<COUNT>(b, o, d, src, lg, wc, aux.status) : 1.0f;
+    }
+    if (valid) {
+        T_out[out_idx] = T;
+        if (aux.hit_count) aux.hit_count[out_idx] = lg.count;
+        rays_done++;
+    }
+}
+
+template <bool COUNT>
+__device__ __forceinline__ void flush_counts(const TraceAux &aux, const WorkCounts &wc, unsigned long long rays_done) {
+    if (COUNT && aux.counters) {
+        const int lane = threadIdx.x & 31;
+        unsigned long long v[4] = {wc.box, wc.gauss, wc.hits, rays_done};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            unsigned long long x = v[c];
+            for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+            if (lane == 0 && x) atomicAdd(aux.counters + c, x);
+        }
+    }
+}
+

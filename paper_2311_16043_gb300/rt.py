@@ -50,9 +50,20 @@ class rt_trace_opts(C.Structure):
                 ("hit_count", C.c_void_p)]
 
 
+class rt_batch_job(C.Structure):
+    _fields_ = [("bvh", C.c_void_p), ("rays", rt_rayspec), ("T_out", C.c_void_p)]
+
+
+class rt_mlp_cfg(C.Structure):
+    _fields_ = [("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+                ("batch", C.c_int32), ("reserved", C.c_int32)]
+
+
 _P = C.c_void_p
 _I64 = C.c_int64
 _I32 = C.c_int32
+_U64 = C.c_uint64
+_F32 = C.c_float
 _SIGS = {
     "rt_params_default": (None, [_P]),
     "rt_status_string": (C.c_char_p, [_I32]),
@@ -70,6 +81,24 @@ _SIGS = {
     "rt_trace_visibility_dirs": (_I32, [_P, _P, _I32, _P, _P, _P]),
     "rt_trace_visibility_backward": (_I32, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I32,
                                             _P, _P, _P, _P, _P, _P]),
+    "rt_mlp_cfg_default": (None, [_P]),
+    "rt_surrogate_param_count": (_I64, []),
+    "rt_surrogate_create": (_I32, [_P, _U64, _P, _P]),
+    "rt_surrogate_destroy": (_I32, [_P, _P]),
+    "rt_surrogate_set_params": (_I32, [_P, _P, _P]),
+    "rt_surrogate_get_params": (_I32, [_P, _P, _P]),
+    "rt_surrogate_get_state": (_I32, [_P, _P, _P]),
+    "rt_surrogate_set_state": (_I32, [_P, _P, _P]),
+    "rt_surrogate_set_bounds": (_I32, [_P, _P, _P]),
+    "rt_surrogate_forward": (_I32, [_P, _P, _P, _I64, _P, _P]),
+    "rt_surrogate_loss_grad": (_I32, [_P, _P, _P, _P, _I64, _P, _P, _P]),
+    "rt_surrogate_train": (_I32, [_P, _P, _P, _P, _I32, _U64, _P, _P]),
+    "rt_surrogate_infer": (_I32, [_P, _P, _P, _F32, _P, _P, _P]),
+    "rt_trace_autotune": (_I32, [_P, _P, _P, _P, _P]),
+    "rt_batch_create": (_I32, [_P, _I32, _I32, _P, _P]),
+    "rt_batch_run": (_I32, [_P, _P]),
+    "rt_batch_info": (_I32, [_P, _P, _P, _P, _P]),
+    "rt_batch_destroy": (_I32, [_P, _P]),
 }
 
 
@@ -309,3 +338,166 @@ def rt_trace_visibility_backward(bvh: Bvh, rs: rt_rayspec, mean, scale, quat, op
         _ptr(d_quat, torch.float32, "d_quat"), _ptr(d_opacity, torch.float32, "d_opacity"),
         _ptr(d_ray_o, torch.float32, "d_ray_o"), _stream(stream)), "rt_trace_visibility_backward")
     return {"mean": d_mean, "scale": d_scale, "quat": d_quat, "opacity": d_opacity, "ray_o": d_ray_o}
+
+
+# ---------------------------------------------------------------------------
+# Learned visibility surrogate
+# ---------------------------------------------------------------------------
+def mlp_cfg(lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, batch=262144) -> rt_mlp_cfg:
+    c = rt_mlp_cfg()
+    lib().rt_mlp_cfg_default(C.byref(c))
+    c.lr, c.beta1, c.beta2, c.eps, c.batch = lr, beta1, beta2, eps, batch
+    return c
+
+
+def rt_surrogate_param_count() -> int:
+    return int(lib().rt_surrogate_param_count())
+
+
+class Surrogate:
+    """Owning wrapper of an ``rt_surrogate*`` handle."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def destroy(self, stream=None):
+        if self.handle:
+            _check(lib().rt_surrogate_destroy(self.handle, _stream(stream)), "rt_surrogate_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            if self.handle and _LIB is not None and torch.cuda.is_initialized():
+                _LIB.rt_surrogate_destroy(self.handle, _stream())
+                self.handle = None
+        except Exception:
+            pass
+
+
+def rt_surrogate_create(cfg: rt_mlp_cfg | None = None, seed: int = 0, stream=None) -> Surrogate:
+    h = C.c_void_p()
+    _check(lib().rt_surrogate_create(C.byref(cfg) if cfg is not None else None, seed, _stream(stream),
+                                     C.byref(h)), "rt_surrogate_create")
+    return Surrogate(h)
+
+
+def rt_surrogate_set_params(s: Surrogate, params, stream=None):
+    if params.numel() != rt_surrogate_param_count():
+        raise ValueError("wrong parameter count")
+    _check(lib().rt_surrogate_set_params(s.handle, _ptr(params, torch.float32, "params"), _stream(stream)),
+           "rt_surrogate_set_params")
+
+
+def rt_surrogate_get_params(s: Surrogate, stream=None):
+    out = torch.empty(rt_surrogate_param_count(), dtype=torch.float32, device="cuda")
+    _check(lib().rt_surrogate_get_params(s.handle, _ptr(out), _stream(stream)), "rt_surrogate_get_params")
+    return out
+
+
+def rt_surrogate_get_state(s: Surrogate, stream=None):
+    out = torch.empty(3 * rt_surrogate_param_count() + 1, dtype=torch.float32, device="cuda")
+    _check(lib().rt_surrogate_get_state(s.handle, _ptr(out), _stream(stream)), "rt_surrogate_get_state")
+    return out
+
+
+def rt_surrogate_set_state(s: Surrogate, state, stream=None):
+    if state.numel() != 3 * rt_surrogate_param_count() + 1:
+        raise ValueError("wrong state size")
+    _check(lib().rt_surrogate_set_state(s.handle, _ptr(state, torch.float32, "state"), _stream(stream)),
+           "rt_surrogate_set_state")
+
+
+def rt_surrogate_set_bounds(s: Surrogate, lo, hi):
+    lo_a = (C.c_float * 3)(*[float(x) for x in lo])
+    hi_a = (C.c_float * 3)(*[float(x) for x in hi])
+    _check(lib().rt_surrogate_set_bounds(s.handle, lo_a, hi_a), "rt_surrogate_set_bounds")
+
+
+def rt_surrogate_forward(s: Surrogate, pos, dirs, p_out=None, stream=None):
+    m = pos.shape[0]
+    if p_out is None:
+        p_out = torch.empty(m, dtype=torch.float32, device="cuda")
+    _check(lib().rt_surrogate_forward(s.handle, _ptr(pos, torch.float32, "pos"), _ptr(dirs, torch.float32, "dir"),
+                                      m, _ptr(p_out, torch.float32, "p_out"), _stream(stream)),
+           "rt_surrogate_forward")
+    return p_out
+
+
+def rt_surrogate_loss_grad(s: Surrogate, pos, dirs, y, stream=None):
+    m = pos.shape[0]
+    g = torch.empty(rt_surrogate_param_count(), dtype=torch.float32, device="cuda")
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    _check(lib().rt_surrogate_loss_grad(s.handle, _ptr(pos, torch.float32, "pos"), _ptr(dirs, torch.float32, "dir"),
+                                        _ptr(y, torch.float32, "y"), m, _ptr(g), _ptr(loss), _stream(stream)),
+           "rt_surrogate_loss_grad")
+    return loss, g
+
+
+def rt_surrogate_train(s: Surrogate, bvh: Bvh, rs: rt_rayspec, T_target, steps: int, seed: int = 0,
+                       loss_curve=None, stream=None):
+    if loss_curve is None:
+        loss_curve = torch.empty(max(steps, 1), dtype=torch.float32, device="cuda")
+    _check(lib().rt_surrogate_train(s.handle, bvh.handle, C.byref(rs), _ptr(T_target, torch.float32, "T_target"),
+                                    steps, seed, _ptr(loss_curve, torch.float32, "loss_curve"), _stream(stream)),
+           "rt_surrogate_train")
+    return loss_curve
+
+
+def rt_surrogate_infer(s: Surrogate, bvh: Bvh, rs: rt_rayspec, band: float = 0.3, T_out=None, n_fallback=None,
+                       stream=None):
+    R = rt_rayspec_count(bvh, rs)
+    if T_out is None:
+        T_out = torch.empty(R, dtype=torch.float32, device="cuda")
+    _check(lib().rt_surrogate_infer(s.handle, bvh.handle, C.byref(rs), band, _ptr(T_out, torch.float32, "T_out"),
+                                    _ptr(n_fallback, torch.int64, "n_fallback"), _stream(stream)),
+           "rt_surrogate_infer")
+    return T_out
+
+
+# ---------------------------------------------------------------------------
+# Autotuning and multi-scene batches
+# ---------------------------------------------------------------------------
+def rt_trace_autotune(bvh: Bvh, rs: rt_rayspec, T_scratch, opts: rt_trace_opts | None = None, stream=None):
+    opts = opts if opts is not None else trace_opts()
+    _check(lib().rt_trace_autotune(bvh.handle, C.byref(rs), _ptr(T_scratch, torch.float32, "T_scratch"),
+                                   C.byref(opts), _stream(stream)), "rt_trace_autotune")
+    return opts
+
+
+class Batch:
+    """Owning wrapper of an ``rt_batch*`` (keeps its jobs' objects alive)."""
+
+    def __init__(self, handle, n_jobs, keep):
+        self.handle = handle
+        self.n_jobs = n_jobs
+        self._keep = keep
+
+    def run(self, stream=None):
+        _check(lib().rt_batch_run(self.handle, _stream(stream)), "rt_batch_run")
+
+    def info(self):
+        nr, ni = C.c_int64(), C.c_int64()
+        k = (C.c_int32 * self.n_jobs)()
+        b = (C.c_int32 * self.n_jobs)()
+        _check(lib().rt_batch_info(self.handle, C.byref(nr), C.byref(ni), k, b), "rt_batch_info")
+        return {"n_rays": nr.value, "n_items": ni.value, "kernel": list(k), "order_block": list(b)}
+
+    def destroy(self, stream=None):
+        if self.handle:
+            _check(lib().rt_batch_destroy(self.handle, _stream(stream)), "rt_batch_destroy")
+            self.handle = None
+
+
+def rt_batch_create(jobs, autotune: bool = True, stream=None) -> Batch:
+    """jobs: list of (Bvh, rt_rayspec, T_out tensor)."""
+    arr = (rt_batch_job * len(jobs))()
+    for i, (bvh, rs, T) in enumerate(jobs):
+        if T.numel() != rt_rayspec_count(bvh, rs):
+            raise ValueError(f"job {i}: T_out has the wrong size")
+        arr[i].bvh = bvh.handle
+        arr[i].rays = rs
+        arr[i].T_out = _ptr(T, torch.float32, "T_out")
+    h = C.c_void_p()
+    _check(lib().rt_batch_create(arr, len(jobs), 1 if autotune else 0, _stream(stream), C.byref(h)),
+           "rt_batch_create")
+    return Batch(h, len(jobs), [j for j in jobs])
