@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--cpu-rays", type=int, default=2048, help="oracle sample for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--surrogate-steps", type=int, default=2000)
+    ap.add_argument("--band", type=float, default=0.3)
     return ap.parse_args()
 
 
@@ -169,6 +172,67 @@ def peaks():
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
     except Exception:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def run_surrogate(args, rt, torch, d, dirs, T, prm, dev):
+    """Learned visibility: train the MLP on the tracer's table, then infer on
+    held-out (randomly rotated) Fibonacci directions in batches of 1M-64M rays,
+    with and without tracer fallback; MAE and rays/s against the tracer."""
+    import scenes
+    n, K = T.shape
+    bvh = rt.rt_build_bvh(d["mean"], d["scale"], d["quat"], d["opacity"], prm)
+    rs = rt.rayspec(rt.RT_RAYS_DIRS, dirs=dirs)
+    s = rt.rt_surrogate_create(rt.mlp_cfg(batch=262144, lr=1e-3), seed=5)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    curve = rt.rt_surrogate_train(s, bvh, rs, T.view(-1), steps=args.surrogate_steps, seed=5)
+    ev[1].record()
+    torch.cuda.synchronize()
+    train_ms = ev[0].elapsed_time(ev[1])
+    held = torch.from_numpy(scenes.rotated_fibonacci(K, 51)).to(dev)
+    rs_h = rt.rayspec(rt.RT_RAYS_DIRS, dirs=held)
+    Th = torch.empty(n * K, dtype=torch.float32, device=dev)
+    rt.rt_trace_visibility(bvh, rs_h, Th)
+    ev[0].record()
+    rt.rt_trace_visibility(bvh, rs_h, Th)
+    ev[1].record()
+    torch.cuda.synchronize()
+    tracer_rate = n * K / (ev[0].elapsed_time(ev[1]) / 1000.0)
+    out = {"train_steps": args.surrogate_steps, "train_batch": 262144, "train_ms": train_ms,
+           "train_samples": args.surrogate_steps * 262144, "loss_first": float(curve[:10].mean()),
+           "loss_last": float(curve[-10:].mean()), "band": args.band,
+           "tracer_rays_per_s_heldout_full": tracer_rate, "batches": []}
+    nfb = torch.zeros(1, dtype=torch.int64, device=dev)
+    for B in (1 << 20, 1 << 22, 1 << 24, 1 << 26):
+        if B > n * K:
+            break
+        ids = torch.arange(B, dtype=torch.int64, device=dev)
+        rsb = rt.rayspec(rt.RT_RAYS_DIRS, dirs=held, ray_ids=ids)
+        ref = Th[:B]
+        out_b = {"rays": B}
+        for band, key in ((0.0, "surrogate_only"), (args.band, "with_fallback")):
+            q = torch.empty(B, dtype=torch.float32, device=dev)
+            rt.rt_surrogate_infer(s, bvh, rsb, band=band, T_out=q, n_fallback=nfb)
+            ev[0].record()
+            rt.rt_surrogate_infer(s, bvh, rsb, band=band, T_out=q, n_fallback=nfb)
+            ev[1].record()
+            torch.cuda.synchronize()
+            ms = ev[0].elapsed_time(ev[1])
+            out_b[key] = {"ms": ms, "rays_per_s": B / (ms / 1000.0), "mae": float((q - ref).abs().mean()),
+                          "fallback_fraction": float(nfb.item()) / B}
+        tq = torch.empty(B, dtype=torch.float32, device=dev)
+        rt.rt_trace_visibility(bvh, rsb, tq)
+        ev[0].record()
+        rt.rt_trace_visibility(bvh, rsb, tq)
+        ev[1].record()
+        torch.cuda.synchronize()
+        out_b["tracer_same_rays"] = {"ms": ev[0].elapsed_time(ev[1]),
+                                     "rays_per_s": B / (ev[0].elapsed_time(ev[1]) / 1000.0)}
+        out_b["speedup_vs_tracer_full_rate"] = out_b["with_fallback"]["rays_per_s"] / tracer_rate
+        out["batches"].append(out_b)
+    s.destroy()
+    bvh.destroy()
+    return out
 
 
 def run_reference(args, rank, world):
@@ -304,6 +368,10 @@ def main():
         e2e = {"value": world * R / (em / 1000.0), "unit": "rays/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": em}
 
+    surrogate = None
+    if not args.no_surrogate and rank == 0:
+        surrogate = run_surrogate(args, rt, torch, d, dirs, T, prm, dev)
+
     pk, pk_kind = peaks()
     tr_ms = statistics.mean(trace_ms)
     achieved = alg_bytes / (tr_ms / 1000.0) / 1e9
@@ -332,7 +400,7 @@ def main():
                     "kernel": ["auto", "per-ray", "packet"][args.kernel]}),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": (BUILD_KERNELS_PER_STEP + 1) * args.steps,
-                "clocks": clk}
+                "clocks": clk, "surrogate": surrogate}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()

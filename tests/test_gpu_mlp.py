@@ -154,19 +154,22 @@ def test_one_adam_step_matches_oracle(orc, small_trace):
     np.testing.assert_allclose(P1[big], w[big], atol=2e-5)
 
 
-def test_training_and_fallback(orc, small_trace):
-    """Train on the tracer's visibility of the scene, then infer on held-out
-    directions: the loss falls, the surrogate predicts T, and with the
-    fallback band the uncertain rays carry the traced value exactly."""
+def test_training_and_fallback():
+    """Train on the tracer's visibility of an object-scale scene (300k
+    flattened Gaussians on analytic surfaces x 32 directions), then infer on
+    held-out (rotated) directions: the loss falls, the surrogate beats a
+    constant predictor, and with the fallback band the uncertain rays carry
+    the traced value exactly."""
     from paper_2311_16043_gb300 import rt
-    sc, dirs, ref, o, d = small_trace
+    sc = scenes.object_scene(300_000, 2)
+    dirs = scenes.fibonacci_sphere(32)
     dv = {k: _dev(v) for k, v in sc.items()}
     bvh = rt.rt_build_bvh(dv["mean"], dv["scale"], dv["quat"], dv["opacity"])
     rs = rt.rayspec(rt.RT_RAYS_DIRS, dirs=_dev(dirs))
     T = rt.rt_trace_visibility(bvh, rs)
-    s = rt.rt_surrogate_create(rt.mlp_cfg(batch=16384, lr=2e-3), seed=3)
+    s = rt.rt_surrogate_create(rt.mlp_cfg(batch=65536, lr=1e-3), seed=3)
     curve = rt.rt_surrogate_train(s, bvh, rs, T, steps=1500, seed=5).cpu().numpy()
-    assert curve[-50:].mean() < 0.9 * curve[:5].mean(), (curve[:5], curve[-50:])
+    assert curve[-50:].mean() < 0.8 * curve[:5].mean(), (curve[:5], curve[-50:])
     held = scenes.rotated_fibonacci(32, 51)
     rs_h = rt.rayspec(rt.RT_RAYS_DIRS, dirs=_dev(held))
     T_h = rt.rt_trace_visibility(bvh, rs_h)
@@ -185,5 +188,6 @@ def test_training_and_fallback(orc, small_trace):
     assert mae_f <= mae_s
     mae_const = (T_h - T.mean()).abs().mean().item()
     print(f"held-out MAE: surrogate {mae_s:.4f}, with fallback {mae_f:.4f} ({nf} of {T_h.numel()} rays traced), "
-          f"constant {mae_const:.4f}")
-    assert mae_s < 0.9 * mae_const  # the network learned something beyond the mean
+          f"constant {mae_const:.4f}; loss {curve[:5].mean():.4f} -> {curve[-50:].mean():.4f}")
+    assert mae_s < 0.5 * mae_const
+    assert mae_f < 0.5 * mae_s or mae_f < 0.01
