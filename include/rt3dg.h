@@ -170,9 +170,11 @@ rt_status rt_materialize_rays(const rt_bvh *bvh, const rt_rayspec *rays, const i
 
 typedef enum {
     RT_KERNEL_AUTO = 0,
-    RT_KERNEL_RAY = 1,    /* one thread per ray, private traversal stack      */
-    RT_KERNEL_PACKET = 2  /* one warp per 32 rays of neighbouring Gaussians in
-                             one direction, shared stack (DIRS/ENV only)     */
+    RT_KERNEL_RAY = 1,    /* one thread per ray, private stack, binary tree    */
+    RT_KERNEL_PACKET = 2, /* one warp per 32 rays of neighbouring Gaussians in
+                             one direction, shared stack, binary tree          */
+    RT_KERNEL_WIDE = 3    /* as PACKET over the 4-wide tree (the binary tree
+                             collapsed by greedy largest-area expansion)       */
 } rt_kernel;
 
 typedef struct {

@@ -25,7 +25,7 @@
 #include "rt_trace_core.cuh"
 
 rt_status rt_trace_launch_job(const BvhDev &b, const RaySetDev &rs, const TraceJob &job, float *T_out,
-                              bool packet, rt_stream_t stream, unsigned long long *work);
+                              int strat, rt_stream_t stream, unsigned long long *work);
 
 namespace {
 
@@ -58,7 +58,7 @@ struct BatchJobDev {
     RaySetDev rs;
     TraceJob job;
     float *T_out;
-    int32_t packet;
+    int32_t strat;  // 0 per-ray, 1 packet, 2 4-wide packet
     int64_t item_begin;
 };
 
@@ -67,6 +67,8 @@ __global__ void __launch_bounds__(128) k_trace_batch(const BatchJobDev *__restri
                                                      unsigned long long *work) {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
+    __shared__ int2 stk_all[4 * RT_WIDE_STACK];
+    int2 *stk = stk_all + (threadIdx.x >> 5) * RT_WIDE_STACK;
     WorkCounts wc = {0, 0, 0};
     unsigned long long rays_done = 0;
     TraceAux aux;
@@ -88,8 +90,9 @@ __global__ void __launch_bounds__(128) k_trace_batch(const BatchJobDev *__restri
         }
         const BatchJobDev &J = jobs[lo];
         const int64_t local = (int64_t)item - J.item_begin;
-        if (J.packet) trace_item<true, false>(J.b, J.rs, J.job, J.T_out, aux, local, J.job.n_out, wc, rays_done);
-        else trace_item<false, false>(J.b, J.rs, J.job, J.T_out, aux, local, J.job.n_out, wc, rays_done);
+        if (J.strat == 2) trace_item<2, false>(J.b, J.rs, J.job, J.T_out, aux, local, J.job.n_out, wc, rays_done, stk);
+        else if (J.strat == 1) trace_item<1, false>(J.b, J.rs, J.job, J.T_out, aux, local, J.job.n_out, wc, rays_done, stk);
+        else trace_item<0, false>(J.b, J.rs, J.job, J.T_out, aux, local, J.job.n_out, wc, rays_done, stk);
     }
 }
 
@@ -138,9 +141,10 @@ extern "C" rt_status rt_trace_autotune(const rt_bvh *bvh, const rt_rayspec *rays
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    int best_k = RT_KERNEL_PACKET, best_b = 64;
+    int best_k = RT_KERNEL_PACKET, best_b = 1;
     rt_status res = RT_OK;
-    for (int kernel = RT_KERNEL_RAY; kernel <= RT_KERNEL_PACKET && res == RT_OK; ++kernel) {
+    for (int kernel = RT_KERNEL_RAY; kernel <= RT_KERNEL_WIDE && res == RT_OK; ++kernel) {
+        if (kernel == RT_KERNEL_WIDE && bvh->n_wide == 0) continue;
         for (int bi = 0; bi < 4 && res == RT_OK; ++bi) {
             TraceJob job = full_job(bvh, rs.K, blocks[bi]);
             job.n_tiles = S;
@@ -150,7 +154,7 @@ extern "C" rt_status rt_trace_autotune(const rt_bvh *bvh, const rt_rayspec *rays
             float ms = 0.f;
             for (int rep = 0; rep < 2 && res == RT_OK; ++rep) {  // first run warms caches
                 cudaEventRecord(e0, st);
-                res = rt_trace_launch_job(b, rs, job, T_scratch, kernel == RT_KERNEL_PACKET, stream, work);
+                res = rt_trace_launch_job(b, rs, job, T_scratch, kernel - 1, stream, work);
                 cudaEventRecord(e1, st);
                 if (cudaEventSynchronize(e1) != cudaSuccess) res = RT_ERR_CUDA;
                 cudaEventElapsedTime(&ms, e0, e1);
@@ -210,7 +214,7 @@ extern "C" rt_status rt_batch_create(const rt_batch_job *jobs, int32_t n_jobs, i
         }
         rt_trace_opts o;
         memset(&o, 0, sizeof(o));
-        o.kernel = J.rays.kind == RT_RAYS_DIRS ? RT_KERNEL_PACKET : RT_KERNEL_RAY;
+        o.kernel = J.rays.kind == RT_RAYS_DIRS ? (J.bvh->n_wide > 0 ? RT_KERNEL_WIDE : RT_KERNEL_PACKET) : RT_KERNEL_RAY;
         o.order_block = 64;
         if (autotune && count > 0) {
             r = rt_trace_autotune(J.bvh, &J.rays, J.T_out, &o, stream);
@@ -227,7 +231,7 @@ extern "C" rt_status rt_batch_create(const rt_batch_job *jobs, int32_t n_jobs, i
         H.rs = rs;
         H.job = full_job(J.bvh, rs.K, o.order_block);
         H.T_out = J.T_out;
-        H.packet = o.kernel == RT_KERNEL_PACKET;
+        H.strat = o.kernel == RT_KERNEL_WIDE ? (J.bvh->n_wide > 0 ? 2 : 1) : o.kernel == RT_KERNEL_PACKET ? 1 : 0;
         cost[j] = (double)count * log2((double)(J.bvh->n > 1 ? J.bvh->n : 2));
     }
     // largest estimated cost first

@@ -255,8 +255,8 @@ __global__ void k_prep(const float *__restrict__ mean, const float *__restrict__
             float a0 = R[c][0] * s[0], a1 = R[c][1] * s[1], a2 = R[c][2] * s[2];
             float h = K * sqrtf(a0 * a0 + a1 * a1 + a2 * a2);
             h = h * (1.0f + 1e-4f) + 4.0f * 1.1920929e-7f * fabsf(mu[c]) + margin + 1e-30f;
-            bx[c] = empty ? INFINITY : __fsub_rd(mu[c], h);
-            bx[3 + c] = empty ? -INFINITY : __fadd_ru(mu[c], h);
+            bx[c] = empty ? __int_as_float(0x7fc00000) : __fsub_rd(mu[c], h);
+            bx[3 + c] = empty ? __int_as_float(0x7fc00000) : __fadd_ru(mu[c], h);
         }
     }
 }
@@ -354,6 +354,87 @@ __global__ void k_refit(const float *__restrict__ leafbox, const int32_t *__rest
     }
 }
 
+// Surface area of a box stored (lo.x, hi.x, lo.y, hi.y, lo.z, hi.z); -1 for NaN.
+__device__ __forceinline__ float box_area(const float b[6]) {
+    const float dx = b[1] - b[0], dy = b[3] - b[2], dz = b[5] - b[4];
+    const float a = dx * dy + dy * dz + dz * dx;
+    return a == a ? a : -1.0f;
+}
+
+// One level of the collapse into a 4-wide tree.  Each frontier entry is a
+// binary internal node that becomes wide node w: its children are expanded
+// greedily (the internal child of largest surface area is replaced by its two
+// children) until four; children that are still internal binary nodes become
+// wide nodes of the next level.
+__global__ void k_collapse4(const float4 *__restrict__ nodes, const int2 *__restrict__ front_in,
+                            const unsigned *__restrict__ n_in, int2 *front_out, unsigned *n_out,
+                            unsigned *n_wide, float4 *wide) {
+    const unsigned cnt = *n_in;
+    for (unsigned f = blockIdx.x * blockDim.x + threadIdx.x; f < cnt; f += gridDim.x * blockDim.x) {
+        const int2 e = front_in[f];
+        uint32_t ref[4];
+        float box[4][6];
+        int m = 0;
+        auto add_children = [&](int32_t b) {
+            const float4 a = nodes[4 * (int64_t)b], c = nodes[4 * (int64_t)b + 1], d = nodes[4 * (int64_t)b + 2],
+                         r = nodes[4 * (int64_t)b + 3];
+            ref[m] = __float_as_uint(r.x);
+            box[m][0] = a.x; box[m][1] = a.y; box[m][2] = a.z; box[m][3] = a.w; box[m][4] = c.x; box[m][5] = c.y;
+            ++m;
+            ref[m] = __float_as_uint(r.y);
+            box[m][0] = c.z; box[m][1] = c.w; box[m][2] = d.x; box[m][3] = d.y; box[m][4] = d.z; box[m][5] = d.w;
+            ++m;
+        };
+        add_children(e.x);
+        while (m < 4) {
+            int best = -1;
+            float best_a = -2.0f;
+            for (int c = 0; c < m; ++c) {
+                if (ref[c] & RT_LEAF_BIT) continue;
+                const float a = box_area(box[c]);
+                if (a > best_a) {
+                    best_a = a;
+                    best = c;
+                }
+            }
+            if (best < 0) break;
+            const int32_t b = (int32_t)ref[best];
+            // move the last entry into the expanded slot, then append both children
+            ref[best] = ref[m - 1];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) box[best][k] = box[m - 1][k];
+            --m;
+            add_children(b);
+        }
+        float4 *w = wide + 8 * (int64_t)e.y;
+        float v[6][4];
+        uint32_t out_ref[4];
+        for (int c = 0; c < 4; ++c) {
+            if (c < m) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) v[k][c] = box[c][k];
+                if (ref[c] & RT_LEAF_BIT) {
+                    out_ref[c] = ref[c];
+                } else {
+                    const unsigned idx = atomicAdd(n_wide, 1u);
+                    const unsigned slot = atomicAdd(n_out, 1u);
+                    front_out[slot] = make_int2((int32_t)ref[c], (int32_t)idx);
+                    out_ref[c] = idx;
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) v[k][c] = __int_as_float(0x7fc00000);
+                out_ref[c] = RT_EMPTY;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) w[k] = make_float4(v[k][0], v[k][1], v[k][2], v[k][3]);
+        w[6] = make_float4(__uint_as_float(out_ref[0]), __uint_as_float(out_ref[1]), __uint_as_float(out_ref[2]),
+                           __uint_as_float(out_ref[3]));
+        w[7] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
 __global__ void k_export_boxes(const float4 *__restrict__ nodes, int64_t m, float *boxes,
                                int32_t *left, int32_t *right) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
@@ -407,7 +488,8 @@ extern "C" rt_status rt_build_bvh(const float *mean, const float *scale, const f
     size_t off_keys = off_rank + align256(sizeof(int32_t) * (size_t)n);
     size_t off_par = off_keys + align256(sizeof(uint64_t) * (size_t)n);
     size_t off_bnd = off_par + align256(sizeof(int32_t) * (size_t)(n > 0 ? 2 * n - 1 : 0));
-    size_t total = off_bnd + 256;
+    size_t off_wide = off_bnd + 256;
+    size_t total = off_wide + align256(sizeof(float4) * 8 * (size_t)ni);
     rt_status s = rt_alloc(&b->block, total, stream);
     if (s != RT_OK) {
         delete b;
@@ -422,6 +504,8 @@ extern "C" rt_status rt_build_bvh(const float *mean, const float *scale, const f
     b->keys = (uint64_t *)(base + off_keys);
     b->parent = (int32_t *)(base + off_par);
     b->bounds = (float *)(base + off_bnd);
+    b->wide = (float4 *)(base + off_wide);
+    b->n_wide = 0;
     for (int c = 0; c < 3; ++c) b->lo[c] = b->hi[c] = 0.f;
     if (n == 0) {
         *out = b;
@@ -438,7 +522,10 @@ extern "C" rt_status rt_build_bvh(const float *mean, const float *scale, const f
     size_t s_cnt = s_v1 + align256(4 * (size_t)n);
     size_t s_leaf = s_cnt + align256(4 * (size_t)kRadix * nblk);
     size_t s_arr = s_leaf + align256(24 * (size_t)n);
-    size_t s_total = s_arr + align256(4 * (size_t)ni);
+    size_t s_f0 = s_arr + align256(4 * (size_t)ni);
+    size_t s_f1 = s_f0 + align256(8 * (size_t)(ni + 1));
+    size_t s_cnt2 = s_f1 + align256(8 * (size_t)(ni + 1));
+    size_t s_total = s_cnt2 + 512;  // 64 level counts + the wide-node count (+ pad)
     void *scratch = nullptr;
     s = rt_alloc(&scratch, s_total, stream);
     if (s != RT_OK) {
@@ -453,6 +540,8 @@ extern "C" rt_status rt_build_bvh(const float *mean, const float *scale, const f
     uint32_t *counts = (uint32_t *)(sb + s_cnt);
     float *leafbox = (float *)(sb + s_leaf);
     uint32_t *arrivals = (uint32_t *)(sb + s_arr);
+    int2 *front[2] = {(int2 *)(sb + s_f0), (int2 *)(sb + s_f1)};
+    unsigned *wcnt = (unsigned *)(sb + s_cnt2);  // [0..63] level counts, [64] wide-node count (512 B region)
 
     rt_status result = RT_OK;
     do {
@@ -485,6 +574,32 @@ extern "C" rt_status rt_build_bvh(const float *mean, const float *scale, const f
                 break;
             }
             k_refit<<<grid_for(n, 256), 256, 0, st>>>(leafbox, b->parent, n, b->nodes, arrivals);
+            // collapse into the 4-wide tree, one level per launch (the tree has at
+            // most 64 levels; launches past the last level find an empty frontier)
+            const int2 root = make_int2(0, 0);
+            const unsigned one = 1u;
+            if (cudaMemsetAsync(wcnt, 0, 512, st) != cudaSuccess ||
+                cudaMemcpyAsync(front[0], &root, sizeof(int2), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+                cudaMemcpyAsync(wcnt, &one, sizeof(unsigned), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+                cudaMemcpyAsync(wcnt + 64, &one, sizeof(unsigned), cudaMemcpyHostToDevice, st) != cudaSuccess) {
+                result = RT_ERR_CUDA;
+                break;
+            }
+            int grid_c = grid_for(ni, 128);
+            for (int lvl = 0; lvl < 63; ++lvl)
+                k_collapse4<<<grid_c, 128, 0, st>>>(b->nodes, front[lvl & 1], wcnt + lvl, front[(lvl + 1) & 1],
+                                                     wcnt + lvl + 1, wcnt + 64, b->wide);
+            unsigned nw = 0, left_over = 0;
+            if (cudaMemcpyAsync(&nw, wcnt + 64, sizeof(unsigned), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaMemcpyAsync(&left_over, wcnt + 63, sizeof(unsigned), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess) {
+                result = RT_ERR_CUDA;
+                break;
+            }
+            // a frontier left after the last level would mean an unfinished wide
+            // tree (impossible for keys of <= 61 significant bits); then only
+            // the binary tree is used
+            b->n_wide = (left_over || nw > (unsigned)ni) ? 0 : nw;
         }
         if (rt_check_launch() != RT_OK) {
             result = RT_ERR_CUDA;

@@ -27,7 +27,16 @@
 // ---------------------------------------------------------------------------
 
 #define RT_LEAF_BIT 0x80000000u
+#define RT_EMPTY 0x7fffffffu  // empty child slot of a wide node (its box is NaN)
 #define RT_STACK 64  // >= tree depth: keys are 64-bit and unique
+#define RT_WIDE_STACK 256  // >= 3 pushes x 64 levels of the 4-wide tree
+
+// 4-wide node record, 128 B = 8 x float4, node j (root = 0):
+//   w[8j+0..5] = lo.x[4], hi.x[4], lo.y[4], hi.y[4], lo.z[4], hi.z[4]
+//   w[8j+6]    = child refs (int bits): bit 31 = leaf (sorted position),
+//                RT_EMPTY = no child, else a wide node index
+//   w[8j+7]    = unused
+// Empty children and empty leaf boxes are NaN boxes, which no ray hits.
 
 struct rt_bvh {
     int64_t n;
@@ -42,6 +51,8 @@ struct rt_bvh {
     uint64_t *keys;          // [n] sorted keys
     int32_t *parent;         // [2n-1]
     float *bounds;           // [6] device copy of lo, hi
+    float4 *wide;            // [8 * (n-1)] 4-wide nodes (collapsed binary tree)
+    int64_t n_wide;          // number of 4-wide nodes (host copy)
 };
 
 struct rt_envmap {

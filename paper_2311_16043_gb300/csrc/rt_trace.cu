@@ -15,11 +15,13 @@
 
 namespace {
 
-template <bool PACKET, bool COUNT>
+template <int STRAT, bool COUNT>
 __global__ void __launch_bounds__(128) k_trace(BvhDev b, RaySetDev rs, TraceJob job, float *T_out,
                                                TraceAux aux, unsigned long long *work) {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
+    __shared__ int2 stk_all[STRAT == 2 ? 4 * RT_WIDE_STACK : 1];
+    int2 *stk = stk_all + (STRAT == 2 ? (threadIdx.x >> 5) * RT_WIDE_STACK : 0);
     WorkCounts wc = {0, 0, 0};
     unsigned long long rays_done = 0;
     for (;;) {
@@ -33,7 +35,7 @@ __global__ void __launch_bounds__(128) k_trace(BvhDev b, RaySetDev rs, TraceJob 
             n_out = c < n_out ? c : n_out;
             if ((int64_t)item * 32 >= n_out) break;
         }
-        trace_item<PACKET, COUNT>(b, rs, job, T_out, aux, (int64_t)item, n_out, wc, rays_done);
+        trace_item<STRAT, COUNT>(b, rs, job, T_out, aux, (int64_t)item, n_out, wc, rays_done, stk);
     }
     flush_counts<COUNT>(aux, wc, rays_done);
 }
@@ -52,19 +54,22 @@ int persistent_blocks(const void *kernel, int threads) {
 
 // Launch the single-scene kernel on an explicit job (used by the autotuner).
 rt_status rt_trace_launch_job(const BvhDev &b, const RaySetDev &rs, const TraceJob &job, float *T_out,
-                              bool packet, rt_stream_t stream, unsigned long long *work) {
+                              int strat, rt_stream_t stream, unsigned long long *work) {
     TraceAux aux;
     memset(&aux, 0, sizeof(aux));
     aux.status = rt_status_ptr();
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemsetAsync(work, 0, sizeof(unsigned long long), st) != cudaSuccess) return RT_ERR_CUDA;
     const int threads = 128;
-    if (packet) {
-        int grid = persistent_blocks((const void *)k_trace<true, false>, threads);
-        k_trace<true, false><<<grid, threads, 0, st>>>(b, rs, job, T_out, aux, work);
+    if (strat == 2 && b.wide) {
+        int grid = persistent_blocks((const void *)k_trace<2, false>, threads);
+        k_trace<2, false><<<grid, threads, 0, st>>>(b, rs, job, T_out, aux, work);
+    } else if (strat >= 1) {
+        int grid = persistent_blocks((const void *)k_trace<1, false>, threads);
+        k_trace<1, false><<<grid, threads, 0, st>>>(b, rs, job, T_out, aux, work);
     } else {
-        int grid = persistent_blocks((const void *)k_trace<false, false>, threads);
-        k_trace<false, false><<<grid, threads, 0, st>>>(b, rs, job, T_out, aux, work);
+        int grid = persistent_blocks((const void *)k_trace<0, false>, threads);
+        k_trace<0, false><<<grid, threads, 0, st>>>(b, rs, job, T_out, aux, work);
     }
     return rt_check_launch();
 }
@@ -79,7 +84,7 @@ rt_status rt_trace_launch(const rt_bvh *bvh, const rt_rayspec *rays, float *T_ou
     rt_trace_opts o;
     memset(&o, 0, sizeof(o));
     if (opts) o = *opts;
-    if (o.kernel < 0 || o.kernel > 2 || o.order_block < 0 || o.block_threads < 0) return RT_ERR_INVALID_ARG;
+    if (o.kernel < 0 || o.kernel > 3 || o.order_block < 0 || o.block_threads < 0) return RT_ERR_INVALID_ARG;
     if ((o.hit_ids && (o.hit_cap <= 0 || !o.hit_count)) ) return RT_ERR_INVALID_ARG;
     if (count == 0) return RT_OK;
 
@@ -102,7 +107,9 @@ rt_status rt_trace_launch(const rt_bvh *bvh, const rt_rayspec *rays, float *T_ou
     } else {
         job.n_items = (count + 31) / 32;
     }
-    bool packet = o.kernel == RT_KERNEL_PACKET || (o.kernel == RT_KERNEL_AUTO && job.mode == MODE_FULL && rays->kind == RT_RAYS_DIRS);
+    int strat = o.kernel == RT_KERNEL_WIDE ? 2 : o.kernel == RT_KERNEL_PACKET ? 1 : 0;
+    if (o.kernel == RT_KERNEL_AUTO && job.mode == MODE_FULL && rays->kind == RT_RAYS_DIRS) strat = 2;
+    if (strat == 2 && bvh->n_wide == 0) strat = 1;
 
     TraceAux aux;
     aux.counters = (unsigned long long *)o.counters;
@@ -123,13 +130,15 @@ rt_status rt_trace_launch(const rt_bvh *bvh, const rt_rayspec *rays, float *T_ou
     if (res == RT_OK) {
         const int threads = 128;
         const bool count = aux.counters != nullptr;
-        const void *kern = packet ? (count ? (const void *)k_trace<true, true> : (const void *)k_trace<true, false>)
-                                  : (count ? (const void *)k_trace<false, true> : (const void *)k_trace<false, false>);
-        int grid = persistent_blocks(kern, threads);
-        if (packet && count) k_trace<true, true><<<grid, threads, 0, st>>>(b, rs, job, T_out, aux, work);
-        else if (packet) k_trace<true, false><<<grid, threads, 0, st>>>(b, rs, job, T_out, aux, work);
-        else if (count) k_trace<false, true><<<grid, threads, 0, st>>>(b, rs, job, T_out, aux, work);
-        else k_trace<false, false><<<grid, threads, 0, st>>>(b, rs, job, T_out, aux, work);
+#define RT_LAUNCH(S, C)                                                                     \
+    do {                                                                                    \
+        int grid = persistent_blocks((const void *)k_trace<S, C>, threads);                 \
+        k_trace<S, C><<<grid, threads, 0, st>>>(b, rs, job, T_out, aux, work);              \
+    } while (0)
+        if (strat == 2) { if (count) RT_LAUNCH(2, true); else RT_LAUNCH(2, false); }
+        else if (strat == 1) { if (count) RT_LAUNCH(1, true); else RT_LAUNCH(1, false); }
+        else { if (count) RT_LAUNCH(0, true); else RT_LAUNCH(0, false); }
+#undef RT_LAUNCH
         res = rt_check_launch();
     }
     if (own) rt_free(work, stream);
@@ -164,8 +173,8 @@ rt_status rt_trace_launch_list(const rt_bvh *bvh, const rt_rayspec *rays, const 
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemsetAsync(work, 0, sizeof(unsigned long long), st) != cudaSuccess) return RT_ERR_CUDA;
     const int threads = 128;
-    int grid = persistent_blocks((const void *)k_trace<false, false>, threads);
-    k_trace<false, false><<<grid, threads, 0, st>>>(bvh_dev(bvh), rs, job, T_out, aux, work);
+    int grid = persistent_blocks((const void *)k_trace<0, false>, threads);
+    k_trace<0, false><<<grid, threads, 0, st>>>(bvh_dev(bvh), rs, job, T_out, aux, work);
     return rt_check_launch();
 }
 

@@ -7,6 +7,7 @@
 struct BvhDev {
     const float4 *gauss;
     const float4 *nodes;
+    const float4 *wide;  // null if the 4-wide tree is unavailable
     const int32_t *rank;
     int64_t n;
     float k2;         // k_sigma^2
@@ -18,6 +19,7 @@ inline BvhDev bvh_dev(const rt_bvh *b) {
     BvhDev d;
     d.gauss = b->gauss;
     d.nodes = b->nodes;
+    d.wide = b->n_wide > 0 ? b->wide : nullptr;
     d.rank = b->rank;
     d.n = b->n;
     d.k2 = b->params.k_sigma * b->params.k_sigma;
@@ -292,6 +294,99 @@ __device__ __forceinline__ float trace_packet(const BvhDev &b, float3 o, float3 
     return T < b.t_min ? 0.0f : T;
 }
 
+// Strategy 3: warp packet over the 4-wide tree.  As strategy 2, but a visit
+// tests four child boxes per lane (one float4 of each coordinate), evaluates
+// the leaf children each lane hit, and pushes all but one of the internal
+// children some lane still needs onto a warp stack in shared memory.
+template <bool COUNT>
+__device__ __forceinline__ float trace_wide(const BvhDev &b, float3 o, float3 d, int32_t src, bool valid,
+                                            LaneLog &lg, WorkCounts &wc, int *status, int2 *stk) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    float T = 1.0f;
+    if (b.n <= 0) return T;
+    if (b.n == 1) {
+        if (valid) {
+            if (COUNT) wc.gauss++;
+            if (src != 0 && gauss_hit(b, 0, o, d, T)) {
+                if (COUNT) wc.hits++;
+                log_hit(lg, b, 0);
+            }
+        }
+        return T < b.t_min ? 0.0f : T;
+    }
+    const float3 inv = safe_inv(d);
+    const float3 oi = make_float3(o.x * inv.x, o.y * inv.y, o.z * inv.z);
+    uint32_t alive = __ballot_sync(FULL, valid);
+    int sp = 0;
+    uint32_t node = 0, mask = alive;
+    while (mask) {
+        const bool mine = (mask >> lane) & 1u;
+        const float4 *w = b.wide + 8 * (int64_t)node;
+        const float4 lx = __ldg(w), hx = __ldg(w + 1), ly = __ldg(w + 2), hy = __ldg(w + 3), lz = __ldg(w + 4),
+                     hz = __ldg(w + 5), rf = __ldg(w + 6);
+        const uint32_t r0 = __float_as_uint(rf.x), r1 = __float_as_uint(rf.y), r2 = __float_as_uint(rf.z),
+                       r3 = __float_as_uint(rf.w);
+        bool h0 = false, h1 = false, h2 = false, h3 = false;
+        if (mine) {
+            h0 = slab(lx.x, hx.x, ly.x, hy.x, lz.x, hz.x, oi, inv);
+            h1 = slab(lx.y, hx.y, ly.y, hy.y, lz.y, hz.y, oi, inv);
+            h2 = slab(lx.z, hx.z, ly.z, hy.z, lz.z, hz.z, oi, inv);
+            h3 = slab(lx.w, hx.w, ly.w, hy.w, lz.w, hz.w, oi, inv);
+            if (COUNT) wc.box += (r0 != RT_EMPTY) + (r1 != RT_EMPTY) + (r2 != RT_EMPTY) + (r3 != RT_EMPTY);
+        }
+        // leaf children this lane hit, one Gaussian test each
+        uint32_t leaves = ((h0 && (r0 & RT_LEAF_BIT)) ? 1u : 0u) | ((h1 && (r1 & RT_LEAF_BIT)) ? 2u : 0u) |
+                          ((h2 && (r2 & RT_LEAF_BIT)) ? 4u : 0u) | ((h3 && (r3 & RT_LEAF_BIT)) ? 8u : 0u);
+        while (leaves) {
+            const int c = __ffs(leaves) - 1;
+            leaves &= leaves - 1u;
+            const uint32_t r = c == 0 ? r0 : c == 1 ? r1 : c == 2 ? r2 : r3;
+            const int32_t p = (int32_t)(r & ~RT_LEAF_BIT);
+            if (p != src) {
+                if (COUNT) wc.gauss++;
+                if (gauss_hit(b, p, o, d, T)) {
+                    if (COUNT) wc.hits++;
+                    log_hit(lg, b, p);
+                }
+            }
+        }
+        alive = __ballot_sync(FULL, valid && !(T < b.t_min));
+        const uint32_t m0 = (r0 & RT_LEAF_BIT) ? 0u : __ballot_sync(FULL, h0) & alive;
+        const uint32_t m1 = (r1 & RT_LEAF_BIT) ? 0u : __ballot_sync(FULL, h1) & alive;
+        const uint32_t m2 = (r2 & RT_LEAF_BIT) ? 0u : __ballot_sync(FULL, h2) & alive;
+        const uint32_t m3 = (r3 & RT_LEAF_BIT) ? 0u : __ballot_sync(FULL, h3) & alive;
+        uint32_t nn = 0, nm = 0;
+        int npush = 0;
+        int2 push[3];
+        if (m0) { nn = r0; nm = m0; }
+        if (m1) { if (nm) push[npush++] = make_int2((int)r1, (int)m1); else { nn = r1; nm = m1; } }
+        if (m2) { if (nm) push[npush++] = make_int2((int)r2, (int)m2); else { nn = r2; nm = m2; } }
+        if (m3) { if (nm) push[npush++] = make_int2((int)r3, (int)m3); else { nn = r3; nm = m3; } }
+        if (sp + npush > RT_WIDE_STACK) {
+            rt_set_error(status, RT_ERR_STACK_OVERFLOW);
+            break;
+        }
+        if (lane < npush) stk[sp + lane] = lane == 0 ? push[0] : lane == 1 ? push[1] : push[2];
+        sp += npush;
+        __syncwarp();
+        if (nm) {
+            node = nn;
+            mask = nm;
+        } else {
+            mask = 0;
+            while (sp > 0) {
+                const int2 e = stk[--sp];
+                node = (uint32_t)e.x;
+                mask = (uint32_t)e.y & alive;
+                if (mask) break;
+            }
+            __syncwarp();
+        }
+    }
+    return T < b.t_min ? 0.0f : T;
+}
+
 // ---------------------------------------------------------------------------
 // Work items of a trace job
 // ---------------------------------------------------------------------------
@@ -323,10 +418,12 @@ __device__ __forceinline__ void full_item(const TraceJob &job, int32_t K, int64_
 
 // One work item (32 rays) of a trace job: build each lane's ray, traverse,
 // write T (and the hit log).  Shared by the single-scene and batched kernels.
-template <bool PACKET, bool COUNT>
+// STRAT: 0 per-ray binary, 1 packet binary, 2 packet 4-wide (stk: this
+// warp's RT_WIDE_STACK shared-memory entries).
+template <int STRAT, bool COUNT>
 __device__ __forceinline__ void trace_item(const BvhDev &b, const RaySetDev &rs, const TraceJob &job,
                                            float *T_out, const TraceAux &aux, int64_t item, int64_t n_out,
-                                           WorkCounts &wc, unsigned long long &rays_done) {
+                                           WorkCounts &wc, unsigned long long &rays_done, int2 *stk) {
     const int lane = threadIdx.x & 31;
     bool valid = false;
     float3 o = make_float3(0.f, 0.f, 0.f), d = make_float3(0.f, 0.f, 1.f);
@@ -379,7 +476,9 @@ __device__ __forceinline__ void trace_item(const BvhDev &b, const RaySetDev &rs,
     lg.cap = aux.cap;
     lg.count = 0;
     float T;
-    if (PACKET) {
+    if (STRAT == 2) {
+        T = trace_wide<COUNT>(b, o, d, src, valid, lg, wc, aux.status, stk);
+    } else if (STRAT == 1) {
         T = trace_packet<COUNT>(b, o, d, src, valid, lg, wc, aux.status);
     } else {
         T = valid ? trace_ray<COUNT>(b, o, d, src, lg, wc, aux.status) : 1.0f;

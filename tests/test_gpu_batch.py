@@ -30,12 +30,14 @@ def test_batch_equals_single_launches(orc):
         for rs in (rt.rayspec(rt.RT_RAYS_DIRS, dirs=dirs),
                    rt.rayspec(rt.RT_RAYS_ENV, env=E, n_samples=24, seed=399 + s)):
             R = rt.rt_rayspec_count(bvh, rs)
-            ref = rt.rt_trace_visibility(bvh, rs)
             T = torch.full((R,), -1.0, device="cuda")
             jobs.append((bvh, rs, T))
-            refs.append(ref)
         scs.append((sc, bvh))
     batch = rt.rt_batch_create(jobs, autotune=True)
+    info = batch.info()
+    # single launches with each job's chosen strategy give the same T bit for bit
+    for (bvh, rs, T), kernel in zip(jobs, info["kernel"]):
+        refs.append(rt.rt_trace_visibility(bvh, rs, opts=rt.trace_opts(kernel=kernel)))
     for rep in range(2):  # the captured graph replays
         for _, _, T in jobs:
             T.fill_(-1.0)
@@ -44,9 +46,8 @@ def test_batch_equals_single_launches(orc):
         assert rt.rt_status_last() == 0
         for (bvh, rs, T), ref in zip(jobs, refs):
             assert torch.equal(T, ref)
-    info = batch.info()
     assert info["n_rays"] == sum(T.numel() for _, _, T in jobs)
-    assert set(info["kernel"]) <= {1, 2}
+    assert set(info["kernel"]) <= {1, 2, 3}
     # oracle on sampled rays of the largest scene
     sc, bvh = scs[4]
     sel = scenes.sample_ray_ids(20000 * 16, 2000, 5)
@@ -67,8 +68,8 @@ def test_autotune_picks_a_valid_shape():
     rs = rt.rayspec(rt.RT_RAYS_DIRS, dirs=_dev(scenes.fibonacci_sphere(32)))
     T = torch.empty(50000 * 32, device="cuda")
     o = rt.rt_trace_autotune(bvh, rs, T)
-    assert o.kernel in (1, 2) and o.order_block in (1, 16, 128, 1024)
+    assert o.kernel in (1, 2, 3) and o.order_block in (1, 16, 128, 1024)
     a = rt.rt_trace_visibility(bvh, rs, opts=o)
-    b = rt.rt_trace_visibility(bvh, rs)
+    b = rt.rt_trace_visibility(bvh, rs, opts=rt.trace_opts(kernel=1))
     torch.cuda.synchronize()
-    assert torch.equal(a, b)
+    assert (a - b).abs().max().item() <= 1e-6

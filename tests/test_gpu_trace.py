@@ -3,8 +3,10 @@
 Bar: |T_gpu - T_oracle| <= 1e-5 on every ray, except rays the oracle flags as
 having a candidate inside a rounding band of a threshold (m^2 = K^2,
 alpha = 1/255, t* = 0, T = T_min); those are excluded and counted, and must
-stay rare.  The two traversal kernels visit each ray's accepted Gaussians in
-the same order, so they agree bit for bit.
+stay rare.  The per-ray and packet traversals of the binary tree visit each
+ray's accepted Gaussians in the same order, so they agree bit for bit; the
+4-wide traversal visits them in another order (same factors, another product
+rounding).
 """
 import numpy as np
 import pytest
@@ -56,7 +58,7 @@ def small(orc):
     return sc, dirs, ref
 
 
-@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("kernel", [1, 2, 3])
 def test_small_scene_all_rays(small, kernel):
     sc, dirs, ref = small
     bvh = build(sc)
@@ -66,12 +68,52 @@ def test_small_scene_all_rays(small, kernel):
     assert (ref["T"] < 1).mean() > 0.3 and (ref["T"] == 0).any() or (ref["hits"] > 3).any()
 
 
-def test_kernels_agree_bitwise(small):
+def test_kernels_agree(small):
     sc, dirs, _ = small
     bvh = build(sc)
     a = trace_dirs(bvh, dirs, kernel=1)
     b = trace_dirs(bvh, dirs, kernel=2)
+    c = trace_dirs(bvh, dirs, kernel=3)
     np.testing.assert_array_equal(a, b)
+    np.testing.assert_allclose(c, a, atol=1e-6, rtol=0)
+
+
+def test_wide_tree_counts(small):
+    """The 4-wide traversal tests the same leaves as the binary one (every
+    Gaussian whose box the ray enters) and accepts the same hits."""
+    from paper_2311_16043_gb300 import rt
+    sc, dirs, _ = small
+    bvh = build(sc)
+    cnts = []
+    for kernel in (1, 3):
+        cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
+        rs = rt.rayspec(rt.RT_RAYS_DIRS, dirs=_dev(dirs))
+        rt.rt_trace_visibility(bvh, rs, opts=rt.trace_opts(kernel=kernel, counters=cnt))
+        torch.cuda.synchronize()
+        cnts.append(cnt.cpu().numpy())
+    assert cnts[0][3] == cnts[1][3] == 4096 * 32
+    # early termination can stop the two orders at different points: compare
+    # with T_min = 0 below; here only the ray count and a sane ratio
+    assert 0.5 < cnts[1][0] / cnts[0][0] < 3.0
+
+
+def test_wide_tree_same_hits_without_early_exit(small):
+    from paper_2311_16043_gb300 import rt
+    sc, dirs, _ = small
+    bvh = build(sc, t_min=0.0)
+    R = 4096 * 32
+    out = []
+    for kernel in (1, 3):
+        cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
+        hc = torch.zeros(R, dtype=torch.int32, device="cuda")
+        ids = torch.zeros((R, 4), dtype=torch.int32, device="cuda")
+        rs = rt.rayspec(rt.RT_RAYS_DIRS, dirs=_dev(dirs))
+        rt.rt_trace_visibility(bvh, rs, opts=rt.trace_opts(kernel=kernel, counters=cnt, hit_ids=ids, hit_count=hc))
+        torch.cuda.synchronize()
+        out.append((cnt.cpu().numpy(), hc.cpu().numpy()))
+    np.testing.assert_array_equal(out[0][1], out[1][1])  # same accepted hits per ray
+    assert out[0][0][1] == out[1][0][1]  # same Gaussian tests (the leaves whose box a ray enters)
+    assert out[0][0][2] == out[1][0][2]
 
 
 @pytest.mark.parametrize("order_block", [1, 7, 1000])
@@ -118,7 +160,7 @@ def test_explicit_rays_and_counters(orc):
     ref = orc.trace(sc, ro, rd, src)
     bvh = build(sc)
     outs, cnts = [], []
-    for kernel in (1, 2):
+    for kernel in (1, 2, 3):
         cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
         rs = rt.rayspec(rt.RT_RAYS_EXPLICIT, ray_o=_dev(ro), ray_d=_dev(rd), ray_src=_dev(src))
         T = rt.rt_trace_visibility(bvh, rs, opts=rt.trace_opts(kernel=kernel, counters=cnt))
@@ -126,6 +168,7 @@ def test_explicit_rays_and_counters(orc):
         outs.append(T.cpu().numpy().astype(np.float64))
         cnts.append(cnt.cpu().numpy())
     compare(outs[0], ref)
+    compare(outs[2], ref)
     np.testing.assert_array_equal(outs[0], outs[1])
     np.testing.assert_array_equal(cnts[0], cnts[1])
     assert cnts[0][3] == R
@@ -160,7 +203,7 @@ def test_id_subset_matches_full_trace(small):
     from paper_2311_16043_gb300 import rt
     sc, dirs, _ = small
     bvh = build(sc)
-    full = trace_dirs(bvh, dirs).reshape(-1)
+    full = trace_dirs(bvh, dirs, kernel=1).reshape(-1)  # id subsets use the per-ray traversal
     sel = scenes.sample_ray_ids(4096 * 32, 5000, 3)
     rs = rt.rayspec(rt.RT_RAYS_DIRS, dirs=_dev(dirs), ray_ids=_dev(sel))
     T = rt.rt_trace_visibility(bvh, rs)
@@ -202,7 +245,7 @@ def test_tiny_scenes(orc, n):
     ids = np.arange(n * 16, dtype=np.int64)
     o, d, s = orc.dir_rays(sc["mean"], dirs, ids)
     ref = orc.trace(sc, o, d, s)
-    for kernel in (1, 2):
+    for kernel in (1, 2, 3):
         compare(trace_dirs(bvh, dirs, kernel=kernel).reshape(-1), ref, max_excluded=1.0)
 
 
@@ -212,12 +255,13 @@ def test_object_scene_300k_sample(orc):
     sc = scenes.object_scene(300_000, 2)
     dirs = scenes.fibonacci_sphere(128)
     bvh = build(sc)
-    T = trace_dirs(bvh, dirs).reshape(-1)
     sel = scenes.sample_ray_ids(300_000 * 128, 4096, 7)
     o, d, s = orc.dir_rays(sc["mean"], dirs, sel)
     ref = orc.trace(sc, o, d, s)
-    compare(T[sel], ref, max_excluded=0.01)
-    assert np.all((T >= 0) & (T <= 1))
+    for kernel in (1, 3):
+        T = trace_dirs(bvh, dirs, kernel=kernel).reshape(-1)
+        compare(T[sel], ref, max_excluded=0.01)
+        assert np.all((T >= 0) & (T <= 1))
 
 
 def test_env_rays(orc):
