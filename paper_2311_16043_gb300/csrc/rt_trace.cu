@@ -13,10 +13,15 @@
 
 #include "rt_trace_core.cuh"
 
+// Resident blocks per SM the trace kernels are compiled for (register cap).
+#ifndef RT_TRACE_MIN_BLOCKS
+#define RT_TRACE_MIN_BLOCKS 1
+#endif
+
 namespace {
 
 template <int STRAT, bool COUNT>
-__global__ void __launch_bounds__(128) k_trace(BvhDev b, RaySetDev rs, TraceJob job, float *T_out,
+__global__ void __launch_bounds__(128, RT_TRACE_MIN_BLOCKS) k_trace(BvhDev b, RaySetDev rs, TraceJob job, float *T_out,
                                                TraceAux aux, unsigned long long *work) {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
