@@ -15,7 +15,7 @@
 
 // Resident blocks per SM the trace kernels are compiled for (register cap).
 #ifndef RT_TRACE_MIN_BLOCKS
-#define RT_TRACE_MIN_BLOCKS 1
+#define RT_TRACE_MIN_BLOCKS 8
 #endif
 
 namespace {
