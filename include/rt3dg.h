@@ -305,6 +305,22 @@ rt_status rt_surrogate_train(rt_surrogate *s, const rt_bvh *bvh, const rt_rayspe
 rt_status rt_surrogate_infer(const rt_surrogate *s, const rt_bvh *bvh, const rt_rayspec *rays,
                              float band, float *T_out, int64_t *n_fallback, rt_stream_t stream);
 
+/* rt_surrogate_infer without any device allocation during the call (the paper
+ * has no counterpart).  For callers that may not let a library allocate
+ * device memory mid-call: engines that reserve the whole device budget up
+ * front and forbid allocation in their frame loop, or hosts whose device
+ * memory belongs to another runtime's allocator.  The fallback lists and
+ * counters live in a fixed 16 MiB + 256 B array inside the library, reserved
+ * on every device that loads it until the process exits.  Same arguments and
+ * results as rt_surrogate_infer; at most 1,048,576 rays per call (more:
+ * RT_ERR_INVALID_ARG before anything is enqueued).  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  All calls share the array and
+ * it keeps the previous call's contents (the call clears its counter itself):
+ * calls that overlap on the GPU (other streams, other threads) race. */
+rt_status rt_surrogate_infer_noalloc(const rt_surrogate *s, const rt_bvh *bvh, const rt_rayspec *rays,
+                                     float band, float *T_out, int64_t *n_fallback, rt_stream_t stream);
+
 /* ------------------------------------------------------------------------ */
 /* Autotuning and multi-scene batches (not in the paper)                      */
 /* ------------------------------------------------------------------------ */

@@ -27,6 +27,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "rt_tc.cuh"
 #include "rt_trace_core.cuh"
 
@@ -945,4 +947,87 @@ extern "C" rt_status rt_surrogate_infer(const rt_surrogate *s, const rt_bvh *bvh
     }
     if (fb) rt_free(fb, stream);
     return r;
+}
+
+// ---------------------------------------------------------------------------
+// Inference without device allocation
+// ---------------------------------------------------------------------------
+// Some callers cannot let a library allocate device memory during a call:
+// engines that reserve the whole device budget up front and forbid
+// allocation inside their frame loop, and hosts whose device memory is owned
+// by another runtime's allocator.  For them the fallback lists and counters of
+// rt_surrogate_infer live in a fixed array that is part of the library image
+// (reserved on every device that loads the library, until the process exits).
+namespace {
+
+constexpr int64_t kNoAllocMaxRays = 1 << 20;
+// [0, M): fallback ray ids, [M, 2M): their output positions, then the fallback
+// count and the trace work counter (M = kNoAllocMaxRays): 16 MiB + 256 B.
+static __device__ __align__(256) int64_t g_noalloc_scratch[2 * kNoAllocMaxRays + 32];
+
+std::mutex g_noalloc_mu;
+int64_t *g_noalloc_ptr[64] = {nullptr};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (the host-side symbol is only a stand-in, never a device address).
+rt_status noalloc_scratch(int64_t **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return RT_ERR_CUDA;
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return RT_ERR_CUDA;
+        }
+        g_noalloc_ptr[dev] = (int64_t *)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return RT_OK;
+}
+
+}  // namespace
+
+extern "C" rt_status rt_surrogate_infer_noalloc(const rt_surrogate *s, const rt_bvh *bvh, const rt_rayspec *rays,
+                                                float band, float *T_out, int64_t *n_fallback,
+                                                rt_stream_t stream) {
+    if (!s || !bvh || !rays || !(band >= 0.f && band <= 0.5f)) return RT_ERR_INVALID_ARG;
+    if (rays->kind == RT_RAYS_EXPLICIT) return RT_ERR_UNSUPPORTED;
+    RaySetDev rs;
+    int64_t m = 0;
+    RT_TRY(rt_rayset_dev(bvh, rays, &rs, &m));
+    if (m > kNoAllocMaxRays) return RT_ERR_INVALID_ARG;  // beyond the fixed scratch capacity
+    if (m == 0) return RT_OK;
+    if (!T_out) return RT_ERR_INVALID_ARG;
+    int64_t *scratch = nullptr;
+    RT_TRY(noalloc_scratch(&scratch));
+    RT_TRY(set_smem_attrs());
+    cudaStream_t st = (cudaStream_t)stream;
+    int64_t *fb_rid = scratch;
+    int64_t *fb_pos = scratch + kNoAllocMaxRays;
+    unsigned long long *fb_count = (unsigned long long *)(scratch + 2 * kNoAllocMaxRays);
+    unsigned long long *work = fb_count + 4;
+    const bool use_fb = band > 0.f;
+    // the array keeps the previous call's contents: the count must start at 0
+    if (use_fb && cudaMemsetAsync(fb_count, 0, sizeof(unsigned long long), st) != cudaSuccess) return RT_ERR_CUDA;
+    SampleSrc S;
+    memset(&S, 0, sizeof(S));
+    S.mode = 1;
+    S.b = bvh_dev(bvh);
+    S.rs = rs;
+    S.R = rs.n_rays;
+    int64_t ntiles = (m + 127) / 128;
+    int grid = (int)(ntiles < rt_num_sms() ? ntiles : rt_num_sms());
+    k_mlp_infer<<<grid, 128, INF_SMEM_TOTAL, st>>>(mlp_dev(s), S, m, T_out, band, use_fb ? fb_rid : nullptr,
+                                                   use_fb ? fb_pos : nullptr, use_fb ? fb_count : nullptr,
+                                                   rt_status_ptr());
+    RT_TRY(rt_check_launch());
+    if (use_fb) {
+        RT_TRY(rt_trace_launch_list(bvh, rays, fb_rid, fb_pos, fb_count, m, T_out, stream, work));
+        if (n_fallback && cudaMemcpyAsync(n_fallback, fb_count, 8, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return RT_ERR_CUDA;
+    } else if (n_fallback && cudaMemsetAsync(n_fallback, 0, 8, st) != cudaSuccess) {
+        return RT_ERR_CUDA;
+    }
+    return RT_OK;
 }

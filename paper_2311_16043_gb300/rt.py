@@ -94,6 +94,7 @@ _SIGS = {
     "rt_surrogate_loss_grad": (_I32, [_P, _P, _P, _P, _I64, _P, _P, _P]),
     "rt_surrogate_train": (_I32, [_P, _P, _P, _P, _I32, _U64, _P, _P]),
     "rt_surrogate_infer": (_I32, [_P, _P, _P, _F32, _P, _P, _P]),
+    "rt_surrogate_infer_noalloc": (_I32, [_P, _P, _P, _F32, _P, _P, _P]),
     "rt_trace_autotune": (_I32, [_P, _P, _P, _P, _P]),
     "rt_batch_create": (_I32, [_P, _I32, _I32, _P, _P]),
     "rt_batch_run": (_I32, [_P, _P]),
@@ -501,3 +502,14 @@ def rt_batch_create(jobs, autotune: bool = True, stream=None) -> Batch:
     _check(lib().rt_batch_create(arr, len(jobs), 1 if autotune else 0, _stream(stream), C.byref(h)),
            "rt_batch_create")
     return Batch(h, len(jobs), [j for j in jobs])
+
+
+def rt_surrogate_infer_noalloc(s: Surrogate, bvh: Bvh, rs: rt_rayspec, band: float, T_out, n_fallback=None,
+                               stream=None):
+    """rt_surrogate_infer without device allocation in the library: the
+    caller provides T_out (and n_fallback); at most 2**20 rays per call."""
+    _check(lib().rt_surrogate_infer_noalloc(s.handle, bvh.handle, C.byref(rs), band,
+                                            _ptr(T_out, torch.float32, "T_out"),
+                                            _ptr(n_fallback, torch.int64, "n_fallback"), _stream(stream)),
+           "rt_surrogate_infer_noalloc")
+    return T_out
