@@ -41,7 +41,11 @@ WORKLOADS = {
     "object_2m_k128": ("object", 2_000_000, 2, 128),
     "object_300k_k128": ("object", 300_000, 2, 128),
     "uniform_4k_k32": ("uniform", 4096, 1, 32),
+    # 16 uniform scenes (log-uniform sizes, ~8M Gaussians), 128 directions +
+    # 512 env-map shadow rays per Gaussian, one graph-captured launch
+    "batch16_k128_env512": ("batch", 8_000_000, 300, 128),
 }
+ENV_SAMPLES = 512
 METRIC = "traced rays/s & ms per 2M-Gaussian visibility precompute; surrogate speedup at MAE"
 TRACE_SOURCES = ["paper_2311_16043_gb300/csrc/rt_trace.cu", "paper_2311_16043_gb300/csrc/rt_trace_core.cuh"]
 BUILD_KERNELS_PER_STEP = 18  # bounds, morton, 4 x (hist, scan, scatter), perm, prep, karras, refit
@@ -68,12 +72,22 @@ def parse():
 def make_scene(name):
     import scenes
     gen, n, seed, K = WORKLOADS[name]
+    if gen == "batch":
+        return scenes.batch_scenes(scenes.batch_scene_sizes(16, n, seed), seed_base=seed), scenes.fibonacci_sphere(K)
     sc = scenes.object_scene(n, seed) if gen == "object" else scenes.uniform_scene(n, seed)
     return sc, scenes.fibonacci_sphere(K)
 
 
 def workload_config(name, extra=None):
     gen, n, seed, K = WORKLOADS[name]
+    if gen == "batch":
+        cfg = {"workload": name, "scenes": 16, "gaussians": n, "directions": K, "env_samples": ENV_SAMPLES,
+               "rays_per_step": None, "scene": "16 uniform scenes, log-uniform sizes in [50k, 2M]",
+               "seed": seed, "step": "one replay of the graph-captured persistent launch over all scenes",
+               "l2": "outputs > L2 (T tables ~20 GB)"}
+        if extra:
+            cfg.update(extra)
+        return cfg
     cfg = {"workload": name, "gaussians": n, "directions": K, "rays_per_step": n * K,
            "scene": "object-scale: 2 spheres, torus, box, ground plane" if gen == "object"
            else "uniform cube", "seed": seed,
@@ -235,10 +249,76 @@ def run_surrogate(args, rt, torch, d, dirs, T, prm, dev):
     return out
 
 
+def run_batch(args, rank, world, local, torch, dist, rt):
+    """Batched multi-scene workload: every scene's BVH is built, then one
+    graph-captured persistent launch traces all scenes' direction and
+    env-map rays; a step is one replay of that graph."""
+    import scenes
+    dev = torch.device("cuda", local)
+    scs, dirs_np = make_scene(args.workload)
+    env = scenes.envmap(399)
+    E = rt.rt_envmap_create(env["radiance"], env["solid_angle"], env["corners"])
+    dirs = torch.from_numpy(dirs_np).to(dev)
+    jobs, bvhs, build_ms = [], [], 0.0
+    for s_idx, sc in enumerate(scs):
+        d = {k: torch.from_numpy(v).to(dev) for k, v in sc.items()}
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        bvh = rt.rt_build_bvh(d["mean"], d["scale"], d["quat"], d["opacity"], rt.params())
+        e1.record()
+        torch.cuda.synchronize()
+        build_ms += e0.elapsed_time(e1)
+        bvhs.append((bvh, d))
+        for rs in (rt.rayspec(rt.RT_RAYS_DIRS, dirs=dirs),
+                   rt.rayspec(rt.RT_RAYS_ENV, env=E, n_samples=ENV_SAMPLES, seed=399 + s_idx)):
+            jobs.append((bvh, rs, torch.empty(rt.rt_rayspec_count(bvh, rs), dtype=torch.float32, device=dev)))
+    t0 = time.perf_counter()
+    batch = rt.rt_batch_create(jobs, autotune=True)
+    create_s = time.perf_counter() - t0
+    info = batch.info()
+    R = info["n_rays"]
+    for _ in range(args.warmup):
+        batch.run()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms = []
+    for i in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        batch.run()
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    clk = clocks.stop()
+    m = statistics.mean(ms)
+    if world > 1:
+        t = torch.tensor([m], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        m = float(t.item())
+    if rank == 0:
+        line = {"metric": METRIC, "value": world * R / (m / 1000.0), "unit": "rays/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": m, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": workload_config(args.workload, {
+                    "rays_per_step": R, "work_items": info["n_items"], "build_ms_all_scenes": build_ms,
+                    "batch_create_s": create_s, "strategy_per_job": info["kernel"],
+                    "order_block_per_job": info["order_block"],
+                    "scene_sizes": [b.n for b, _ in bvhs]}),
+                "cpu_baseline": None, "e2e": None, "gpu_launches": args.steps, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    batch.destroy()
+    E.destroy()
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
     sc, dirs = make_scene(args.workload)
+    if isinstance(sc, list):  # batched scenes: sample rays of the largest scene
+        sc = max(sc, key=lambda x: x["mean"].shape[0])
     n, K = sc["mean"].shape[0], dirs.shape[0]
     m = max(32, min(args.cpu_rays, int(4e8 // max(n, 1))))  # ~4e8 ray-Gaussian tests per step
     rates = []
@@ -275,6 +355,9 @@ def main():
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if WORKLOADS[args.workload][0] == "batch":
+        run_batch(args, rank, world, local, torch, dist, rt)
+        return
 
     def barrier():
         if world > 1:

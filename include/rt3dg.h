@@ -173,8 +173,9 @@ typedef enum {
     RT_KERNEL_RAY = 1,    /* one thread per ray, private stack, binary tree    */
     RT_KERNEL_PACKET = 2, /* one warp per 32 rays of neighbouring Gaussians in
                              one direction, shared stack, binary tree          */
-    RT_KERNEL_WIDE = 3    /* as PACKET over the 4-wide tree (the binary tree
+    RT_KERNEL_WIDE = 3,   /* as PACKET over the 4-wide tree (the binary tree
                              collapsed by greedy largest-area expansion)       */
+    RT_KERNEL_RAY_WIDE = 4 /* one thread per ray over the 4-wide tree         */
 } rt_kernel;
 
 typedef struct {
@@ -327,8 +328,8 @@ rt_status rt_surrogate_infer_noalloc(const rt_surrogate *s, const rt_bvh *bvh, c
 
 /* Picks the traversal strategy (rt_kernel) and the work order (order_block)
  * for a full implicit ray set (DIRS or ENV, no ray_ids) over `bvh`: each
- * candidate traces the same contiguous block of up to 1024 tiles of 32
- * Gaussians (all directions), timed with CUDA events; the fastest is written
+ * candidate traces the same contiguous block of tiles of 32 Gaussians (all
+ * directions; about 2M rays), timed with CUDA events; the fastest is written
  * into opts->kernel and opts->order_block (other fields untouched).  Results
  * are cached in-process per (device, log2 n, ray kind, K).  T_scratch must
  * hold rt_rayspec_count(bvh, rays) floats.  Synchronises `stream`. */

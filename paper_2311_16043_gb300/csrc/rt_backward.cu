@@ -23,10 +23,12 @@ struct GradOut {
     const float *mean, *scale, *quat, *opacity;
 };
 
-// Peak evaluation returning alpha and e = x(t*) - mu (same arithmetic as
-// gauss_hit).
-__device__ __forceinline__ bool gauss_eval(const BvhDev &b, int32_t p, float3 o, float3 d,
-                                           float &alpha, float3 &e) {
+// Peak point for the gradient: e = x(t*) - mu and alpha with IEEE division
+// and exponential.  dm^2/dmu = -2 Sigma^-1 e is first order in e, so t* must
+// be accurate here (the forward's accept decision tolerates a fast
+// reciprocal because m^2 itself is stationary in t).
+__device__ __forceinline__ void peak_accurate(const BvhDev &b, int32_t p, float3 o, float3 d, float &alpha,
+                                              float3 &e) {
     const float4 g0 = __ldg(b.gauss + 4 * p);
     const float4 g1 = __ldg(b.gauss + 4 * p + 1);
     const float4 g2 = __ldg(b.gauss + 4 * p + 2);
@@ -42,13 +44,9 @@ __device__ __forceinline__ bool gauss_eval(const BvhDev &b, int32_t p, float3 o,
     const float3 ud = make_float3(dot3(w0, d), dot3(w1, d), dot3(w2, d));
     const float3 uo = make_float3(dot3(w0, dh), dot3(w1, dh), dot3(w2, dh));
     const float t = -dot3(uo, ud) / dot3(ud, ud);
-    if (!(t > 0.0f)) return false;
     e = make_float3(fmaf(t, d.x, hx) + lx, fmaf(t, d.y, hy) + ly, fmaf(t, d.z, hz) + lz);
     const float3 u = make_float3(dot3(w0, e), dot3(w1, e), dot3(w2, e));
-    const float m2 = dot3(u, u);
-    if (!(m2 <= b.k2)) return false;
-    alpha = g0.w * expf(-0.5f * m2);
-    return alpha >= b.alpha_min;
+    alpha = g0.w * expf(-0.5f * dot3(u, u));
 }
 
 // Gradient contribution of one accepted hit (Gaussian with original index i).
@@ -134,18 +132,21 @@ __global__ void __launch_bounds__(128) k_backward(BvhDev b, RaySetDev rs, int64_
         if (live) {
             const int32_t cnt = hit_count ? hit_count[r] : -1;
             if (hit_ids && cnt >= 0 && cnt <= cap) {
-                for (int32_t h = 0; h < cnt; ++h) {
+                for (int32_t h = 0; h < cnt; ++h) {  // the forward accepted these: no re-check
                     const int32_t i = hit_ids[r * (int64_t)cap + h];
                     const int32_t p = b.rank[i];
                     float alpha;
                     float3 e;
-                    if (gauss_eval(b, p, o, d, alpha, e)) hit_grad(G, i, gT, Tr, alpha, e, d_origin);
+                    peak_accurate(b, p, o, d, alpha, e);
+                    hit_grad(G, i, gT, Tr, alpha, e, d_origin);
                 }
             } else if (b.n == 1) {
                 float alpha;
                 float3 e;
-                if (src != 0 && gauss_eval(b, 0, o, d, alpha, e))
+                if (src != 0 && gauss_eval(b, 0, o, d, alpha, e)) {
+                    peak_accurate(b, 0, o, d, alpha, e);
                     hit_grad(G, __float_as_int(__ldg(b.gauss + 1).w), gT, Tr, alpha, e, d_origin);
+                }
             } else if (b.n > 1) {
                 const float3 inv = safe_inv(d);
                 const float3 oi = make_float3(o.x * inv.x, o.y * inv.y, o.z * inv.z);
@@ -168,9 +169,11 @@ __global__ void __launch_bounds__(128) k_backward(BvhDev b, RaySetDev rs, int64_
                             const int32_t p = (int32_t)(ch[c] & ~RT_LEAF_BIT);
                             float alpha;
                             float3 e;
-                            if (p != src && gauss_eval(b, p, o, d, alpha, e))
+                            if (p != src && gauss_eval(b, p, o, d, alpha, e)) {  // the forward's decision
+                                peak_accurate(b, p, o, d, alpha, e);
                                 hit_grad(G, __float_as_int(__ldg(b.gauss + 4 * p + 1).w), gT, Tr, alpha, e,
                                          d_origin);
+                            }
                         }
                     }
                     if (hit2[0] && hit2[1]) {

@@ -58,7 +58,7 @@ struct BatchJobDev {
     RaySetDev rs;
     TraceJob job;
     float *T_out;
-    int32_t strat;  // 0 per-ray, 1 packet, 2 4-wide packet
+    int32_t strat;  // 0 per-ray, 1 packet, 2 4-wide packet, 3 4-wide packet with a shared direction, 4 per-ray 4-wide
     int64_t item_begin;
 };
 
@@ -90,7 +90,9 @@ __global__ void __launch_bounds__(128) k_trace_batch(const BatchJobDev *__restri
         }
         const BatchJobDev &J = jobs[lo];
         const int64_t local = (int64_t)item - J.item_begin;
-        if (J.strat == 2) trace_item<2, false>(J.b, J.rs, J.job, J.T_out, aux, local, J.job.n_out, wc, rays_done, stk);
+        if (J.strat == 4) trace_item<4, false>(J.b, J.rs, J.job, J.T_out, aux, local, J.job.n_out, wc, rays_done, stk);
+        else if (J.strat == 3) trace_item<3, false>(J.b, J.rs, J.job, J.T_out, aux, local, J.job.n_out, wc, rays_done, stk);
+        else if (J.strat == 2) trace_item<2, false>(J.b, J.rs, J.job, J.T_out, aux, local, J.job.n_out, wc, rays_done, stk);
         else if (J.strat == 1) trace_item<1, false>(J.b, J.rs, J.job, J.T_out, aux, local, J.job.n_out, wc, rays_done, stk);
         else trace_item<0, false>(J.b, J.rs, J.job, J.T_out, aux, local, J.job.n_out, wc, rays_done, stk);
     }
@@ -134,7 +136,10 @@ extern "C" rt_status rt_trace_autotune(const rt_bvh *bvh, const rt_rayspec *rays
     RT_TRY(rt_alloc((void **)&work, 8, stream));
     const BvhDev b = bvh_dev(bvh);
     const int64_t ntiles = (bvh->n + 31) / 32;
-    const int64_t S = ntiles < 1024 ? ntiles : 1024;
+    // about 2M rays per candidate: a contiguous block of tiles, all directions
+    int64_t S = (2ll << 20) / (32ll * rs.K);
+    if (S < 16) S = 16;
+    if (S > ntiles) S = ntiles;
     const int64_t base = (ntiles - S) / 2;
     const int blocks[] = {1, 16, 128, 1024};
     cudaEvent_t e0, e1;
@@ -143,9 +148,11 @@ extern "C" rt_status rt_trace_autotune(const rt_bvh *bvh, const rt_rayspec *rays
     float best = 1e30f;
     int best_k = RT_KERNEL_PACKET, best_b = 1;
     rt_status res = RT_OK;
-    for (int kernel = RT_KERNEL_RAY; kernel <= RT_KERNEL_WIDE && res == RT_OK; ++kernel) {
-        if (kernel == RT_KERNEL_WIDE && bvh->n_wide == 0) continue;
-        for (int bi = 0; bi < 4 && res == RT_OK; ++bi) {
+    for (int kernel = RT_KERNEL_RAY; kernel <= RT_KERNEL_RAY_WIDE && res == RT_OK; ++kernel) {
+        if ((kernel == RT_KERNEL_WIDE || kernel == RT_KERNEL_RAY_WIDE) && bvh->n_wide == 0) continue;
+        // order_block only changes which rays share a warp for the packet strategies
+        const int n_blocks = (kernel == RT_KERNEL_PACKET || kernel == RT_KERNEL_WIDE) ? 4 : 1;
+        for (int bi = 0; bi < n_blocks && res == RT_OK; ++bi) {
             TraceJob job = full_job(bvh, rs.K, blocks[bi]);
             job.n_tiles = S;
             job.tile_base = base;
@@ -154,7 +161,8 @@ extern "C" rt_status rt_trace_autotune(const rt_bvh *bvh, const rt_rayspec *rays
             float ms = 0.f;
             for (int rep = 0; rep < 2 && res == RT_OK; ++rep) {  // first run warms caches
                 cudaEventRecord(e0, st);
-                res = rt_trace_launch_job(b, rs, job, T_scratch, kernel - 1, stream, work);
+                const int strat = kernel == RT_KERNEL_RAY_WIDE ? 4 : kernel - 1;
+                res = rt_trace_launch_job(b, rs, job, T_scratch, strat, stream, work);
                 cudaEventRecord(e1, st);
                 if (cudaEventSynchronize(e1) != cudaSuccess) res = RT_ERR_CUDA;
                 cudaEventElapsedTime(&ms, e0, e1);
@@ -214,7 +222,8 @@ extern "C" rt_status rt_batch_create(const rt_batch_job *jobs, int32_t n_jobs, i
         }
         rt_trace_opts o;
         memset(&o, 0, sizeof(o));
-        o.kernel = J.rays.kind == RT_RAYS_DIRS ? (J.bvh->n_wide > 0 ? RT_KERNEL_WIDE : RT_KERNEL_PACKET) : RT_KERNEL_RAY;
+        o.kernel = J.rays.kind == RT_RAYS_DIRS ? (J.bvh->n_wide > 0 ? RT_KERNEL_WIDE : RT_KERNEL_PACKET)
+                                               : (J.bvh->n_wide > 0 ? RT_KERNEL_RAY_WIDE : RT_KERNEL_RAY);
         o.order_block = 64;
         if (autotune && count > 0) {
             r = rt_trace_autotune(J.bvh, &J.rays, J.T_out, &o, stream);
@@ -231,7 +240,9 @@ extern "C" rt_status rt_batch_create(const rt_batch_job *jobs, int32_t n_jobs, i
         H.rs = rs;
         H.job = full_job(J.bvh, rs.K, o.order_block);
         H.T_out = J.T_out;
-        H.strat = o.kernel == RT_KERNEL_WIDE ? (J.bvh->n_wide > 0 ? 2 : 1) : o.kernel == RT_KERNEL_PACKET ? 1 : 0;
+        H.strat = o.kernel == RT_KERNEL_RAY_WIDE ? (J.bvh->n_wide > 0 ? 4 : 0)
+                  : o.kernel == RT_KERNEL_WIDE ? (J.bvh->n_wide > 0 ? (J.rays.kind == RT_RAYS_DIRS ? 3 : 2) : 1)
+                  : o.kernel == RT_KERNEL_PACKET ? 1 : 0;
         cost[j] = (double)count * log2((double)(J.bvh->n > 1 ? J.bvh->n : 2));
     }
     // largest estimated cost first

@@ -25,8 +25,8 @@ __global__ void __launch_bounds__(128, RT_TRACE_MIN_BLOCKS) k_trace(BvhDev b, Ra
                                                TraceAux aux, unsigned long long *work) {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    __shared__ int2 stk_all[STRAT == 2 ? 4 * RT_WIDE_STACK : 1];
-    int2 *stk = stk_all + (STRAT == 2 ? (threadIdx.x >> 5) * RT_WIDE_STACK : 0);
+    __shared__ int2 stk_all[(STRAT == 2 || STRAT == 3) ? 4 * RT_WIDE_STACK : 1];
+    int2 *stk = stk_all + ((STRAT == 2 || STRAT == 3) ? (threadIdx.x >> 5) * RT_WIDE_STACK : 0);
     WorkCounts wc = {0, 0, 0};
     unsigned long long rays_done = 0;
     for (;;) {
@@ -66,9 +66,20 @@ rt_status rt_trace_launch_job(const BvhDev &b, const RaySetDev &rs, const TraceJ
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemsetAsync(work, 0, sizeof(unsigned long long), st) != cudaSuccess) return RT_ERR_CUDA;
     const int threads = 128;
-    if (strat == 2 && b.wide) {
-        int grid = persistent_blocks((const void *)k_trace<2, false>, threads);
-        k_trace<2, false><<<grid, threads, 0, st>>>(b, rs, job, T_out, aux, work);
+    if (strat == 4 && b.wide) {
+        int grid = persistent_blocks((const void *)k_trace<4, false>, threads);
+        k_trace<4, false><<<grid, threads, 0, st>>>(b, rs, job, T_out, aux, work);
+    } else if (strat == 4) {
+        int grid = persistent_blocks((const void *)k_trace<0, false>, threads);
+        k_trace<0, false><<<grid, threads, 0, st>>>(b, rs, job, T_out, aux, work);
+    } else if (strat >= 2 && b.wide) {
+        if (job.mode == MODE_FULL && rs.kind == RT_RAYS_DIRS) {
+            int grid = persistent_blocks((const void *)k_trace<3, false>, threads);
+            k_trace<3, false><<<grid, threads, 0, st>>>(b, rs, job, T_out, aux, work);
+        } else {
+            int grid = persistent_blocks((const void *)k_trace<2, false>, threads);
+            k_trace<2, false><<<grid, threads, 0, st>>>(b, rs, job, T_out, aux, work);
+        }
     } else if (strat >= 1) {
         int grid = persistent_blocks((const void *)k_trace<1, false>, threads);
         k_trace<1, false><<<grid, threads, 0, st>>>(b, rs, job, T_out, aux, work);
@@ -89,7 +100,7 @@ rt_status rt_trace_launch(const rt_bvh *bvh, const rt_rayspec *rays, float *T_ou
     rt_trace_opts o;
     memset(&o, 0, sizeof(o));
     if (opts) o = *opts;
-    if (o.kernel < 0 || o.kernel > 3 || o.order_block < 0 || o.block_threads < 0) return RT_ERR_INVALID_ARG;
+    if (o.kernel < 0 || o.kernel > 4 || o.order_block < 0 || o.block_threads < 0) return RT_ERR_INVALID_ARG;
     if ((o.hit_ids && (o.hit_cap <= 0 || !o.hit_count)) ) return RT_ERR_INVALID_ARG;
     if (count == 0) return RT_OK;
 
@@ -112,9 +123,11 @@ rt_status rt_trace_launch(const rt_bvh *bvh, const rt_rayspec *rays, float *T_ou
     } else {
         job.n_items = (count + 31) / 32;
     }
-    int strat = o.kernel == RT_KERNEL_WIDE ? 2 : o.kernel == RT_KERNEL_PACKET ? 1 : 0;
-    if (o.kernel == RT_KERNEL_AUTO && job.mode == MODE_FULL && rays->kind == RT_RAYS_DIRS) strat = 2;
+    int strat = o.kernel == RT_KERNEL_RAY_WIDE ? 4 : o.kernel == RT_KERNEL_WIDE ? 2 : o.kernel == RT_KERNEL_PACKET ? 1 : 0;
+    if (o.kernel == RT_KERNEL_AUTO && job.mode == MODE_FULL) strat = rays->kind == RT_RAYS_DIRS ? 2 : 4;
     if (strat == 2 && bvh->n_wide == 0) strat = 1;
+    if (strat == 4 && bvh->n_wide == 0) strat = 0;
+    if (strat == 2 && job.mode == MODE_FULL && rays->kind == RT_RAYS_DIRS) strat = 3;  // shared direction
 
     TraceAux aux;
     aux.counters = (unsigned long long *)o.counters;
@@ -140,7 +153,9 @@ rt_status rt_trace_launch(const rt_bvh *bvh, const rt_rayspec *rays, float *T_ou
         int grid = persistent_blocks((const void *)k_trace<S, C>, threads);                 \
         k_trace<S, C><<<grid, threads, 0, st>>>(b, rs, job, T_out, aux, work);              \
     } while (0)
-        if (strat == 2) { if (count) RT_LAUNCH(2, true); else RT_LAUNCH(2, false); }
+        if (strat == 4) { if (count) RT_LAUNCH(4, true); else RT_LAUNCH(4, false); }
+        else if (strat == 3) { if (count) RT_LAUNCH(3, true); else RT_LAUNCH(3, false); }
+        else if (strat == 2) { if (count) RT_LAUNCH(2, true); else RT_LAUNCH(2, false); }
         else if (strat == 1) { if (count) RT_LAUNCH(1, true); else RT_LAUNCH(1, false); }
         else { if (count) RT_LAUNCH(0, true); else RT_LAUNCH(0, false); }
 #undef RT_LAUNCH

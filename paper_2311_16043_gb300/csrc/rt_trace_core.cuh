@@ -67,18 +67,30 @@ __device__ __forceinline__ bool slab(float lox, float hix, float loy, float hiy,
     return tnear <= fmaf(fabsf(tfar), 1e-6f, tfar);
 }
 
+// Slab test with the planes already ordered along the ray (near plane first
+// on every axis): same result as slab() without the per-axis min/max.
+__device__ __forceinline__ bool slab_sorted(float nx, float fx, float ny, float fy, float nz, float fz,
+                                            float3 oi, float3 inv) {
+    const float tnear = fmaxf(fmaxf(fmaf(nx, inv.x, -oi.x), fmaf(ny, inv.y, -oi.y)),
+                              fmaxf(fmaf(nz, inv.z, -oi.z), 0.0f));
+    const float tfar = fminf(fminf(fmaf(fx, inv.x, -oi.x), fmaf(fy, inv.y, -oi.y)), fmaf(fz, inv.z, -oi.z));
+    return tnear <= fmaf(fabsf(tfar), 1e-6f, tfar);
+}
+
 // Peak response of the Gaussian at sorted position p along the ray
-// (Eq. 13-14 with Sigma^-1) and the transmittance update (Eq. 15).
-// In the whitened frame u = W (x - mu) the squared Mahalanobis distance along
-// the ray is |u_o + t u_d|^2, minimised at t* = -(u_o . u_d)/(u_d . u_d).
+// (Eq. 13-14 with Sigma^-1).  In the whitened frame u = W (x - mu) the squared
+// Mahalanobis distance along the ray is |u_o + t u_d|^2, minimised at
+// t* = -(u_o . u_d)/(u_d . u_d).
 // Accuracy: o - mu is split exactly into hi + lo; the point e = x(t*) - mu is
 // rebuilt in world space as fma(t*, d, hi) + lo (it is small, so this has no
-// cancellation), and m^2 = |W e|^2.  Since m^2 is stationary at t*, the
-// rounding of t* enters m^2 only at second order.
-// Returns true if the Gaussian is accepted (t* > 0, m^2 <= K^2,
-// alpha >= alpha_min) and multiplies T by (1 - alpha).
-__device__ __forceinline__ bool gauss_hit(const BvhDev &b, int32_t p, float3 o, float3 d, float &T,
-                                          float *alpha_out = nullptr) {
+// cancellation), and m^2 = |W e|^2.  m^2 is stationary at t*, so t* needs only
+// a fast reciprocal (its relative error ~1e-7 enters m^2 squared; its sign is
+// exact); alpha = o exp(-m^2/2) uses the fast exponential (relative error
+// ~4e-7).  Returns true if the Gaussian is accepted (t* > 0, m^2 <= K^2,
+// alpha >= alpha_min), with alpha and e.  The forward and the adjoint both use
+// this routine, so they make the same decisions.
+__device__ __forceinline__ bool gauss_eval(const BvhDev &b, int32_t p, float3 o, float3 d, float &alpha,
+                                           float3 &e) {
     const float4 g0 = __ldg(b.gauss + 4 * p);
     const float4 g1 = __ldg(b.gauss + 4 * p + 1);
     const float4 g2 = __ldg(b.gauss + 4 * p + 2);
@@ -93,18 +105,22 @@ __device__ __forceinline__ bool gauss_hit(const BvhDev &b, int32_t p, float3 o, 
     const float3 dh = make_float3(hx, hy, hz);
     const float3 ud = make_float3(dot3(w0, d), dot3(w1, d), dot3(w2, d));
     const float3 uo = make_float3(dot3(w0, dh), dot3(w1, dh), dot3(w2, dh));
-    const float a = dot3(ud, ud);
-    const float bb = dot3(uo, ud);
-    const float t = -bb / a;
+    const float t = __fdividef(-dot3(uo, ud), dot3(ud, ud));
     if (!(t > 0.0f)) return false;
-    const float3 e = make_float3(fmaf(t, d.x, hx) + lx, fmaf(t, d.y, hy) + ly, fmaf(t, d.z, hz) + lz);
+    e = make_float3(fmaf(t, d.x, hx) + lx, fmaf(t, d.y, hy) + ly, fmaf(t, d.z, hz) + lz);
     const float3 u = make_float3(dot3(w0, e), dot3(w1, e), dot3(w2, e));
     const float m2 = dot3(u, u);
     if (!(m2 <= b.k2)) return false;
-    const float alpha = g0.w * expf(-0.5f * m2);
-    if (!(alpha >= b.alpha_min)) return false;
+    alpha = g0.w * __expf(-0.5f * m2);
+    return alpha >= b.alpha_min;
+}
+
+// gauss_eval and, when accepted, the transmittance update of Eq. 15.
+__device__ __forceinline__ bool gauss_hit(const BvhDev &b, int32_t p, float3 o, float3 d, float &T) {
+    float alpha;
+    float3 e;
+    if (!gauss_eval(b, p, o, d, alpha, e)) return false;
     T *= (1.0f - alpha);
-    if (alpha_out) *alpha_out = alpha;
     return true;
 }
 
@@ -298,7 +314,10 @@ __device__ __forceinline__ float trace_packet(const BvhDev &b, float3 o, float3 
 // tests four child boxes per lane (one float4 of each coordinate), evaluates
 // the leaf children each lane hit, and pushes all but one of the internal
 // children some lane still needs onto a warp stack in shared memory.
-template <bool COUNT>
+// UNIFORM: every lane has the same direction (a direction set): each box is
+// then tested against its near and far planes, chosen once per packet from
+// the direction's signs, without per-box min/max.
+template <bool COUNT, bool UNIFORM>
 __device__ __forceinline__ float trace_wide(const BvhDev &b, float3 o, float3 d, int32_t src, bool valid,
                                             LaneLog &lg, WorkCounts &wc, int *status, int2 *stk) {
     const unsigned FULL = 0xffffffffu;
@@ -317,24 +336,38 @@ __device__ __forceinline__ float trace_wide(const BvhDev &b, float3 o, float3 d,
     }
     const float3 inv = safe_inv(d);
     const float3 oi = make_float3(o.x * inv.x, o.y * inv.y, o.z * inv.z);
+    const int sx = inv.x < 0.0f, sy = inv.y < 0.0f, sz = inv.z < 0.0f;
     uint32_t alive = __ballot_sync(FULL, valid);
     int sp = 0;
     uint32_t node = 0, mask = alive;
     while (mask) {
         const bool mine = (mask >> lane) & 1u;
         const float4 *w = b.wide + 8 * (int64_t)node;
-        const float4 lx = __ldg(w), hx = __ldg(w + 1), ly = __ldg(w + 2), hy = __ldg(w + 3), lz = __ldg(w + 4),
-                     hz = __ldg(w + 5), rf = __ldg(w + 6);
+        const float4 rf = __ldg(w + 6);
         const uint32_t r0 = __float_as_uint(rf.x), r1 = __float_as_uint(rf.y), r2 = __float_as_uint(rf.z),
                        r3 = __float_as_uint(rf.w);
         bool h0 = false, h1 = false, h2 = false, h3 = false;
-        if (mine) {
-            h0 = slab(lx.x, hx.x, ly.x, hy.x, lz.x, hz.x, oi, inv);
-            h1 = slab(lx.y, hx.y, ly.y, hy.y, lz.y, hz.y, oi, inv);
-            h2 = slab(lx.z, hx.z, ly.z, hy.z, lz.z, hz.z, oi, inv);
-            h3 = slab(lx.w, hx.w, ly.w, hy.w, lz.w, hz.w, oi, inv);
-            if (COUNT) wc.box += (r0 != RT_EMPTY) + (r1 != RT_EMPTY) + (r2 != RT_EMPTY) + (r3 != RT_EMPTY);
+        if (UNIFORM) {
+            // near/far planes by the shared direction's signs (sx = 1 if d.x < 0)
+            const float4 nx = __ldg(w + sx), fx = __ldg(w + 1 - sx), ny = __ldg(w + 2 + sy),
+                         fy = __ldg(w + 3 - sy), nz = __ldg(w + 4 + sz), fz = __ldg(w + 5 - sz);
+            if (mine) {
+                h0 = slab_sorted(nx.x, fx.x, ny.x, fy.x, nz.x, fz.x, oi, inv);
+                h1 = slab_sorted(nx.y, fx.y, ny.y, fy.y, nz.y, fz.y, oi, inv);
+                h2 = slab_sorted(nx.z, fx.z, ny.z, fy.z, nz.z, fz.z, oi, inv);
+                h3 = slab_sorted(nx.w, fx.w, ny.w, fy.w, nz.w, fz.w, oi, inv);
+            }
+        } else {
+            const float4 lx = __ldg(w), hx = __ldg(w + 1), ly = __ldg(w + 2), hy = __ldg(w + 3),
+                         lz = __ldg(w + 4), hz = __ldg(w + 5);
+            if (mine) {
+                h0 = slab(lx.x, hx.x, ly.x, hy.x, lz.x, hz.x, oi, inv);
+                h1 = slab(lx.y, hx.y, ly.y, hy.y, lz.y, hz.y, oi, inv);
+                h2 = slab(lx.z, hx.z, ly.z, hy.z, lz.z, hz.z, oi, inv);
+                h3 = slab(lx.w, hx.w, ly.w, hy.w, lz.w, hz.w, oi, inv);
+            }
         }
+        if (COUNT && mine) wc.box += (r0 != RT_EMPTY) + (r1 != RT_EMPTY) + (r2 != RT_EMPTY) + (r3 != RT_EMPTY);
         // leaf children this lane hit, one Gaussian test each
         uint32_t leaves = ((h0 && (r0 & RT_LEAF_BIT)) ? 1u : 0u) | ((h1 && (r1 & RT_LEAF_BIT)) ? 2u : 0u) |
                           ((h2 && (r2 & RT_LEAF_BIT)) ? 4u : 0u) | ((h3 && (r3 & RT_LEAF_BIT)) ? 8u : 0u);
@@ -387,6 +420,74 @@ __device__ __forceinline__ float trace_wide(const BvhDev &b, float3 o, float3 d,
     return T < b.t_min ? 0.0f : T;
 }
 
+// Strategy 4: one thread per ray over the 4-wide tree with a private stack,
+// for rays without a shared direction (env-map samples, explicit rays).
+template <bool COUNT>
+__device__ __forceinline__ float trace_ray_wide(const BvhDev &b, float3 o, float3 d, int32_t src, LaneLog &lg,
+                                                WorkCounts &wc, int *status) {
+    float T = 1.0f;
+    if (b.n <= 0) return T;
+    if (b.n == 1) {
+        if (COUNT) wc.gauss++;
+        if (src != 0 && gauss_hit(b, 0, o, d, T)) {
+            if (COUNT) wc.hits++;
+            log_hit(lg, b, 0);
+        }
+        return T < b.t_min ? 0.0f : T;
+    }
+    const float3 inv = safe_inv(d);
+    const float3 oi = make_float3(o.x * inv.x, o.y * inv.y, o.z * inv.z);
+    uint32_t stack[RT_WIDE_STACK];
+    int sp = 0;
+    uint32_t node = 0;
+    for (;;) {
+        const float4 *w = b.wide + 8 * (int64_t)node;
+        const float4 lx = __ldg(w), hx = __ldg(w + 1), ly = __ldg(w + 2), hy = __ldg(w + 3), lz = __ldg(w + 4),
+                     hz = __ldg(w + 5), rf = __ldg(w + 6);
+        const uint32_t r[4] = {__float_as_uint(rf.x), __float_as_uint(rf.y), __float_as_uint(rf.z),
+                               __float_as_uint(rf.w)};
+        const bool h[4] = {slab(lx.x, hx.x, ly.x, hy.x, lz.x, hz.x, oi, inv),
+                           slab(lx.y, hx.y, ly.y, hy.y, lz.y, hz.y, oi, inv),
+                           slab(lx.z, hx.z, ly.z, hy.z, lz.z, hz.z, oi, inv),
+                           slab(lx.w, hx.w, ly.w, hy.w, lz.w, hz.w, oi, inv)};
+        if (COUNT) wc.box += (r[0] != RT_EMPTY) + (r[1] != RT_EMPTY) + (r[2] != RT_EMPTY) + (r[3] != RT_EMPTY);
+        int next = -1;
+        bool overflow = false;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            if (!h[c]) continue;
+            if (r[c] & RT_LEAF_BIT) {
+                const int32_t p = (int32_t)(r[c] & ~RT_LEAF_BIT);
+                if (p != src) {
+                    if (COUNT) wc.gauss++;
+                    if (gauss_hit(b, p, o, d, T)) {
+                        if (COUNT) wc.hits++;
+                        log_hit(lg, b, p);
+                    }
+                }
+            } else if (next < 0) {
+                next = (int)r[c];
+            } else if (sp < RT_WIDE_STACK) {
+                stack[sp++] = r[c];
+            } else {
+                overflow = true;
+            }
+        }
+        if (overflow) {
+            rt_set_error(status, RT_ERR_STACK_OVERFLOW);
+            break;
+        }
+        if (T < b.t_min) break;
+        if (next >= 0) {
+            node = (uint32_t)next;
+        } else {
+            if (sp == 0) break;
+            node = stack[--sp];
+        }
+    }
+    return T < b.t_min ? 0.0f : T;
+}
+
 // ---------------------------------------------------------------------------
 // Work items of a trace job
 // ---------------------------------------------------------------------------
@@ -418,8 +519,9 @@ __device__ __forceinline__ void full_item(const TraceJob &job, int32_t K, int64_
 
 // One work item (32 rays) of a trace job: build each lane's ray, traverse,
 // write T (and the hit log).  Shared by the single-scene and batched kernels.
-// STRAT: 0 per-ray binary, 1 packet binary, 2 packet 4-wide (stk: this
-// warp's RT_WIDE_STACK shared-memory entries).
+// STRAT: 0 per-ray binary, 1 packet binary, 2 packet 4-wide, 3 packet 4-wide
+// for a direction set (all lanes share the direction), 4 per-ray 4-wide
+// (stk: this warp's RT_WIDE_STACK shared-memory entries, strategies 2-3).
 template <int STRAT, bool COUNT>
 __device__ __forceinline__ void trace_item(const BvhDev &b, const RaySetDev &rs, const TraceJob &job,
                                            float *T_out, const TraceAux &aux, int64_t item, int64_t n_out,
@@ -476,8 +578,12 @@ __device__ __forceinline__ void trace_item(const BvhDev &b, const RaySetDev &rs,
     lg.cap = aux.cap;
     lg.count = 0;
     float T;
-    if (STRAT == 2) {
-        T = trace_wide<COUNT>(b, o, d, src, valid, lg, wc, aux.status, stk);
+    if (STRAT == 4) {
+        T = valid ? trace_ray_wide<COUNT>(b, o, d, src, lg, wc, aux.status) : 1.0f;
+    } else if (STRAT == 3) {
+        T = trace_wide<COUNT, true>(b, o, d, src, valid, lg, wc, aux.status, stk);
+    } else if (STRAT == 2) {
+        T = trace_wide<COUNT, false>(b, o, d, src, valid, lg, wc, aux.status, stk);
     } else if (STRAT == 1) {
         T = trace_packet<COUNT>(b, o, d, src, valid, lg, wc, aux.status);
     } else {

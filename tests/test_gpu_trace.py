@@ -58,7 +58,7 @@ def small(orc):
     return sc, dirs, ref
 
 
-@pytest.mark.parametrize("kernel", [1, 2, 3])
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4])
 def test_small_scene_all_rays(small, kernel):
     sc, dirs, ref = small
     bvh = build(sc)
@@ -74,8 +74,10 @@ def test_kernels_agree(small):
     a = trace_dirs(bvh, dirs, kernel=1)
     b = trace_dirs(bvh, dirs, kernel=2)
     c = trace_dirs(bvh, dirs, kernel=3)
+    e = trace_dirs(bvh, dirs, kernel=4)
     np.testing.assert_array_equal(a, b)
     np.testing.assert_allclose(c, a, atol=1e-6, rtol=0)
+    np.testing.assert_allclose(e, a, atol=1e-6, rtol=0)
 
 
 def test_wide_tree_counts(small):
@@ -103,7 +105,7 @@ def test_wide_tree_same_hits_without_early_exit(small):
     bvh = build(sc, t_min=0.0)
     R = 4096 * 32
     out = []
-    for kernel in (1, 3):
+    for kernel in (1, 3, 4):
         cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
         hc = torch.zeros(R, dtype=torch.int32, device="cuda")
         ids = torch.zeros((R, 4), dtype=torch.int32, device="cuda")
@@ -111,9 +113,10 @@ def test_wide_tree_same_hits_without_early_exit(small):
         rt.rt_trace_visibility(bvh, rs, opts=rt.trace_opts(kernel=kernel, counters=cnt, hit_ids=ids, hit_count=hc))
         torch.cuda.synchronize()
         out.append((cnt.cpu().numpy(), hc.cpu().numpy()))
-    np.testing.assert_array_equal(out[0][1], out[1][1])  # same accepted hits per ray
-    assert out[0][0][1] == out[1][0][1]  # same Gaussian tests (the leaves whose box a ray enters)
-    assert out[0][0][2] == out[1][0][2]
+    for k in (1, 2):
+        np.testing.assert_array_equal(out[0][1], out[k][1])  # same accepted hits per ray
+        assert out[0][0][1] == out[k][0][1]  # same Gaussian tests (the leaves whose box a ray enters)
+        assert out[0][0][2] == out[k][0][2]
 
 
 @pytest.mark.parametrize("order_block", [1, 7, 1000])
@@ -160,7 +163,7 @@ def test_explicit_rays_and_counters(orc):
     ref = orc.trace(sc, ro, rd, src)
     bvh = build(sc)
     outs, cnts = [], []
-    for kernel in (1, 2, 3):
+    for kernel in (1, 2, 3, 4):
         cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
         rs = rt.rayspec(rt.RT_RAYS_EXPLICIT, ray_o=_dev(ro), ray_d=_dev(rd), ray_src=_dev(src))
         T = rt.rt_trace_visibility(bvh, rs, opts=rt.trace_opts(kernel=kernel, counters=cnt))
@@ -169,6 +172,7 @@ def test_explicit_rays_and_counters(orc):
         cnts.append(cnt.cpu().numpy())
     compare(outs[0], ref)
     compare(outs[2], ref)
+    compare(outs[3], ref)
     np.testing.assert_array_equal(outs[0], outs[1])
     np.testing.assert_array_equal(cnts[0], cnts[1])
     assert cnts[0][3] == R
@@ -245,7 +249,7 @@ def test_tiny_scenes(orc, n):
     ids = np.arange(n * 16, dtype=np.int64)
     o, d, s = orc.dir_rays(sc["mean"], dirs, ids)
     ref = orc.trace(sc, o, d, s)
-    for kernel in (1, 2, 3):
+    for kernel in (1, 2, 3, 4):
         compare(trace_dirs(bvh, dirs, kernel=kernel).reshape(-1), ref, max_excluded=1.0)
 
 
@@ -258,7 +262,7 @@ def test_object_scene_300k_sample(orc):
     sel = scenes.sample_ray_ids(300_000 * 128, 4096, 7)
     o, d, s = orc.dir_rays(sc["mean"], dirs, sel)
     ref = orc.trace(sc, o, d, s)
-    for kernel in (1, 3):
+    for kernel in (1, 3, 4):
         T = trace_dirs(bvh, dirs, kernel=kernel).reshape(-1)
         compare(T[sel], ref, max_excluded=0.01)
         assert np.all((T >= 0) & (T <= 1))
