@@ -55,35 +55,66 @@ __device__ __forceinline__ float bf16_lo(uint32_t u) { return __uint_as_float(u 
 __device__ __forceinline__ float bf16_hi(uint32_t u) { return __uint_as_float(u & 0xffff0000u); }
 
 // Frequency encoding of one ray into 80 floats (rounded to bf16 at store).
-// The origin is normalised in float64, x = 2 (p - lo)/(hi - lo) - 1 (IEEE
-// operations, so the same value as a float64 host computation), and the
-// argument 2^k x of sin/cos(pi 2^k x) is reduced modulo 2 in float64 (both
-// steps exact) before the float32 sincospif: the feature is then within a
-// few 1e-7 of its exact value, so its bf16 rounding rarely differs from that
-// of an exact evaluation.
-__device__ __forceinline__ void sincospi_k(double x, int k, float &s, float &c) {
-    const double t = ldexp(x, k);             // exact
-    const double r = t - 2.0 * rint(0.5 * t);  // exact, in [-1, 1]
-    sincospif((float)r, &s, &c);
+// The sin/cos arguments pi 2^k x reach 32 pi x, so x must be far more
+// accurate than one float rounding for the features to round to the same
+// bf16 values as an exact evaluation.  With float32 error-free transforms:
+// p - lo and hi - lo are split exactly into pairs, the quotient is a pair
+// q + ql (remainder-corrected, relative error ~1e-13), x = 2 (q + ql) - 1 is
+// kept as a pair xh + xl, and 2^k x is reduced modulo 2 exactly
+// (t_h - 2 rint(t_h / 2) is exact) before sincospif.  No float64 is used
+// (float64 throughput is very low on this part).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-__device__ __forceinline__ void encode(float3 p, float3 d, const double *lo, const double *ext, float (&f)[IN]) {
-    double x[6];
-    x[0] = ext[0] > 0.0 ? 2.0 * ((double)p.x - lo[0]) / ext[0] - 1.0 : 0.0;
-    x[1] = ext[1] > 0.0 ? 2.0 * ((double)p.y - lo[1]) / ext[1] - 1.0 : 0.0;
-    x[2] = ext[2] > 0.0 ? 2.0 * ((double)p.z - lo[2]) / ext[2] - 1.0 : 0.0;
-    x[3] = d.x;
-    x[4] = d.y;
-    x[5] = d.z;
+__device__ __forceinline__ void normalise_pair(float p, float lo, float eh, float el, float &xh, float &xl) {
+    if (eh == 0.0f) {
+        xh = 0.0f;
+        xl = 0.0f;
+        return;
+    }
+    float dh, dl;
+    two_diff(p, lo, dh, dl);                 // dh + dl = p - lo exactly
+    const float q = __fdiv_rn(dh, eh);
+    float r = fmaf(-q, eh, dh);              // exact remainder
+    r = __fadd_rn(r, dl);
+    r = fmaf(-q, el, r);
+    const float ql = __fdiv_rn(r, eh);       // (p - lo)/(hi - lo) = q + ql
+    float s, e;
+    two_sum(2.0f * q, -1.0f, s, e);
+    const float lo2 = __fadd_rn(e, 2.0f * ql);
+    xh = __fadd_rn(s, lo2);                  // renormalise the pair
+    xl = __fsub_rn(lo2, __fsub_rn(xh, s));
+}
+
+__device__ __forceinline__ void sincospi_k(float xh, float xl, int k, float &s, float &c) {
+    const float th = ldexpf(xh, k), tl = ldexpf(xl, k);   // exact
+    const float n = 2.0f * rintf(0.5f * th);
+    const float r = __fadd_rn(__fsub_rn(th, n), tl);      // th - n exact
+    sincospif(r, &s, &c);
+}
+
+__device__ __forceinline__ void encode(float3 p, float3 d, const float *lo, const float *eh, const float *el,
+                                       float (&f)[IN]) {
+    float xh[6], xl[6];
+    normalise_pair(p.x, lo[0], eh[0], el[0], xh[0], xl[0]);
+    normalise_pair(p.y, lo[1], eh[1], el[1], xh[1], xl[1]);
+    normalise_pair(p.z, lo[2], eh[2], el[2], xh[2], xl[2]);
+    xh[3] = d.x;
+    xh[4] = d.y;
+    xh[5] = d.z;
+    xl[3] = xl[4] = xl[5] = 0.0f;
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
-        f[13 * c] = (float)x[c];
+        f[13 * c] = xh[c];
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-            float s, co;
-            sincospi_k(x[c], k, s, co);
-            f[13 * c + 1 + 2 * k] = s;
-            f[13 * c + 2 + 2 * k] = co;
+            float sv, cv;
+            sincospi_k(xh[c], xl[c], k, sv, cv);
+            f[13 * c + 1 + 2 * k] = sv;
+            f[13 * c + 2 + 2 * k] = cv;
         }
     }
     f[78] = 0.0f;
@@ -198,31 +229,41 @@ __device__ __forceinline__ bool get_sample(const SampleSrc &S, int64_t i, int64_
 struct MlpDev {
     const float *params;  // f32 master
     const uint8_t *img;   // bf16 images
-    double lo[3], ext[3]; // origin normalisation: x = 2 (p - lo) / ext - 1
+    float lo[3];          // origin normalisation x = 2 (p - lo)/(hi - lo) - 1 with
+    float eh[3], el[3];   // hi - lo = eh + el exactly
 };
 
 // ---------------------------------------------------------------------------
 // Inference
 // ---------------------------------------------------------------------------
-constexpr int INF_SMEM_ACT = IMG_BYTES;                   // 32768
-constexpr int INF_SMEM_B = INF_SMEM_ACT + 32768;          // b1..b4, w5: 5*128 floats
-constexpr int INF_SMEM_BAR = INF_SMEM_B + 5 * 128 * 4;    // mbarrier + tmem slot
+// INF_WG warpgroups per CTA work on separate tiles (own activation buffer,
+// TMEM columns and mbarrier, named barrier 1 + g) and share the weight
+// images, so one group's MMAs run while the others encode or run epilogues.
+constexpr int INF_WG = 3;
+constexpr int INF_SMEM_ACT = IMG_BYTES;                          // INF_WG x 32768
+constexpr int INF_SMEM_B = INF_SMEM_ACT + INF_WG * 32768;        // b1..b4, w5: 5*128 floats
+constexpr int INF_SMEM_BAR = INF_SMEM_B + 5 * 128 * 4;           // INF_WG mbarriers + tmem slot
 constexpr int INF_SMEM_TOTAL = INF_SMEM_BAR + 64;
 
-__global__ void __launch_bounds__(128, 1) k_mlp_infer(MlpDev net, SampleSrc S, int64_t m, float *out, float band,
-                                                      int64_t *fb_rid, int64_t *fb_pos,
-                                                      unsigned long long *fb_count, int *status) {
+__device__ __forceinline__ void wg_sync(int g) {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(128) : "memory");
+}
+
+__global__ void __launch_bounds__(128 * INF_WG, 1) k_mlp_infer(MlpDev net, SampleSrc S, int64_t m, float *out,
+                                                               float band, int64_t *fb_rid, int64_t *fb_pos,
+                                                               unsigned long long *fb_count, int *status) {
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *wimg = smem;
-    uint8_t *act = smem + INF_SMEM_ACT;
     float *bias = reinterpret_cast<float *>(smem + INF_SMEM_B);  // [4][128], then w5[128]
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + INF_SMEM_BAR);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + INF_SMEM_BAR + 8);
-    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + INF_SMEM_BAR);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + INF_SMEM_BAR + 8 * INF_WG);
+    const int t = threadIdx.x, g = t >> 7, tl = t & 127, wq = tl >> 5, lane = t & 31;
+    uint8_t *act = smem + INF_SMEM_ACT + g * 32768;
+    uint64_t *bar = bars + g;
 
-    for (int i = t; i < IMG_BYTES / 16; i += 128)
+    for (int i = t; i < IMG_BYTES / 16; i += 128 * INF_WG)
         reinterpret_cast<uint4 *>(wimg)[i] = __ldg(reinterpret_cast<const uint4 *>(net.img) + i);
-    for (int i = t; i < 128; i += 128) {
+    for (int i = t; i < 128; i += 128 * INF_WG) {
         bias[i] = net.params[OFF_B1 + i];
         bias[128 + i] = net.params[OFF_B2 + i];
         bias[256 + i] = net.params[OFF_B3 + i];
@@ -230,14 +271,15 @@ __global__ void __launch_bounds__(128, 1) k_mlp_infer(MlpDev net, SampleSrc S, i
         bias[512 + i] = net.params[OFF_W5 + i];
     }
     const float b5 = net.params[OFF_B5];
-    if (t == 0) mbar_init(bar, 1);
-    if (warp == 0) tmem_alloc(tslot, 128);
+    if (t == 0)
+        for (int k = 0; k < INF_WG; ++k) mbar_init(bars + k, 1);
+    if (t < 32) tmem_alloc(tslot, 512);
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = *tslot;
-    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t tmem = *tslot + (uint32_t)(g * 128);  // this group's 128 columns
+    const uint32_t lane_addr = tmem + ((uint32_t)(wq * 32) << 16);
     const uint32_t a_addr = smem_u32(act);
     const uint32_t w_addr = smem_u32(wimg);
     const uint32_t idesc = tc_idesc_bf16(128, 128, false, false);
@@ -245,26 +287,26 @@ __global__ void __launch_bounds__(128, 1) k_mlp_infer(MlpDev net, SampleSrc S, i
     bool ok = true;
     const int64_t ntiles = (m + 127) / 128;
 
-    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        const int64_t i = tile * 128 + t;
+    for (int64_t tile = (int64_t)blockIdx.x * INF_WG + g; tile < ntiles && ok; tile += (int64_t)gridDim.x * INF_WG) {
+        const int64_t i = tile * 128 + tl;
         float3 p = make_float3(0.f, 0.f, 0.f), d = make_float3(0.f, 0.f, 1.f);
         float y;
         int64_t rid = -1;
         const bool valid = get_sample(S, i, m, p, d, y, rid);
         {
             float f[IN];
-            if (valid) encode(p, d, net.lo, net.ext, f);
+            if (valid) encode(p, d, net.lo, net.eh, net.el, f);
             else
 #pragma unroll
                 for (int k = 0; k < IN; ++k) f[k] = 0.0f;
-            store_row_x0(act, t, f);
+            store_row_x0(act, tl, f);
         }
         float z5 = b5;
         for (int l = 0; l < 4; ++l) {
             fence_async_smem();
             tc_fence_before();
-            __syncthreads();
-            if (t == 0) {
+            wg_sync(g);
+            if (tl == 0) {
                 tc_fence_after();
                 const int K = l == 0 ? IN : H;
                 const uint32_t sbo = (uint32_t)(K / 8 * 128);
@@ -287,7 +329,7 @@ __global__ void __launch_bounds__(128, 1) k_mlp_infer(MlpDev net, SampleSrc S, i
 #pragma unroll
                 for (int k = 0; k < 32; ++k) v[k] = fmaxf(v[k] + bl[32 * cc + k], 0.0f);
                 if (l < 3) {
-                    store_chunk(act, t, 32 * cc, v);
+                    store_chunk(act, tl, 32 * cc, v);
                 } else {
 #pragma unroll
                     for (int k = 0; k < 32; ++k) z5 = fmaf(bias[512 + 32 * cc + k], bf16_round(v[k]), z5);
@@ -296,7 +338,7 @@ __global__ void __launch_bounds__(128, 1) k_mlp_infer(MlpDev net, SampleSrc S, i
         }
         if (!ok) break;
         if (valid) {
-            const float pr = 1.0f / (1.0f + expf(-z5));
+            const float pr = 1.0f / (1.0f + __expf(-z5));
             out[i] = pr;
             const bool fb = band > 0.0f && fabsf(pr - 0.5f) < band;
             const uint32_t mask = __ballot_sync(__activemask(), fb);
@@ -311,12 +353,12 @@ __global__ void __launch_bounds__(128, 1) k_mlp_infer(MlpDev net, SampleSrc S, i
             }
         }
         tc_fence_before();
-        __syncthreads();
+        wg_sync(g);
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 0) tmem_dealloc(tmem, 128);
+    if (t < 32) tmem_dealloc(*tslot, 512);
 }
 
 // ---------------------------------------------------------------------------
@@ -414,7 +456,7 @@ __global__ void __launch_bounds__(128, 1) k_mlp_train(MlpDev net, SampleSrc S, i
         const bool valid = get_sample(S, i, m, p, d, y, rid);
         {
             float f[IN];
-            if (valid) encode(p, d, net.lo, net.ext, f);
+            if (valid) encode(p, d, net.lo, net.eh, net.el, f);
             else
 #pragma unroll
                 for (int k = 0; k < IN; ++k) f[k] = 0.0f;
@@ -669,8 +711,13 @@ MlpDev mlp_dev(const rt_surrogate *s) {
     n.params = s->params;
     n.img = s->img;
     for (int c = 0; c < 3; ++c) {
-        n.lo[c] = (double)s->lo[c];
-        n.ext[c] = (double)s->hi[c] - (double)s->lo[c];
+        // exact split of hi - lo (host float arithmetic is IEEE round-to-nearest)
+        const volatile float hi = s->hi[c], lo = s->lo[c];
+        const float sh = hi - lo;
+        const float bb = sh - hi;
+        n.lo[c] = lo;
+        n.eh[c] = sh;
+        n.el[c] = (hi - (sh - bb)) - (lo + bb);
     }
     return n;
 }
@@ -837,9 +884,9 @@ extern "C" rt_status rt_surrogate_forward(const rt_surrogate *s, const float *po
     S.mode = 0;
     S.pos = pos;
     S.dir = dir;
-    int64_t ntiles = (m + 127) / 128;
-    int grid = (int)(ntiles < rt_num_sms() ? ntiles : rt_num_sms());
-    k_mlp_infer<<<grid, 128, INF_SMEM_TOTAL, (cudaStream_t)stream>>>(mlp_dev(s), S, m, p_out, 0.f, nullptr,
+    int64_t ngroups = ((m + 127) / 128 + INF_WG - 1) / INF_WG;
+    int grid = (int)(ngroups < rt_num_sms() ? ngroups : rt_num_sms());
+    k_mlp_infer<<<grid, 128 * INF_WG, INF_SMEM_TOTAL, (cudaStream_t)stream>>>(mlp_dev(s), S, m, p_out, 0.f, nullptr,
                                                                      nullptr, nullptr, rt_status_ptr());
     return rt_check_launch();
 }
@@ -932,9 +979,9 @@ extern "C" rt_status rt_surrogate_infer(const rt_surrogate *s, const rt_bvh *bvh
             return RT_ERR_CUDA;
         }
     }
-    int64_t ntiles = (m + 127) / 128;
-    int grid = (int)(ntiles < rt_num_sms() ? ntiles : rt_num_sms());
-    k_mlp_infer<<<grid, 128, INF_SMEM_TOTAL, st>>>(mlp_dev(s), S, m, T_out, band, fb_rid, fb_pos, fb_count,
+    int64_t ngroups = ((m + 127) / 128 + INF_WG - 1) / INF_WG;
+    int grid = (int)(ngroups < rt_num_sms() ? ngroups : rt_num_sms());
+    k_mlp_infer<<<grid, 128 * INF_WG, INF_SMEM_TOTAL, st>>>(mlp_dev(s), S, m, T_out, band, fb_rid, fb_pos, fb_count,
                                                    rt_status_ptr());
     rt_status r = rt_check_launch();
     if (r == RT_OK && use_fb) {
@@ -1016,9 +1063,9 @@ extern "C" rt_status rt_surrogate_infer_noalloc(const rt_surrogate *s, const rt_
     S.b = bvh_dev(bvh);
     S.rs = rs;
     S.R = rs.n_rays;
-    int64_t ntiles = (m + 127) / 128;
-    int grid = (int)(ntiles < rt_num_sms() ? ntiles : rt_num_sms());
-    k_mlp_infer<<<grid, 128, INF_SMEM_TOTAL, st>>>(mlp_dev(s), S, m, T_out, band, use_fb ? fb_rid : nullptr,
+    int64_t ngroups = ((m + 127) / 128 + INF_WG - 1) / INF_WG;
+    int grid = (int)(ngroups < rt_num_sms() ? ngroups : rt_num_sms());
+    k_mlp_infer<<<grid, 128 * INF_WG, INF_SMEM_TOTAL, st>>>(mlp_dev(s), S, m, T_out, band, use_fb ? fb_rid : nullptr,
                                                    use_fb ? fb_pos : nullptr, use_fb ? fb_count : nullptr,
                                                    rt_status_ptr());
     RT_TRY(rt_check_launch());
