@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--surrogate-steps", type=int, default=2000)
     ap.add_argument("--band", type=float, default=0.3)
     return ap.parse_args()
@@ -96,6 +97,22 @@ def workload_config(name, extra=None):
     if extra:
         cfg.update(extra)
     return cfg
+
+
+def reduce_max(x: float, world: int, device=None) -> float:
+    """Maximum of x over the ranks (the replicas' slowest time)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(units_per_rank: int, ms_max: float, world: int) -> float:
+    """Whole-job throughput: every replica's units over the slowest time."""
+    return world * units_per_rank / (ms_max / 1000.0)
 
 
 def oracle_rate(sc, dirs, m, seed=99):
@@ -249,6 +266,52 @@ def run_surrogate(args, rt, torch, d, dirs, T, prm, dev):
     return out
 
 
+def run_adjoint(rt, torch, dev):
+    """Differentiation workload: L = sum_r w_r T_r over the rays of the first
+    1,024 Gaussians of a 4,096-Gaussian uniform scene x 16 directions, and
+    over all 4,096 x 32; forward + hand-written adjoint, with the hit log
+    replayed and with re-traversal; hit-log memory."""
+    import scenes
+    out = []
+    for n_sub, K in ((1024, 16), (4096, 32)):
+        sc = {k: v[:n_sub].copy() for k, v in scenes.uniform_scene(4096, 4).items()}
+        d = {k: torch.from_numpy(v).to(dev) for k, v in sc.items()}
+        dirs = torch.from_numpy(scenes.fibonacci_sphere(K)).to(dev)
+        R = n_sub * K
+        w = torch.from_numpy(scenes.loss_weights(R, 41)).to(dev)
+        prm = rt.params(t_min=0.0)
+        bvh = rt.rt_build_bvh(d["mean"], d["scale"], d["quat"], d["opacity"], prm)
+        rs = rt.rayspec(rt.RT_RAYS_DIRS, dirs=dirs)
+        cap = 64
+        ids = torch.empty((R, cap), dtype=torch.int32, device=dev)
+        cnt = torch.empty(R, dtype=torch.int32, device=dev)
+        res = {"gaussians": n_sub, "directions": K, "rays": R}
+        for mode in ("log", "recompute"):
+            def run():
+                o = rt.trace_opts(hit_ids=ids, hit_count=cnt) if mode == "log" else None
+                T = rt.rt_trace_visibility(bvh, rs, opts=o)
+                return T, rt.rt_trace_visibility_backward(bvh, rs, d["mean"], d["scale"], d["quat"], d["opacity"], T, w,
+                                                          ids if mode == "log" else None,
+                                                          cnt if mode == "log" else None)
+            for _ in range(3):
+                run()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record()
+            for _ in range(10):
+                run()
+            ev[1].record()
+            torch.cuda.synchronize()
+            res[f"{mode}_ms_fwd_bwd"] = ev[0].elapsed_time(ev[1]) / 10
+        hits = int(cnt.to(torch.int64).sum())
+        res["hits"] = hits
+        res["hit_log_bytes_compact"] = 4 * hits + 8 * R
+        res["hit_log_bytes_fixed_capacity"] = 4 * cap * R + 4 * R
+        res["max_hits_per_ray"] = int(cnt.max())
+        out.append(res)
+        bvh.destroy()
+    return out
+
+
 def run_batch(args, rank, world, local, torch, dist, rt):
     """Batched multi-scene workload: every scene's BVH is built, then one
     graph-captured persistent launch traces all scenes' direction and
@@ -293,13 +356,9 @@ def run_batch(args, rank, world, local, torch, dist, rt):
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
     clk = clocks.stop()
-    m = statistics.mean(ms)
-    if world > 1:
-        t = torch.tensor([m], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        m = float(t.item())
+    m = reduce_max(statistics.mean(ms), world, dev)
     if rank == 0:
-        line = {"metric": METRIC, "value": world * R / (m / 1000.0), "unit": "rays/s", "n_gpus": world,
+        line = {"metric": METRIC, "value": replica_rate(R, m, world), "unit": "rays/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": m, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": workload_config(args.workload, {
@@ -413,12 +472,8 @@ def main():
     step_ms = [e[0].elapsed_time(e[2]) for e in evs]
     build_ms = [e[0].elapsed_time(e[1]) for e in evs]
     trace_ms = [e[1].elapsed_time(e[2]) for e in evs]
-    ms = statistics.mean(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * R / (ms / 1000.0)
+    ms = reduce_max(statistics.mean(step_ms), world, dev)
+    value = replica_rate(R, ms, world)
 
     # end to end through the C ABI from pinned host buffers
     e2e = None
@@ -443,17 +498,16 @@ def main():
             torch.cuda.synchronize()
             if i >= args.warmup:
                 e_ms.append(e0.elapsed_time(e1))
-        em = statistics.mean(e_ms)
-        if world > 1:
-            t = torch.tensor([em], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            em = float(t.item())
-        e2e = {"value": world * R / (em / 1000.0), "unit": "rays/s", "h2d_bytes_per_step": h2d,
+        em = reduce_max(statistics.mean(e_ms), world, dev)
+        e2e = {"value": replica_rate(R, em, world), "unit": "rays/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": em}
 
     surrogate = None
     if not args.no_surrogate and rank == 0:
         surrogate = run_surrogate(args, rt, torch, d, dirs, T, prm, dev)
+    adjoint = None
+    if not args.no_adjoint and rank == 0:
+        adjoint = run_adjoint(rt, torch, dev)
 
     pk, pk_kind = peaks()
     tr_ms = statistics.mean(trace_ms)
@@ -483,7 +537,7 @@ def main():
                     "kernel": ["auto", "per-ray", "packet"][args.kernel]}),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": (BUILD_KERNELS_PER_STEP + 1) * args.steps,
-                "clocks": clk, "surrogate": surrogate}
+                "clocks": clk, "surrogate": surrogate, "adjoint": adjoint}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()

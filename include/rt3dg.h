@@ -77,6 +77,11 @@ const char *rt_status_string(rt_status s);
  * rt_status_clear() resets it. */
 rt_status rt_status_last(void);
 rt_status rt_status_clear(void);
+/* Exercises the failure path of the kernels' bounded waits: one thread waits
+ * on an mbarrier that nothing completes, gives up after max_cycles SM cycles
+ * (1 .. 4e9), records RT_ERR_TIMEOUT in the status word and returns.  No
+ * fault, no hang; for tests of failure handling. */
+rt_status rt_selftest_wait_timeout(int64_t max_cycles, rt_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
 /* LBVH (Sec. 4.1: binary radix tree of Karras 2012 over the Gaussians)      */

@@ -997,6 +997,28 @@ extern "C" rt_status rt_surrogate_infer(const rt_surrogate *s, const rt_bvh *bvh
 }
 
 // ---------------------------------------------------------------------------
+// Failure path of the bounded waits
+// ---------------------------------------------------------------------------
+namespace {
+// One thread waits on an mbarrier that nothing ever completes, with the same
+// bounded wait the surrogate kernels use; on giving up it records
+// RT_ERR_TIMEOUT in the status word and returns.
+__global__ void k_wait_selftest(long long max_cycles, int *status) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        if (!mbar_wait(&bar, 0, max_cycles)) rt_set_error(status, RT_ERR_TIMEOUT);
+    }
+}
+}  // namespace
+
+extern "C" rt_status rt_selftest_wait_timeout(int64_t max_cycles, rt_stream_t stream) {
+    if (max_cycles <= 0 || max_cycles > 4000000000LL) return RT_ERR_INVALID_ARG;
+    k_wait_selftest<<<1, 32, 0, (cudaStream_t)stream>>>((long long)max_cycles, rt_status_ptr());
+    return rt_check_launch();
+}
+
+// ---------------------------------------------------------------------------
 // Inference without device allocation
 // ---------------------------------------------------------------------------
 // Some callers cannot let a library allocate device memory during a call:

@@ -69,6 +69,7 @@ _SIGS = {
     "rt_status_string": (C.c_char_p, [_I32]),
     "rt_status_last": (_I32, []),
     "rt_status_clear": (_I32, []),
+    "rt_selftest_wait_timeout": (_I32, [_I64, _P]),
     "rt_build_bvh": (_I32, [_P, _P, _P, _P, _I64, _P, _P, _P]),
     "rt_bvh_destroy": (_I32, [_P, _P]),
     "rt_bvh_info": (_I32, [_P, _P, _P, _P, _P]),
