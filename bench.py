@@ -44,7 +44,10 @@ WORKLOADS = {
     # 16 uniform scenes (log-uniform sizes, ~8M Gaussians), 128 directions +
     # 512 env-map shadow rays per Gaussian, one graph-captured launch
     "batch16_k128_env512": ("batch", 8_000_000, 300, 128),
+    # the same composition with object-scale scenes (flattened Gaussians on surfaces)
+    "batch16_objects_k128_env512": ("batch_objects", 8_000_000, 300, 128),
 }
+KERNEL_NAMES = ["auto", "per-ray binary", "packet binary", "packet 4-wide", "per-ray 4-wide"]
 ENV_SAMPLES = 512
 METRIC = "traced rays/s & ms per 2M-Gaussian visibility precompute; surrogate speedup at MAE"
 TRACE_SOURCES = ["paper_2311_16043_gb300/csrc/rt_trace.cu", "paper_2311_16043_gb300/csrc/rt_trace_core.cuh"]
@@ -58,9 +61,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="object_2m_k128")
-    ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 per-ray, 2 packet")
+    ap.add_argument("--kernel", type=int, default=0, choices=range(5),
+                    help="0 auto, 1 per-ray binary, 2 packet binary, 3 packet 4-wide, 4 per-ray 4-wide")
     ap.add_argument("--order-block", type=int, default=0)
     ap.add_argument("--cpu-rays", type=int, default=2048, help="oracle sample for cpu_baseline")
+    ap.add_argument("--cpu-lbvh-rays", type=int, default=1 << 20, help="sample for the CPU BVH tracer baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
@@ -75,15 +80,19 @@ def make_scene(name):
     gen, n, seed, K = WORKLOADS[name]
     if gen == "batch":
         return scenes.batch_scenes(scenes.batch_scene_sizes(16, n, seed), seed_base=seed), scenes.fibonacci_sphere(K)
+    if gen == "batch_objects":
+        return (scenes.batch_object_scenes(scenes.batch_scene_sizes(16, n, seed), seed_base=seed),
+                scenes.fibonacci_sphere(K))
     sc = scenes.object_scene(n, seed) if gen == "object" else scenes.uniform_scene(n, seed)
     return sc, scenes.fibonacci_sphere(K)
 
 
 def workload_config(name, extra=None):
     gen, n, seed, K = WORKLOADS[name]
-    if gen == "batch":
+    if gen.startswith("batch"):
+        kind = "uniform" if gen == "batch" else "object-scale"
         cfg = {"workload": name, "scenes": 16, "gaussians": n, "directions": K, "env_samples": ENV_SAMPLES,
-               "rays_per_step": None, "scene": "16 uniform scenes, log-uniform sizes in [50k, 2M]",
+               "rays_per_step": None, "scene": f"16 {kind} scenes, log-uniform sizes in [50k, 2M]",
                "seed": seed, "step": "one replay of the graph-captured persistent launch over all scenes",
                "l2": "outputs > L2 (T tables ~20 GB)"}
         if extra:
@@ -127,6 +136,26 @@ def oracle_rate(sc, dirs, m, seed=99):
     oracle.trace(sc, o, d, s)
     dt = time.perf_counter() - t0
     return m / dt, dt
+
+
+def lbvh_rate(sc, dirs, m, seed=98):
+    """Rays/s of the oracle's FP64 CPU BVH tracer (the brute-force T through
+    the LBVH twin) on a seeded sample of m rays: a fairer CPU baseline than
+    brute force.  The tree build is timed apart."""
+    import oracle
+    import scenes
+    oracle.build()
+    n, K = sc["mean"].shape[0], dirs.shape[0]
+    ids = scenes.sample_ray_ids(n * K, m, seed)
+    t0 = time.perf_counter()
+    B = oracle.BvhTracer(sc)
+    t1 = time.perf_counter()
+    out = B.trace_dirs(dirs, ids)
+    t2 = time.perf_counter()
+    B.close()
+    return {"value": m / (t2 - t1), "unit": "rays/s", "cores": os.cpu_count(), "kind": "oracle CPU BVH tracer",
+            "build_s": t1 - t0, "sample": f"{m} seeded rays of the {n * K}, {t2 - t1:.1f} s",
+            "per_ray": {"box_tests": float(out["counts"][0]) / m, "gaussian_tests": float(out["counts"][1]) / m}}
 
 
 class ClockSampler:
@@ -260,6 +289,12 @@ def run_surrogate(args, rt, torch, d, dirs, T, prm, dev):
         out_b["tracer_same_rays"] = {"ms": ev[0].elapsed_time(ev[1]),
                                      "rays_per_s": B / (ev[0].elapsed_time(ev[1]) / 1000.0)}
         out_b["speedup_vs_tracer_full_rate"] = out_b["with_fallback"]["rays_per_s"] / tracer_rate
+        # training charged to the batch: spread over the scene's whole ray table
+        # (the precompute the surrogate stands in for), or all on this batch
+        tracer_ms = 1000.0 * B / tracer_rate
+        fb_ms = out_b["with_fallback"]["ms"]
+        out_b["speedup_incl_training_amortised"] = tracer_ms / (fb_ms + train_ms * B / (n * K))
+        out_b["speedup_incl_training_not_amortised"] = tracer_ms / (fb_ms + train_ms)
         out["batches"].append(out_b)
     s.destroy()
     bvh.destroy()
@@ -322,7 +357,7 @@ def run_batch(args, rank, world, local, torch, dist, rt):
     env = scenes.envmap(399)
     E = rt.rt_envmap_create(env["radiance"], env["solid_angle"], env["corners"])
     dirs = torch.from_numpy(dirs_np).to(dev)
-    jobs, bvhs, build_ms = [], [], 0.0
+    jobs, bvhs, build_ms, specs = [], [], 0.0, []
     for s_idx, sc in enumerate(scs):
         d = {k: torch.from_numpy(v).to(dev) for k, v in sc.items()}
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -332,9 +367,12 @@ def run_batch(args, rank, world, local, torch, dist, rt):
         torch.cuda.synchronize()
         build_ms += e0.elapsed_time(e1)
         bvhs.append((bvh, d))
-        for rs in (rt.rayspec(rt.RT_RAYS_DIRS, dirs=dirs),
-                   rt.rayspec(rt.RT_RAYS_ENV, env=E, n_samples=ENV_SAMPLES, seed=399 + s_idx)):
+        for kind, mk in (("dirs", lambda ids=None: rt.rayspec(rt.RT_RAYS_DIRS, dirs=dirs, ray_ids=ids)),
+                         ("env", lambda ids=None, s_idx=s_idx: rt.rayspec(rt.RT_RAYS_ENV, env=E, n_samples=ENV_SAMPLES,
+                                                                          seed=399 + s_idx, ray_ids=ids))):
+            rs = mk()
             jobs.append((bvh, rs, torch.empty(rt.rt_rayspec_count(bvh, rs), dtype=torch.float32, device=dev)))
+            specs.append((kind, mk))
     t0 = time.perf_counter()
     batch = rt.rt_batch_create(jobs, autotune=True)
     create_s = time.perf_counter() - t0
@@ -357,6 +395,24 @@ def run_batch(args, rank, world, local, torch, dist, rt):
         ms.append(e0.elapsed_time(e1))
     clk = clocks.stop()
     m = reduce_max(statistics.mean(ms), world, dev)
+    # ray statistics (outside the timed region): the early-exit fraction over
+    # every output, accepted hits per ray from a counted trace of 2^18 sampled
+    # rays per job
+    stats = {}
+    for kind in ("dirs", "env"):
+        rays = zeros = hits = sampled = 0
+        for (bvh, _, T), (k2, mk) in zip(jobs, specs):
+            if k2 != kind:
+                continue
+            rays += T.numel()
+            zeros += int((T == 0).sum())
+            ids = torch.from_numpy(scenes.sample_ray_ids(T.numel(), 1 << 18, 5)).to(dev)
+            cnt = torch.zeros(4, dtype=torch.int64, device=dev)
+            rt.rt_trace_visibility(bvh, mk(ids), opts=rt.trace_opts(counters=cnt))
+            hits += int(cnt[2])
+            sampled += ids.numel()
+        stats[kind] = {"rays": rays, "early_exit_fraction": zeros / max(rays, 1),
+                       "accepted_hits_per_ray": hits / max(sampled, 1)}
     if rank == 0:
         line = {"metric": METRIC, "value": replica_rate(R, m, world), "unit": "rays/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": m, "higher_is_better": True,
@@ -365,7 +421,7 @@ def run_batch(args, rank, world, local, torch, dist, rt):
                     "rays_per_step": R, "work_items": info["n_items"], "build_ms_all_scenes": build_ms,
                     "batch_create_s": create_s, "strategy_per_job": info["kernel"],
                     "order_block_per_job": info["order_block"],
-                    "scene_sizes": [b.n for b, _ in bvhs]}),
+                    "scene_sizes": [b.n for b, _ in bvhs], "ray_stats": stats}),
                 "cpu_baseline": None, "e2e": None, "gpu_launches": args.steps, "clocks": clk}
         print(json.dumps(line), flush=True)
     batch.destroy()
@@ -414,7 +470,7 @@ def main():
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    if WORKLOADS[args.workload][0] == "batch":
+    if WORKLOADS[args.workload][0].startswith("batch"):
         run_batch(args, rank, world, local, torch, dist, rt)
         return
 
@@ -526,6 +582,7 @@ def main():
         rate, dt = oracle_rate(sc, dirs_np, m)
         cpu = {"value": rate, "unit": "rays/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"{m} seeded rays of the {R} (FP64 brute force, every ray vs all {n} Gaussians), {dt:.1f} s"}
+        cpu["lbvh_tracer"] = lbvh_rate(sc, dirs_np, args.cpu_lbvh_rays)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
@@ -534,7 +591,7 @@ def main():
                 "config": workload_config(args.workload, {
                     "parallelism": "replicas" if world > 1 else "single GPU",
                     "build_ms": statistics.mean(build_ms), "trace_ms": tr_ms,
-                    "kernel": ["auto", "per-ray", "packet"][args.kernel]}),
+                    "kernel": KERNEL_NAMES[args.kernel]}),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": (BUILD_KERNELS_PER_STEP + 1) * args.steps,
                 "clocks": clk, "surrogate": surrogate, "adjoint": adjoint}

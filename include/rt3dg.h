@@ -333,9 +333,12 @@ rt_status rt_surrogate_infer_noalloc(const rt_surrogate *s, const rt_bvh *bvh, c
 
 /* Picks the traversal strategy (rt_kernel) and the work order (order_block)
  * for a full implicit ray set (DIRS or ENV, no ray_ids) over `bvh`: each
- * candidate traces the same contiguous block of tiles of 32 Gaussians (all
- * directions; about 2M rays), timed with CUDA events; the fastest is written
- * into opts->kernel and opts->order_block (other fields untouched).  Results
+ * candidate traces the same four contiguous blocks of tiles of 32 Gaussians
+ * spread over the Morton range (all directions; about 4M rays), timed with
+ * CUDA events, best of two runs after a warm-up; the fastest is written into
+ * opts->kernel and opts->order_block (other fields untouched) when it beats
+ * the default strategy (RT_KERNEL_WIDE for DIRS, RT_KERNEL_RAY_WIDE for ENV)
+ * by more than 3 %, else the default with its best order_block.  Results
  * are cached in-process per (device, log2 n, ray kind, K).  T_scratch must
  * hold rt_rayspec_count(bvh, rays) floats.  Synchronises `stream`. */
 rt_status rt_trace_autotune(const rt_bvh *bvh, const rt_rayspec *rays, float *T_scratch,

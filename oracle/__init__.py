@@ -73,6 +73,11 @@ def _load():
             "oracle_morton": (None, [i64, P, P, P, P]),
             "oracle_lbvh": (None, [i64, P, P, P, P, P]),
             "oracle_leaf_boxes": (None, [i64, P, P, P, P, f64, f64, i32, P]),
+            "oracle_bvh_create": (P, [i64, P, P, P, P, f64, f64]),
+            "oracle_bvh_destroy": (None, [P]),
+            "oracle_bvh_trace": (None, [P, i64, P, P, P, f64, f64, f64, f64, f64, P, P, P, P, P]),
+            "oracle_bvh_trace_dirs": (None, [P, i32, P, f32, P, i64, f64, f64, f64, f64, f64,
+                                             P, P, P, P, P]),
             "oracle_bf16_round": (None, [i64, P, P]),
             "oracle_mlp_encode": (None, [i64, P, P, P, P, P]),
             "oracle_mlp_nparam": (i64, []),
@@ -238,6 +243,65 @@ def leaf_boxes(scene, k_sigma=3.0, alpha_min=1.0 / 255.0, box_mode=0):
     _load().oracle_leaf_boxes(n, _p(mean), _p(scale), _p(quat), _p(opac), k_sigma, alpha_min,
                               box_mode, _p(box))
     return box
+
+
+class BvhTracer:
+    """The brute-force visibility of ``trace`` found through the LBVH twin
+    (``rt_oracle.c``, oracle_bvh_*): same T up to the order of the product,
+    flags a subset of ``trace``'s, and a ray flagged only by ``trace`` has
+    T = 0 (the walk stops once T is certain to snap to 0).  Fast enough to
+    cover every ray of the 300k-Gaussian scene on the host cores."""
+
+    def __init__(self, scene, k_sigma=3.0, bands=None):
+        self._arrs = _scene(scene)
+        mean, scale, quat, opac = self._arrs
+        self.n = mean.shape[0]
+        self.bands = dict(DEFAULT_BANDS)
+        if bands:
+            self.bands.update(bands)
+        self._h = _load().oracle_bvh_create(self.n, _p(mean), _p(scale), _p(quat), _p(opac), k_sigma,
+                                            self.bands["band_m2"])
+        if not self._h:
+            raise MemoryError("oracle_bvh_create")
+
+    def close(self):
+        if self._h:
+            _load().oracle_bvh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _out(self, m):
+        return {"T": np.empty(m), "T_exact": np.empty(m), "hits": np.empty(m, np.int32),
+                "flags": np.empty(m, np.uint32), "counts": np.zeros(2, np.int64)}
+
+    def trace(self, ray_o, ray_d, ray_src=None, alpha_min=1.0 / 255.0, t_min=1e-4):
+        ray_o = _c(ray_o, np.float64).reshape(-1, 3)
+        ray_d = _c(ray_d, np.float64).reshape(-1, 3)
+        src = None if ray_src is None else _c(ray_src, np.int32)
+        m = ray_o.shape[0]
+        o, b = self._out(m), self.bands
+        _load().oracle_bvh_trace(self._h, m, _p(ray_o), _p(ray_d), _p(src), alpha_min, t_min,
+                                 b["band_alpha"], b["band_t"], b["band_T"], _p(o["T"]), _p(o["T_exact"]),
+                                 _p(o["hits"]), _p(o["flags"]), _p(o["counts"]))
+        return o
+
+    def trace_dirs(self, dirs, ids=None, eps=1e-4, alpha_min=1.0 / 255.0, t_min=1e-4):
+        """Rays r = g*K + k of the direction set (``dir_rays``); ids=None
+        traces all n*K in id order."""
+        dirs = _c(dirs, np.float32)
+        K = dirs.shape[0]
+        ids = None if ids is None else _c(ids, np.int64)
+        m = self.n * K if ids is None else ids.shape[0]
+        o, b = self._out(m), self.bands
+        _load().oracle_bvh_trace_dirs(self._h, K, _p(dirs), eps, _p(ids), m, alpha_min, t_min,
+                                      b["band_alpha"], b["band_t"], b["band_T"], _p(o["T"]),
+                                      _p(o["T_exact"]), _p(o["hits"]), _p(o["flags"]), _p(o["counts"]))
+        return o
 
 
 def bf16_round(x) -> np.ndarray:

@@ -33,6 +33,11 @@
  *                      Morton codes of the centroids, keys code<<32|index,
  *                      sorted, internal nodes by the longest-common-prefix
  *                      split rule; exact FP64 leaf boxes (K-sigma extents).
+ *   oracle_bvh_*       the same visibility as oracle_trace, found through the
+ *                      LBVH twin (Sec. 4.1: rays traced through a BVH over the
+ *                      Gaussians' boxes) with boxes that cover every candidate
+ *                      brute force accepts or flags; pinned against
+ *                      oracle_trace, it reaches every ray of the large scenes.
  *   oracle_mlp_*       the visibility surrogate (not in the paper): frequency
  *                      encoding, 4x128 ReLU MLP, sigmoid, BCE, Adam; bf16
  *                      rounding emulated where the GPU stores bf16, FP64
@@ -643,6 +648,281 @@ void oracle_leaf_boxes(int64_t n, const double *mean, const double *scale, const
             box[6 * j + 3 + i] = empty ? -INFINITY : mean[3 * j + i] + h;
         }
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* CPU BVH tracer: oracle_trace's visibility through the LBVH twin           */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Sec. 4.1 finds the Gaussians a ray meets by tracing it through a BVH over
+ * their bounding boxes; the visibility is still the product of Eq. 15 over the
+ * accepted Gaussians.  This tracer computes that product through the tree of
+ * oracle_lbvh and gives the same T as the brute force whenever every Gaussian
+ * that brute force accepts or flags lies in a box the ray meets:
+ *   - leaf box of Gaussian j: the FP64 box of {m^2 <= K^2 + band_m2} (the
+ *     support widened to the m^2 band), widened by 1e-9 of its half-extent and
+ *     1e-12 (|mu| + 1) against rounding; internal boxes are unions;
+ *   - a box counts when the ray meets it at some t >= -(2 band_t + 1e-12), so
+ *     candidates with t* in the t band are reached too;
+ *   - each candidate is evaluated by peak_m2 and the acceptance and band rules
+ *     of oracle_trace.
+ * Every candidate that oracle_trace accepts or flags has m^2 <= K^2 + band_m2
+ * and t* >= -band_t, so it is visited.  The one difference: with t_min > 0 the
+ * walk stops once the product of the accepted factors is below
+ * t_min - band_T.  T is then 0 whatever follows (the product only falls), and
+ * a band flag that brute force would raise further along changes nothing.  So
+ * T agrees with oracle_trace up to the order of the product, the flags here
+ * are a subset of brute force's, and a ray flagged only by brute force has
+ * T = 0.  Children are visited nearer entry first so that the stop comes early.
+ */
+typedef struct {
+    int64_t n;
+    gauss64 *g;        /* original order */
+    int32_t *left, *right;
+    int32_t *leaf_id;  /* sorted position -> original index */
+    double *ibox;      /* internal node boxes [n-1][6] */
+    double *lbox;      /* leaf boxes [n][6], sorted order */
+    double k_sigma, band_m2;
+} orc_bvh;
+
+static const double *node_box(const orc_bvh *b, uint32_t ref)
+{
+    return (ref & ORC_LEAF) ? b->lbox + 6 * (size_t)(ref & ~ORC_LEAF) : b->ibox + 6 * (size_t)ref;
+}
+
+/* Union boxes of internal nodes, children before parents (explicit stack). */
+static void fill_internal_boxes(orc_bvh *b)
+{
+    int64_t m = b->n - 1;
+    if (m <= 0) return;
+    uint8_t *state = (uint8_t *)calloc((size_t)m, 1);
+    int32_t *stk = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m + 1));
+    int64_t top = 0;
+    stk[top++] = 0;
+    while (top > 0) {
+        int32_t i = stk[top - 1];
+        uint32_t c[2] = {(uint32_t)b->left[i], (uint32_t)b->right[i]};
+        if (!state[i]) {
+            state[i] = 1;
+            for (int k = 0; k < 2; ++k)
+                if (!(c[k] & ORC_LEAF)) stk[top++] = (int32_t)c[k];
+            continue;
+        }
+        --top;
+        const double *x = node_box(b, c[0]), *y = node_box(b, c[1]);
+        double *z = b->ibox + 6 * (size_t)i;
+        for (int a = 0; a < 3; ++a) {
+            z[a] = x[a] < y[a] ? x[a] : y[a];
+            z[3 + a] = x[3 + a] > y[3 + a] ? x[3 + a] : y[3 + a];
+        }
+    }
+    free(state);
+    free(stk);
+}
+
+/*
+ * Build the tracer over n Gaussians (FP64 inputs; the means must be float32
+ * values, as the Morton codes are taken in float32).  Returns NULL on n < 0 or
+ * allocation failure.  band_m2 is the m^2 band of oracle_trace the boxes must
+ * cover.
+ */
+void *oracle_bvh_create(int64_t n, const double *mean, const double *scale, const double *quat,
+                        const double *opac, double k_sigma, double band_m2)
+{
+    if (n < 0) return NULL;
+    orc_bvh *b = (orc_bvh *)calloc(1, sizeof(orc_bvh));
+    size_t n1 = (size_t)(n > 0 ? n : 1);
+    b->n = n;
+    b->k_sigma = k_sigma;
+    b->band_m2 = band_m2;
+    b->g = load_gaussians(n, mean, scale, quat, opac);
+    b->left = (int32_t *)malloc(sizeof(int32_t) * n1);
+    b->right = (int32_t *)malloc(sizeof(int32_t) * n1);
+    b->leaf_id = (int32_t *)malloc(sizeof(int32_t) * n1);
+    b->ibox = (double *)malloc(sizeof(double) * 6 * n1);
+    b->lbox = (double *)malloc(sizeof(double) * 6 * n1);
+    float *m32 = (float *)malloc(sizeof(float) * 3 * n1);
+    uint64_t *keys = (uint64_t *)malloc(sizeof(uint64_t) * n1);
+    int32_t *parent = (int32_t *)malloc(sizeof(int32_t) * 2 * n1);
+    double *box = (double *)malloc(sizeof(double) * 6 * n1);
+    for (int64_t i = 0; i < 3 * n; ++i) m32[i] = (float)mean[i];
+    oracle_lbvh(n, m32, keys, b->left, b->right, parent);
+    double kk = sqrt(k_sigma * k_sigma + band_m2);
+    oracle_leaf_boxes(n, mean, scale, quat, opac, kk, 0.0, 0, box);
+    for (int64_t p = 0; p < n; ++p) {
+        int64_t j = (int64_t)(keys[p] & 0xffffffffu);
+        b->leaf_id[p] = (int32_t)j;
+        for (int a = 0; a < 3; ++a) {
+            double c = mean[3 * j + a];
+            double h = 0.5 * (box[6 * j + 3 + a] - box[6 * j + a]);
+            double w = 1e-9 * h + 1e-12 * (fabs(c) + 1.0);
+            b->lbox[6 * p + a] = box[6 * j + a] - w;
+            b->lbox[6 * p + 3 + a] = box[6 * j + 3 + a] + w;
+        }
+    }
+    fill_internal_boxes(b);
+    free(m32);
+    free(keys);
+    free(parent);
+    free(box);
+    return b;
+}
+
+void oracle_bvh_destroy(void *h)
+{
+    orc_bvh *b = (orc_bvh *)h;
+    if (!b) return;
+    free(b->g);
+    free(b->left);
+    free(b->right);
+    free(b->leaf_id);
+    free(b->ibox);
+    free(b->lbox);
+    free(b);
+}
+
+/* Entry parameter of the ray into box bx on [t0, inf), or INFINITY if it
+ * misses.  fmin/fmax drop the NaN of 0 * inf (a face through the origin on a
+ * zero direction component), which can only keep a box, never lose one. */
+static double slab64(const double *bx, const double o[3], const double inv[3], double t0)
+{
+    double lo = t0, hi = INFINITY;
+    for (int a = 0; a < 3; ++a) {
+        double ta = (bx[a] - o[a]) * inv[a], tb = (bx[3 + a] - o[a]) * inv[a];
+        lo = fmax(lo, fmin(ta, tb));
+        hi = fmin(hi, fmax(ta, tb));
+    }
+    return lo <= hi ? lo : INFINITY;
+}
+
+typedef struct {
+    double alpha_min, t_min, band_m2, band_alpha, band_t, band_T;
+} orc_rule;
+
+/* One ray through the tree; returns T and writes T_exact (of the accepted
+ * factors met before a stop), hits, flags and the box / Gaussian test counts. */
+static double bvh_ray(const orc_bvh *b, const orc_rule *u, const double ro[3], const double rd[3],
+                      int64_t src, double *te_out, int32_t *hits_out, uint32_t *flags_out,
+                      int64_t *nbox, int64_t *ngauss)
+{
+    const double K2 = b->k_sigma * b->k_sigma;
+    const double t0 = -(2.0 * u->band_t + 1e-12);
+    const double stop = u->t_min > 0.0 ? u->t_min - u->band_T : -1.0;
+    double inv[3];
+    for (int a = 0; a < 3; ++a) inv[a] = 1.0 / rd[a];
+    double tr = 1.0;
+    int32_t nh = 0;
+    uint32_t fl = 0;
+    uint32_t stk[130];
+    int top = 0;
+    if (b->n > 0) {
+        uint32_t root = b->n == 1 ? ORC_LEAF : 0u;
+        ++*nbox;
+        if (slab64(node_box(b, root), ro, inv, t0) < INFINITY) stk[top++] = root;
+    }
+    while (top > 0 && tr >= stop) {
+        uint32_t ref = stk[--top];
+        if (ref & ORC_LEAF) {
+            int64_t j = b->leaf_id[ref & ~ORC_LEAF];
+            if (j == src) continue;
+            ++*ngauss;
+            double t;
+            double m2 = peak_m2(&b->g[j], ro, rd, &t, NULL);
+            double alpha = b->g[j].o * exp(-0.5 * m2);
+            int ok_t = t > 0.0, ok_m = m2 <= K2, ok_a = alpha >= u->alpha_min;
+            int near_t = fabs(t) <= u->band_t, near_m = fabs(m2 - K2) <= u->band_m2,
+                near_a = fabs(alpha - u->alpha_min) <= u->band_alpha;
+            int lo_t = ok_t || near_t, lo_m = ok_m || near_m, lo_a = ok_a || near_a;
+            if (near_t && lo_m && lo_a) fl |= ORC_FLAG_T;
+            if (near_m && lo_t && lo_a) fl |= ORC_FLAG_M2;
+            if (near_a && lo_t && lo_m) fl |= ORC_FLAG_ALPHA;
+            if (ok_t && ok_m && ok_a) {
+                tr *= (1.0 - alpha);
+                ++nh;
+            }
+            continue;
+        }
+        uint32_t c[2] = {(uint32_t)b->left[ref], (uint32_t)b->right[ref]};
+        double e[2];
+        for (int k = 0; k < 2; ++k) e[k] = slab64(node_box(b, c[k]), ro, inv, t0);
+        *nbox += 2;
+        int near = e[1] < e[0] ? 1 : 0;
+        /* the far child goes on the stack first; depth <= 64 keeps this bounded */
+        if (e[1 - near] < INFINITY) stk[top++] = c[1 - near];
+        if (e[near] < INFINITY) stk[top++] = c[near];
+    }
+    if (u->t_min > 0.0 && fabs(tr - u->t_min) <= u->band_T) fl |= ORC_FLAG_TMIN;
+    *te_out = tr;
+    *hits_out = nh;
+    *flags_out = fl;
+    return tr < u->t_min ? 0.0 : tr;
+}
+
+/*
+ * Visibility of explicit rays through the tree (same arguments and outputs
+ * as oracle_trace; T_exact, hits, flags, counts may be NULL).  counts[0..1]
+ * receive the total box and Gaussian tests.
+ */
+void oracle_bvh_trace(const void *h, int64_t n_rays, const double *ray_o, const double *ray_d,
+                      const int32_t *ray_src, double alpha_min, double t_min, double band_alpha,
+                      double band_t, double band_T, double *T, double *T_exact, int32_t *hits,
+                      uint32_t *flags, int64_t *counts)
+{
+    const orc_bvh *b = (const orc_bvh *)h;
+    orc_rule u = {alpha_min, t_min, b->band_m2, band_alpha, band_t, band_T};
+    int64_t nb = 0, ng = 0;
+#pragma omp parallel for schedule(dynamic, 256) reduction(+ : nb, ng)
+    for (int64_t r = 0; r < n_rays; ++r) {
+        double ro[3] = {ray_o[3 * r], ray_o[3 * r + 1], ray_o[3 * r + 2]};
+        double rd[3] = {ray_d[3 * r], ray_d[3 * r + 1], ray_d[3 * r + 2]};
+        double te;
+        int32_t nh;
+        uint32_t fl;
+        T[r] = bvh_ray(b, &u, ro, rd, ray_src ? ray_src[r] : -1, &te, &nh, &fl, &nb, &ng);
+        if (T_exact) T_exact[r] = te;
+        if (hits) hits[r] = nh;
+        if (flags) flags[r] = fl;
+    }
+    if (counts) { counts[0] = nb; counts[1] = ng; }
+}
+
+/*
+ * Visibility of the direction-set rays (Sec. 4.2) through the tree, the rays
+ * made as in oracle_dir_rays: ray id r = g*K + k, origin fl(mu_g + fl(eps d_k))
+ * in float32, source g.  ids[m] lists the rays (NULL: all n*K in id order);
+ * output i belongs to ray ids[i].
+ */
+void oracle_bvh_trace_dirs(const void *h, int32_t K, const float *dirs, float eps, const int64_t *ids,
+                           int64_t m, double alpha_min, double t_min, double band_alpha, double band_t,
+                           double band_T, double *T, double *T_exact, int32_t *hits, uint32_t *flags,
+                           int64_t *counts)
+{
+    const orc_bvh *b = (const orc_bvh *)h;
+    orc_rule u = {alpha_min, t_min, b->band_m2, band_alpha, band_t, band_T};
+    int64_t nb = 0, ng = 0;
+#pragma omp parallel for schedule(dynamic, 256) reduction(+ : nb, ng)
+    for (int64_t i = 0; i < m; ++i) {
+        int64_t r = ids ? ids[i] : i;
+        int64_t g = r / K;
+        int32_t k = (int32_t)(r % K);
+        double ro[3], rd[3];
+        for (int a = 0; a < 3; ++a) {
+            float d = dirs[3 * k + a];
+            float off = eps * d;
+            float o = (float)b->g[g].mu[a] + off;
+            ro[a] = o;
+            rd[a] = d;
+        }
+        double te;
+        int32_t nh;
+        uint32_t fl;
+        T[i] = bvh_ray(b, &u, ro, rd, g, &te, &nh, &fl, &nb, &ng);
+        if (T_exact) T_exact[i] = te;
+        if (hits) hits[i] = nh;
+        if (flags) flags[i] = fl;
+    }
+    if (counts) { counts[0] = nb; counts[1] = ng; }
 }
 
 /* ------------------------------------------------------------------------ */

@@ -4,9 +4,10 @@
 // of scenes serves).
 //
 // Autotuner: for a full implicit ray set it times each candidate (traversal
-// strategy: one thread per ray or one warp per 32 rays; work order: tiles per
-// direction sweep) on the same contiguous block of tiles and keeps the
-// fastest.
+// strategy: one thread per ray or one warp per 32 rays, binary or 4-wide
+// tree; work order: tiles per direction sweep) on the same four blocks of
+// tiles spread over the Morton range, and keeps the fastest if it beats the
+// default strategy by more than 3 %.
 //
 // Batch: the work items (32 rays each) of all jobs form one virtual queue,
 // job after job in decreasing estimated cost (rays x log2 n), consumed
@@ -37,6 +38,17 @@ struct TuneKey {
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, std::pair<int, int>> g_tune_cache;
+
+constexpr int kTuneBlocks = 4;
+constexpr float kTuneMargin = 0.97f;
+
+// The strategy used without tuning: 4-wide packets sharing a direction for a
+// direction set, one thread per ray on the 4-wide tree for env-map rays (their
+// directions differ within a tile), binary variants when there is no 4-wide tree.
+int default_kernel(const rt_bvh *bvh, int32_t kind) {
+    if (kind == RT_RAYS_DIRS) return bvh->n_wide > 0 ? RT_KERNEL_WIDE : RT_KERNEL_PACKET;
+    return bvh->n_wide > 0 ? RT_KERNEL_RAY_WIDE : RT_KERNEL_RAY;
+}
 
 TraceJob full_job(const rt_bvh *bvh, int32_t K, int32_t order_block) {
     TraceJob job;
@@ -133,44 +145,60 @@ extern "C" rt_status rt_trace_autotune(const rt_bvh *bvh, const rt_rayspec *rays
     }
     cudaStream_t st = (cudaStream_t)stream;
     unsigned long long *work = nullptr;
-    RT_TRY(rt_alloc((void **)&work, 8, stream));
+    RT_TRY(rt_alloc((void **)&work, 8 * kTuneBlocks, stream));
     const BvhDev b = bvh_dev(bvh);
     const int64_t ntiles = (bvh->n + 31) / 32;
-    // about 2M rays per candidate: a contiguous block of tiles, all directions
-    int64_t S = (2ll << 20) / (32ll * rs.K);
+    // about 4M rays per candidate: four contiguous blocks of tiles (all
+    // directions of each tile) spread evenly over the Morton range, so the
+    // sample sees several parts of the scene and each block keeps the
+    // coherence of neighbouring tiles
+    int64_t S = (1ll << 20) / (32ll * rs.K);
     if (S < 16) S = 16;
-    if (S > ntiles) S = ntiles;
-    const int64_t base = (ntiles - S) / 2;
+    int nb = kTuneBlocks;
+    if (S * nb > ntiles) {
+        nb = 1;
+        S = ntiles;
+    }
     const int blocks[] = {1, 16, 128, 1024};
+    const int def_k = default_kernel(bvh, rays->kind);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    float best = 1e30f;
-    int best_k = RT_KERNEL_PACKET, best_b = 1;
+    float best = 1e30f, def_ms = 1e30f;
+    int best_k = def_k, best_b = 64, def_b = 64;
     rt_status res = RT_OK;
     for (int kernel = RT_KERNEL_RAY; kernel <= RT_KERNEL_RAY_WIDE && res == RT_OK; ++kernel) {
         if ((kernel == RT_KERNEL_WIDE || kernel == RT_KERNEL_RAY_WIDE) && bvh->n_wide == 0) continue;
         // order_block only changes which rays share a warp for the packet strategies
         const int n_blocks = (kernel == RT_KERNEL_PACKET || kernel == RT_KERNEL_WIDE) ? 4 : 1;
+        const int strat = kernel == RT_KERNEL_RAY_WIDE ? 4 : kernel - 1;
         for (int bi = 0; bi < n_blocks && res == RT_OK; ++bi) {
-            TraceJob job = full_job(bvh, rs.K, blocks[bi]);
-            job.n_tiles = S;
-            job.tile_base = base;
-            if (job.order_block > S) job.order_block = (int32_t)S;
-            job.n_items = S * rs.K;
-            float ms = 0.f;
-            for (int rep = 0; rep < 2 && res == RT_OK; ++rep) {  // first run warms caches
+            float ms = 1e30f;
+            for (int rep = 0; rep < 3 && res == RT_OK; ++rep) {  // the first run warms caches
                 cudaEventRecord(e0, st);
-                const int strat = kernel == RT_KERNEL_RAY_WIDE ? 4 : kernel - 1;
-                res = rt_trace_launch_job(b, rs, job, T_scratch, strat, stream, work);
+                for (int q = 0; q < nb && res == RT_OK; ++q) {
+                    TraceJob job = full_job(bvh, rs.K, blocks[bi]);
+                    job.n_tiles = S;
+                    job.tile_base = nb == 1 ? 0 : (ntiles - S) * (2 * q + 1) / (2 * nb);
+                    if (job.order_block > S) job.order_block = (int32_t)S;
+                    job.n_items = S * rs.K;
+                    res = rt_trace_launch_job(b, rs, job, T_scratch, strat, stream, work + q);
+                }
                 cudaEventRecord(e1, st);
+                float t = 0.f;
                 if (cudaEventSynchronize(e1) != cudaSuccess) res = RT_ERR_CUDA;
-                cudaEventElapsedTime(&ms, e0, e1);
+                cudaEventElapsedTime(&t, e0, e1);
+                if (rep > 0 && t < ms) ms = t;
             }
-            if (res == RT_OK && ms < best) {
+            if (res != RT_OK) break;
+            if (ms < best) {
                 best = ms;
                 best_k = kernel;
                 best_b = blocks[bi];
+            }
+            if (kernel == def_k && ms < def_ms) {
+                def_ms = ms;
+                def_b = blocks[bi];
             }
         }
     }
@@ -178,6 +206,12 @@ extern "C" rt_status rt_trace_autotune(const rt_bvh *bvh, const rt_rayspec *rays
     cudaEventDestroy(e1);
     rt_free(work, stream);
     if (res != RT_OK) return res;
+    // another strategy replaces the default only when clearly faster: a
+    // small margin on a sample is within run-to-run noise
+    if (best_k != def_k && def_ms < 1e30f && best > kTuneMargin * def_ms) {
+        best_k = def_k;
+        best_b = def_b;
+    }
     opts->kernel = best_k;
     opts->order_block = best_b;
     std::lock_guard<std::mutex> g(g_tune_mu);
@@ -222,8 +256,7 @@ extern "C" rt_status rt_batch_create(const rt_batch_job *jobs, int32_t n_jobs, i
         }
         rt_trace_opts o;
         memset(&o, 0, sizeof(o));
-        o.kernel = J.rays.kind == RT_RAYS_DIRS ? (J.bvh->n_wide > 0 ? RT_KERNEL_WIDE : RT_KERNEL_PACKET)
-                                               : (J.bvh->n_wide > 0 ? RT_KERNEL_RAY_WIDE : RT_KERNEL_RAY);
+        o.kernel = default_kernel(J.bvh, J.rays.kind);
         o.order_block = 64;
         if (autotune && count > 0) {
             r = rt_trace_autotune(J.bvh, &J.rays, J.T_out, &o, stream);

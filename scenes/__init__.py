@@ -222,6 +222,19 @@ def batch_scenes(sizes, seed_base: int = 300) -> list[dict]:
     return out
 
 
+def batch_object_scenes(sizes, seed_base: int = 300) -> list[dict]:
+    """One object-scale scene (``object_scene``) per size, seed seed_base+s,
+    translated by a seeded offset U[-4,4]^3."""
+    out = []
+    for s, n in enumerate(sizes):
+        rng = np.random.default_rng(seed_base + 2000 + s)
+        off = rng.uniform(-4.0, 4.0, size=3)
+        sc = object_scene(int(n), seed_base + s)
+        sc["mean"] = _f32(sc["mean"].astype(np.float64) + off)
+        out.append(sc)
+    return out
+
+
 def envmap(seed: int = 399, h: int = 32, w: int = 64, sigma: float = 1.5) -> dict:
     """Equirectangular HDR environment map with log-normal radiance.
 

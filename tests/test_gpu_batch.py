@@ -60,16 +60,28 @@ def test_batch_equals_single_launches(orc):
     E.destroy()
 
 
-def test_autotune_picks_a_valid_shape():
+@pytest.mark.parametrize("n,kind", [(50_000, "dirs"), (100, "dirs"), (20_000, "env"), (200_000, "env")])
+def test_autotune_picks_a_valid_shape(n, kind):
+    """One block of all tiles (small scenes) or four blocks over the Morton
+    range (large ones); the chosen shape gives the per-ray result."""
     from paper_2311_16043_gb300 import rt
-    sc = scenes.uniform_scene(50000, 3)
+    sc = scenes.uniform_scene(n, 3)
     dv = {k: _dev(v) for k, v in sc.items()}
     bvh = rt.rt_build_bvh(dv["mean"], dv["scale"], dv["quat"], dv["opacity"])
-    rs = rt.rayspec(rt.RT_RAYS_DIRS, dirs=_dev(scenes.fibonacci_sphere(32)))
-    T = torch.empty(50000 * 32, device="cuda")
+    E = None
+    if kind == "dirs":
+        rs = rt.rayspec(rt.RT_RAYS_DIRS, dirs=_dev(scenes.fibonacci_sphere(32)))
+    else:
+        env = scenes.envmap(399)
+        E = rt.rt_envmap_create(env["radiance"], env["solid_angle"], env["corners"])
+        rs = rt.rayspec(rt.RT_RAYS_ENV, env=E, n_samples=64, seed=3)
+    T = torch.empty(rt.rt_rayspec_count(bvh, rs), device="cuda")
     o = rt.rt_trace_autotune(bvh, rs, T)
     assert o.kernel in (1, 2, 3, 4) and o.order_block in (1, 16, 128, 1024)
     a = rt.rt_trace_visibility(bvh, rs, opts=o)
     b = rt.rt_trace_visibility(bvh, rs, opts=rt.trace_opts(kernel=1))
     torch.cuda.synchronize()
+    assert rt.rt_status_last() == 0
     assert (a - b).abs().max().item() <= 1e-6
+    if E is not None:
+        E.destroy()

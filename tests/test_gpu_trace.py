@@ -268,6 +268,56 @@ def test_object_scene_300k_sample(orc):
         assert np.all((T >= 0) & (T <= 1))
 
 
+def test_object_scene_300k_every_ray(orc):
+    """Object-scale scene, 300k Gaussians x 128 directions: every one of the
+    38.4M rays, traced in the default launch configuration, against the
+    oracle's CPU BVH tracer (the brute-force T through the LBVH twin)."""
+    sc = scenes.object_scene(300_000, 2)
+    dirs = scenes.fibonacci_sphere(128)
+    T = trace_dirs(build(sc), dirs).reshape(-1)
+    B = orc.BvhTracer(sc)
+    ref = B.trace_dirs(dirs)
+    B.close()
+    maxerr, excluded = compare(T, ref, max_excluded=0.01)
+    print(f"300k scene, every ray: max |dT| {maxerr:.2e} over {T.size - excluded} rays, "
+          f"{excluded} in a rounding band, {(ref['T'] == 0).mean():.3f} occluded")
+    assert T.size == 300_000 * 128
+
+
+def test_bench_workload_bvh_oracle_sample(orc):
+    """The 2M-Gaussian bench scene: 262,144 sampled rays against the oracle's
+    CPU BVH tracer (many more than brute force can take)."""
+    sc = scenes.object_scene(2_000_000, 2)
+    dirs = scenes.fibonacci_sphere(128)
+    T = trace_dirs(build(sc), dirs).reshape(-1)
+    sel = scenes.sample_ray_ids(2_000_000 * 128, 262_144, 13)
+    B = orc.BvhTracer(sc)
+    ref = B.trace_dirs(dirs, sel)
+    B.close()
+    maxerr, excluded = compare(T[sel], ref, max_excluded=0.06)
+    print(f"2M scene: max |dT| {maxerr:.2e} over {sel.size - excluded} rays, {excluded} in a rounding band")
+
+
+def test_env_rays_every_ray(orc):
+    """Every env-map shadow ray (64 per Gaussian) of the 4,096-Gaussian scene,
+    the rays made by the oracle's own generator, against the CPU BVH tracer."""
+    from paper_2311_16043_gb300 import rt
+    sc = scenes.uniform_scene(4096, 1)
+    env = scenes.envmap(399)
+    E = rt.rt_envmap_create(env["radiance"], env["solid_angle"], env["corners"])
+    S = 64
+    rs = rt.rayspec(rt.RT_RAYS_ENV, env=E, n_samples=S, seed=777)
+    T = rt.rt_trace_visibility(build(sc), rs)
+    torch.cuda.synchronize()
+    assert rt.rt_status_last() == 0
+    T = T.cpu().numpy().astype(np.float64)
+    ids = np.arange(4096 * S, dtype=np.int64)
+    ro, rd, rsrc = orc.env_rays(sc["mean"], env, 777, S, ids)
+    ref = orc.BvhTracer(sc).trace(ro, rd, rsrc)
+    compare(T, ref)
+    E.destroy()
+
+
 def test_env_rays(orc):
     """Shadow rays importance-sampled from the 64x32 environment map: the
     materialised directions equal the oracle's float32 rays bit for bit, and
