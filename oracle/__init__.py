@@ -78,6 +78,11 @@ def _load():
             "oracle_bvh_trace": (None, [P, i64, P, P, P, f64, f64, f64, f64, f64, P, P, P, P, P]),
             "oracle_bvh_trace_dirs": (None, [P, i32, P, f32, P, i64, f64, f64, f64, f64, f64,
                                              P, P, P, P, P]),
+            "oracle_hemi_rays": (None, [i64, P, P, i32, P, f32, P, i64, P, P, P]),
+            "oracle_brdf_spec": (None, [i64, P, P, P, P, P, P]),
+            "oracle_sh_basis": (None, [i64, P, P]),
+            "oracle_env_lookup": (None, [i32, i32, P, i64, P, P]),
+            "oracle_pbr": (None, [i64, P, P, P, P, P, i32, P, P, i32, i32, P, P, P]),
             "oracle_bf16_round": (None, [i64, P, P]),
             "oracle_mlp_encode": (None, [i64, P, P, P, P, P]),
             "oracle_mlp_nparam": (i64, []),
@@ -302,6 +307,71 @@ class BvhTracer:
                                       b["band_alpha"], b["band_t"], b["band_T"], _p(o["T"]),
                                       _p(o["T_exact"]), _p(o["hits"]), _p(o["flags"]), _p(o["counts"]))
         return o
+
+
+def hemi_rays(mean, normals, hemi, ids, eps=1e-4):
+    """Float32 rays (o, d, src) of the hemisphere sets about each Gaussian's
+    normal: ray r = g*K + k uses the local direction hemi[k] (Sec. 3.3)."""
+    mean = _c(mean, np.float32)
+    normals = _c(normals, np.float32)
+    hemi = _c(hemi, np.float32)
+    ids = _c(ids, np.int64)
+    m = ids.shape[0]
+    o = np.empty((m, 3), np.float32)
+    d = np.empty((m, 3), np.float32)
+    s = np.empty(m, np.int32)
+    _load().oracle_hemi_rays(mean.shape[0], _p(mean), _p(normals), hemi.shape[0], _p(hemi), eps, _p(ids), m,
+                             _p(o), _p(d), _p(s))
+    return o, d, s
+
+
+def brdf_spec(n, wi, wo, rough):
+    """Specular term f_s of Eq. 9 and its (D, F, G) for unit vectors (FP64)."""
+    n = _c(n, np.float64).reshape(-1, 3)
+    wi = _c(wi, np.float64).reshape(-1, 3)
+    wo = _c(wo, np.float64).reshape(-1, 3)
+    rough = _c(np.broadcast_to(rough, (n.shape[0],)), np.float64)
+    fs = np.empty(n.shape[0])
+    terms = np.empty((n.shape[0], 3))
+    _load().oracle_brdf_spec(n.shape[0], _p(n), _p(wi), _p(wo), _p(rough), _p(fs), _p(terms))
+    return fs, terms
+
+
+def sh_basis(w):
+    w = _c(w, np.float64).reshape(-1, 3)
+    Y = np.empty((w.shape[0], 9))
+    _load().oracle_sh_basis(w.shape[0], _p(w), _p(Y))
+    return Y
+
+
+def env_lookup(env_rgb, dirs):
+    """Bilinear lookup of an equirectangular RGB map env_rgb[h, w, 3]."""
+    env = _c(env_rgb, np.float64)
+    h, w = env.shape[:2]
+    dirs = _c(dirs, np.float64).reshape(-1, 3)
+    L = np.empty((dirs.shape[0], 3))
+    _load().oracle_env_lookup(h, w, _p(env), dirs.shape[0], _p(dirs), _p(L))
+    return L
+
+
+def pbr(scene, normals, material, hemi, V, env_rgb, cam):
+    """Per-Gaussian PBR colour of Eq. 10 from the visibility V[n, K] of the
+    hemisphere rays; material = dict(albedo[n,3], roughness[n], sh[n,9,3] or
+    None).  Returns rgb[n, 3] (FP64)."""
+    mean = _c(scene["mean"], np.float32)
+    n = mean.shape[0]
+    normals = _c(normals, np.float32)
+    alb = _c(material["albedo"], np.float32)
+    rough = _c(material["roughness"], np.float32)
+    sh = None if material.get("sh") is None else _c(material["sh"], np.float32)
+    hemi = _c(hemi, np.float32)
+    V = _c(V, np.float64).reshape(n, hemi.shape[0])
+    env = _c(env_rgb, np.float64)
+    cam = _c(cam, np.float64)
+    rgb = np.empty((n, 3))
+    _load().oracle_pbr(n, _p(mean), _p(normals), _p(alb), _p(rough), _p(sh), hemi.shape[0], _p(hemi), _p(V),
+                       env.shape[0], env.shape[1], _p(env), _p(cam), _p(rgb))
+    return rgb
 
 
 def bf16_round(x) -> np.ndarray:

@@ -38,6 +38,12 @@
  *                      Gaussians' boxes) with boxes that cover every candidate
  *                      brute force accepts or flags; pinned against
  *                      oracle_trace, it reaches every ray of the large scenes.
+ *   oracle_hemi_rays / oracle_pbr
+ *                      the hemisphere direction set about each Gaussian's
+ *                      normal (Sec. 3.3, Fibonacci sampling) and the
+ *                      per-Gaussian PBR colour of Eq. 10 (simplified Disney
+ *                      BRDF of Eq. 9, light of Eq. 8: visibility x a global
+ *                      environment map plus degree-2 SH indirect light).
  *   oracle_mlp_*       the visibility surrogate (not in the paper): frequency
  *                      encoding, 4x128 ReLU MLP, sigmoid, BCE, Adam; bf16
  *                      rounding emulated where the GPU stores bf16, FP64
@@ -1121,5 +1127,255 @@ void oracle_adam_step(int64_t n, double *w, const double *g, double *mo, double 
         vo[i] = b2 * vo[i] + (1.0 - b2) * g[i] * g[i];
         double mh = mo[i] / c1, vh = vo[i] / c2;
         w[i] -= lr * mh / (sqrt(vh) + eps);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Hemisphere direction sets and the per-Gaussian PBR colour (Sec. 3.3)      */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Sec. 3.3 samples N_s incident directions per Gaussian over the hemisphere
+ * about its normal n (Fibonacci sampling) and Sec. 4.2 precomputes the
+ * visibility of those directions.  Ray id r = g*K + k of Gaussian g uses the
+ * local direction hemi[k] (z along the normal) in an orthonormal frame
+ * (t1, t2, n) built from the normal with the branchless construction of
+ * Duff et al. 2017 ("Building an orthonormal basis, revisited").  All in
+ * float32 with separately rounded operations, in this order:
+ *   s = (nx*nx + ny*ny) + nz*nz;  l = sqrt(s);  n = (nx/l, ny/l, nz/l)
+ *   sg = copysign(1, nz);  a = -1 / (sg + nz);  b = (nx*ny)*a
+ *   t1 = (1 + ((sg*nx)*nx)*a,  sg*b,  -(sg*nx))
+ *   t2 = (b,  sg + (ny*ny)*a,  -ny)
+ *   d_c = (h_x*t1_c + h_y*t2_c) + h_z*n_c
+ * and the origin fl(mu + fl(eps*d)) as in oracle_dir_rays.
+ */
+static void hemi_frame(const float *nin, float t1[3], float t2[3], float n[3])
+{
+    float s = nin[0] * nin[0] + nin[1] * nin[1];
+    s = s + nin[2] * nin[2];
+    float l = sqrtf(s);
+    n[0] = nin[0] / l;
+    n[1] = nin[1] / l;
+    n[2] = nin[2] / l;
+    float sg = copysignf(1.0f, n[2]);
+    float a = -1.0f / (sg + n[2]);
+    float b = (n[0] * n[1]) * a;
+    t1[0] = 1.0f + ((sg * n[0]) * n[0]) * a;
+    t1[1] = sg * b;
+    t1[2] = -(sg * n[0]);
+    t2[0] = b;
+    t2[1] = sg + (n[1] * n[1]) * a;
+    t2[2] = -n[1];
+}
+
+static void hemi_dir(const float *nin, const float *h, float d[3])
+{
+    float t1[3], t2[3], n[3];
+    hemi_frame(nin, t1, t2, n);
+    for (int c = 0; c < 3; ++c) {
+        float x = h[0] * t1[c] + h[1] * t2[c];
+        d[c] = x + h[2] * n[c];
+    }
+}
+
+void oracle_hemi_rays(int64_t n, const float *mean, const float *normals, int32_t K, const float *hemi,
+                      float eps, const int64_t *ids, int64_t m, float *ray_o, float *ray_d, int32_t *ray_src)
+{
+    (void)n;
+    for (int64_t i = 0; i < m; ++i) {
+        int64_t r = ids[i];
+        int64_t g = r / K;
+        int32_t k = (int32_t)(r % K);
+        float d[3];
+        hemi_dir(normals + 3 * g, hemi + 3 * k, d);
+        for (int c = 0; c < 3; ++c) {
+            float off = eps * d[c];
+            ray_o[3 * i + c] = mean[3 * g + c] + off;
+            ray_d[3 * i + c] = d[c];
+        }
+        ray_src[i] = (int32_t)g;
+    }
+}
+
+/*
+ * Simplified Disney BRDF of Sec. 3.3 (Eq. 9): f = f_d + f_s with f_d = b/pi
+ * and the microfacet specular term f_s = D F G / (4 (n.wi)(n.wo)).  Readings
+ * (the paper names D, F, G without formulas):
+ *   h  = (wi + wo)/|wi + wo|  (the half vector, normalised; f_s = 0 if wi = -wo);
+ *   D  = GGX / Trowbridge-Reitz with alpha = r^2:
+ *        alpha^2 / (pi ((n.h)^2 (alpha^2 - 1) + 1)^2);
+ *   F  = Schlick with F0 = 0.04 (the model has no metallic parameter):
+ *        F0 + (1 - F0)(1 - max(wo.h, 0))^5;
+ *   G  = Smith with Schlick-GGX, k = (r + 1)^2 / 8:
+ *        G1(x) = x / (x (1 - k) + k),  G = G1(n.wi) G1(n.wo);
+ *   the factor 4 of the microfacet model, which the printed Eq. 9 omits
+ *   (without it the specular lobe reflects more energy than it receives);
+ *   n.wi and n.wo clamped at 0; r clamped to [0.04, 1].
+ * G1(x)/x = 1/(x(1-k)+k) is used, so f_s stays finite at grazing angles.
+ * Inputs FP64 unit vectors.  fs_terms (may be NULL) gets D, F, G.
+ */
+#define PBR_F0 0.04
+#define PBR_RMIN 0.04
+
+static double spec_term(const double n[3], const double wi[3], const double wo[3], double r, double *Dout,
+                        double *Fout, double *Gout)
+{
+    if (r < PBR_RMIN) r = PBR_RMIN;
+    if (r > 1.0) r = 1.0;
+    double nl = n[0] * wi[0] + n[1] * wi[1] + n[2] * wi[2];
+    double nv = n[0] * wo[0] + n[1] * wo[1] + n[2] * wo[2];
+    if (nl < 0.0) nl = 0.0;
+    if (nv < 0.0) nv = 0.0;
+    double hv[3] = {wi[0] + wo[0], wi[1] + wo[1], wi[2] + wo[2]};
+    double hl = sqrt(hv[0] * hv[0] + hv[1] * hv[1] + hv[2] * hv[2]);
+    if (!(hl > 0.0)) {
+        if (Dout) *Dout = 0.0;
+        if (Fout) *Fout = 0.0;
+        if (Gout) *Gout = 0.0;
+        return 0.0;
+    }
+    for (int c = 0; c < 3; ++c) hv[c] /= hl;
+    double nh = n[0] * hv[0] + n[1] * hv[1] + n[2] * hv[2];
+    double vh = wo[0] * hv[0] + wo[1] * hv[1] + wo[2] * hv[2];
+    if (vh < 0.0) vh = 0.0;
+    double al = r * r, a2 = al * al;
+    double q = nh * nh * (a2 - 1.0) + 1.0;
+    double D = a2 / (M_PI * q * q);
+    double F = PBR_F0 + (1.0 - PBR_F0) * pow(1.0 - vh, 5.0);
+    double k = (r + 1.0) * (r + 1.0) / 8.0;
+    double gl = 1.0 / (nl * (1.0 - k) + k), gv = 1.0 / (nv * (1.0 - k) + k);  /* G1(x)/x */
+    if (Dout) *Dout = D;
+    if (Fout) *Fout = F;
+    if (Gout) *Gout = (nl * gl) * (nv * gv);
+    return D * F * gl * gv / 4.0;
+}
+
+void oracle_brdf_spec(int64_t m, const double *n, const double *wi, const double *wo, const double *rough,
+                      double *fs, double *terms)
+{
+    for (int64_t i = 0; i < m; ++i) {
+        double D, F, G;
+        fs[i] = spec_term(n + 3 * i, wi + 3 * i, wo + 3 * i, rough[i], &D, &F, &G);
+        if (terms) {
+            terms[3 * i] = D;
+            terms[3 * i + 1] = F;
+            terms[3 * i + 2] = G;
+        }
+    }
+}
+
+/*
+ * Indirect light of Sec. 3.3 ("3-level SH"): real spherical harmonics of
+ * degree 0..2 (9 functions) in the usual real basis, e.g. as in 3D Gaussian
+ * splatting: Y0 = c0; Y1..3 = -c1 y, c1 z, -c1 x; Y4..8 = c2a xy, -c2a yz,
+ * c2b (2z^2 - x^2 - y^2), -c2a xz, c2c (x^2 - y^2), with c0 = 1/(2 sqrt(pi)),
+ * c1 = sqrt(3/(4 pi)), c2a = sqrt(15/(4 pi)), c2b = sqrt(5/(16 pi)),
+ * c2c = sqrt(15/(16 pi)).
+ */
+static void sh9(const double w[3], double Y[9])
+{
+    const double c0 = 0.5 / sqrt(M_PI), c1 = sqrt(3.0 / (4.0 * M_PI)), c2a = sqrt(15.0 / (4.0 * M_PI)),
+                 c2b = sqrt(5.0 / (16.0 * M_PI)), c2c = sqrt(15.0 / (16.0 * M_PI));
+    double x = w[0], y = w[1], z = w[2];
+    Y[0] = c0;
+    Y[1] = -c1 * y;
+    Y[2] = c1 * z;
+    Y[3] = -c1 * x;
+    Y[4] = c2a * x * y;
+    Y[5] = -c2a * y * z;
+    Y[6] = c2b * (2.0 * z * z - x * x - y * y);
+    Y[7] = -c2a * x * z;
+    Y[8] = c2c * (x * x - y * y);
+}
+
+void oracle_sh_basis(int64_t m, const double *w, double *Y)
+{
+    for (int64_t i = 0; i < m; ++i) sh9(w + 3 * i, Y + 9 * i);
+}
+
+/*
+ * Direct light of Sec. 3.3: a global h x w environment map (16 x 32 in the
+ * paper), RGB, equirectangular: row i covers polar angles [i pi/h, (i+1) pi/h]
+ * from +z, column j azimuths [2 pi j/w, 2 pi (j+1)/w].  Reading: bilinear
+ * interpolation between pixel centres (continuous in the direction), wrapping
+ * in azimuth and clamped to the first and last rows in polar angle.
+ */
+static void env_bilinear(int32_t h, int32_t w, const double *env, const double d[3], double L[3])
+{
+    double z = d[2];
+    if (z > 1.0) z = 1.0;
+    if (z < -1.0) z = -1.0;
+    double th = acos(z);
+    double ph = atan2(d[1], d[0]);
+    if (ph < 0.0) ph += 2.0 * M_PI;
+    double v = th / M_PI * h - 0.5, u = ph / (2.0 * M_PI) * w - 0.5;
+    double fv = floor(v), fu = floor(u);
+    double bv = v - fv, bu = u - fu;
+    int64_t i0 = (int64_t)fv, j0 = (int64_t)fu;
+    int64_t i1 = i0 + 1, j1 = j0 + 1;
+    if (i0 < 0) i0 = 0;
+    if (i1 < 0) i1 = 0;
+    if (i0 > h - 1) i0 = h - 1;
+    if (i1 > h - 1) i1 = h - 1;
+    j0 = ((j0 % w) + w) % w;
+    j1 = ((j1 % w) + w) % w;
+    for (int c = 0; c < 3; ++c) {
+        double a = env[(i0 * w + j0) * 3 + c] * (1.0 - bu) + env[(i0 * w + j1) * 3 + c] * bu;
+        double b = env[(i1 * w + j0) * 3 + c] * (1.0 - bu) + env[(i1 * w + j1) * 3 + c] * bu;
+        L[c] = a * (1.0 - bv) + b * bv;
+    }
+}
+
+void oracle_env_lookup(int32_t h, int32_t w, const double *env, int64_t m, const double *dirs, double *L)
+{
+    for (int64_t i = 0; i < m; ++i) env_bilinear(h, w, env, dirs + 3 * i, L + 3 * i);
+}
+
+/*
+ * Per-Gaussian PBR colour, Eq. 10: for Gaussian g with normal n (the float32
+ * normal normalised in FP64), albedo b, roughness r, SH coefficients
+ * sh[g][9][3] (NULL: no indirect light) and view direction
+ * wo = (cam - mu)/|cam - mu|,
+ *   c'_c = sum_k (b_c/pi + f_s(wo, wi_k)) L_c(wi_k) max(n.wi_k, 0) (2 pi / K)
+ *   L_c(wi) = V[g,k] L_direct,c(wi) + max(0, sum_j sh[g][j][c] Y_j(wi))
+ * (Eq. 8: visibility times direct light plus indirect light; the solid angle
+ * of one of K directions on the hemisphere is 2 pi / K; reading: the
+ * indirect light is clamped at 0).  wi_k is ray k of Gaussian g from
+ * oracle_hemi_rays (float32, widened).  V[g*K + k] is the traced visibility.
+ */
+void oracle_pbr(int64_t n, const float *mean, const float *normals, const float *albedo, const float *rough,
+                const float *sh, int32_t K, const float *hemi, const double *V, int32_t h, int32_t w,
+                const double *env, const double *cam, double *rgb)
+{
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t g = 0; g < n; ++g) {
+        double nn[3] = {normals[3 * g], normals[3 * g + 1], normals[3 * g + 2]};
+        double l = sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
+        for (int c = 0; c < 3; ++c) nn[c] /= l;
+        double wo[3] = {cam[0] - mean[3 * g], cam[1] - mean[3 * g + 1], cam[2] - mean[3 * g + 2]};
+        double lo = sqrt(wo[0] * wo[0] + wo[1] * wo[1] + wo[2] * wo[2]);
+        for (int c = 0; c < 3; ++c) wo[c] /= lo;
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (int32_t k = 0; k < K; ++k) {
+            float df[3];
+            hemi_dir(normals + 3 * g, hemi + 3 * k, df);
+            double wi[3] = {df[0], df[1], df[2]};
+            double nl = nn[0] * wi[0] + nn[1] * wi[1] + nn[2] * wi[2];
+            if (nl < 0.0) nl = 0.0;
+            double fs = spec_term(nn, wi, wo, rough[g], NULL, NULL, NULL);
+            double Ld[3], Y[9];
+            env_bilinear(h, w, env, wi, Ld);
+            if (sh) sh9(wi, Y);
+            for (int c = 0; c < 3; ++c) {
+                double Li = V[g * K + k] * Ld[c];
+                if (sh) {
+                    double s = 0.0;
+                    for (int j = 0; j < 9; ++j) s += sh[(g * 9 + j) * 3 + c] * Y[j];
+                    if (s > 0.0) Li += s;
+                }
+                acc[c] += (albedo[3 * g + c] / M_PI + fs) * Li * nl;
+            }
+        }
+        for (int c = 0; c < 3; ++c) rgb[3 * g + c] = acc[c] * (2.0 * M_PI / K);
     }
 }

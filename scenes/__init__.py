@@ -222,6 +222,52 @@ def batch_scenes(sizes, seed_base: int = 300) -> list[dict]:
     return out
 
 
+def fibonacci_hemisphere(k: int) -> np.ndarray:
+    """k local directions on the hemisphere z > 0 (Fibonacci sampling):
+    z_i = 1 - (i + 1/2)/k, phi_i = i*pi*(3 - sqrt(5)); float64, rounded once."""
+    i = np.arange(k, dtype=np.float64)
+    z = 1.0 - (i + 0.5) / k
+    r = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    phi = i * math.pi * (3.0 - math.sqrt(5.0))
+    return _f32(np.stack([r * np.cos(phi), r * np.sin(phi), z], axis=1))
+
+
+def shortest_axis_normals(scale, quat) -> np.ndarray:
+    """Per-Gaussian normal: the rotation's column of the smallest scale (the
+    flattened axis), float64 then rounded once."""
+    q = np.asarray(quat, np.float64)
+    q = q / np.linalg.norm(q, axis=1, keepdims=True)
+    w, x, y, z = q.T
+    R = np.stack([
+        np.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)], 1),
+        np.stack([2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)], 1),
+        np.stack([2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], 1)], 1)
+    ax = np.argmin(np.asarray(scale), axis=1)
+    return _f32(R[np.arange(len(ax)), :, ax])
+
+
+def pbr_material(n: int, seed: int, with_sh: bool = True) -> dict:
+    """Per-Gaussian BRDF and indirect light: albedo U[0,1]^3, roughness
+    U[0,1], SH coefficients (9 per channel) N(0, 0.1^2) with the constant term
+    U[0, 0.5] (float32)."""
+    rng = np.random.default_rng(seed)
+    out = {"albedo": _f32(rng.uniform(0.0, 1.0, (n, 3))), "roughness": _f32(rng.uniform(0.0, 1.0, n)),
+           "sh": None}
+    if with_sh:
+        sh = rng.normal(0.0, 0.1, (n, 9, 3))
+        sh[:, 0, :] = rng.uniform(0.0, 0.5, (n, 3))
+        out["sh"] = _f32(sh)
+    return out
+
+
+def light_envmap(seed: int = 499, h: int = 16, w: int = 32, sigma: float = 1.0) -> np.ndarray:
+    """The direct light of the PBR colour: an h x w RGB equirectangular map,
+    log-normal radiance exp(sigma z), z ~ N(0,1) per pixel and channel
+    (float32, [h, w, 3])."""
+    rng = np.random.default_rng(seed)
+    return _f32(np.exp(sigma * rng.standard_normal((h, w, 3))))
+
+
 def batch_object_scenes(sizes, seed_base: int = 300) -> list[dict]:
     """One object-scale scene (``object_scene``) per size, seed seed_base+s,
     translated by a seeded offset U[-4,4]^3."""
