@@ -70,6 +70,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-pbr", action="store_true")
     ap.add_argument("--surrogate-steps", type=int, default=2000)
     ap.add_argument("--band", type=float, default=0.3)
     return ap.parse_args()
@@ -297,6 +298,54 @@ def run_surrogate(args, rt, torch, d, dirs, T, prm, dev):
         out_b["speedup_incl_training_not_amortised"] = tracer_ms / (fb_ms + train_ms)
         out["batches"].append(out_b)
     s.destroy()
+    bvh.destroy()
+    return out
+
+
+def run_pbr(rt, torch, d, sc, dev):
+    """Hemisphere workload of Sec. 3.3 / 4.2 on the bench scene: N_s = 64
+    Fibonacci directions about each Gaussian's normal (its shortest axis):
+    visibility table, the per-Gaussian PBR colour of Eq. 10 from that table,
+    the fused trace + shade (no table), and fused ambient occlusion."""
+    import scenes
+    n, K = sc["mean"].shape[0], 64
+    nrm = torch.from_numpy(scenes.shortest_axis_normals(sc["scale"], sc["quat"])).to(dev)
+    hemi = torch.from_numpy(scenes.fibonacci_hemisphere(K)).to(dev)
+    mat = scenes.pbr_material(n, 6)
+    env = torch.from_numpy(scenes.light_envmap(6)).to(dev)
+    inp = rt.pbr_inputs(torch.from_numpy(mat["albedo"]).to(dev), torch.from_numpy(mat["roughness"]).to(dev),
+                        env, (1.0, 3.0, 2.5), sh=torch.from_numpy(mat["sh"]).to(dev))
+    bvh = rt.rt_build_bvh(d["mean"], d["scale"], d["quat"], d["opacity"], rt.params())
+    rs = rt.rayspec(rt.RT_RAYS_HEMI, dirs=hemi, normals=nrm)
+    V = torch.empty(n * K, dtype=torch.float32, device=dev)
+    rgb = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    ao = torch.empty(n, dtype=torch.float32, device=dev)
+
+    def timed(f, reps):
+        f()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        torch.cuda.synchronize()
+        ev[0].record()
+        for _ in range(reps):
+            f()
+        ev[1].record()
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]) / reps
+
+    t_ms = timed(lambda: rt.rt_trace_visibility(bvh, rs, V), 2)
+    s_ms = timed(lambda: rt.rt_pbr_shade(bvh, rs, inp, V=V, rgb=rgb), 10)
+    f_ms = timed(lambda: rt.rt_pbr_shade(bvh, rs, inp, rgb=rgb), 2)
+    a_ms = timed(lambda: rt.rt_trace_ao(bvh, rs, ao), 2)
+    # bytes the shading kernel must move: the table, the per-Gaussian inputs
+    # (normal 12, albedo 12, roughness 4, SH 108, mean 16, rank 4) and the colour
+    shade_bytes = 4 * n * K + n * (12 + 12 + 4 + 108 + 16 + 4 + 12)
+    out = {"gaussians": n, "directions": K, "rays": n * K, "mean_visibility": float(V.mean()),
+           "trace_table_ms": t_ms, "trace_rays_per_s": n * K / (t_ms / 1000.0),
+           "shade_from_table_ms": s_ms, "shade_terms_per_s": n * K / (s_ms / 1000.0),
+           "shade_bytes_per_launch": shade_bytes, "shade_gbs": shade_bytes / (s_ms / 1000.0) / 1e9,
+           "table_plus_shade_ms": t_ms + s_ms, "fused_trace_shade_ms": f_ms,
+           "fused_gaussians_per_s": n / (f_ms / 1000.0), "fused_ao_ms": a_ms,
+           "mean_ao": float(ao.mean()), "rgb_max": float(rgb.max())}
     bvh.destroy()
     return out
 
@@ -564,6 +613,9 @@ def main():
     adjoint = None
     if not args.no_adjoint and rank == 0:
         adjoint = run_adjoint(rt, torch, dev)
+    pbr = None
+    if not args.no_pbr and rank == 0:
+        pbr = run_pbr(rt, torch, d, sc, dev)
 
     pk, pk_kind = peaks()
     tr_ms = statistics.mean(trace_ms)
@@ -594,7 +646,7 @@ def main():
                     "kernel": KERNEL_NAMES[args.kernel]}),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": (BUILD_KERNELS_PER_STEP + 1) * args.steps,
-                "clocks": clk, "surrogate": surrogate, "adjoint": adjoint}
+                "clocks": clk, "surrogate": surrogate, "adjoint": adjoint, "pbr": pbr}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()

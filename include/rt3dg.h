@@ -133,7 +133,9 @@ rt_status rt_envmap_destroy(rt_envmap *env, rt_stream_t stream);
 typedef enum {
     RT_RAYS_EXPLICIT = 0, /* ray_o[R*3], ray_d[R*3], ray_src[R] (or NULL)       */
     RT_RAYS_DIRS = 1,     /* from every Gaussian g along dirs[k]: id g*K + k     */
-    RT_RAYS_ENV = 2       /* from every Gaussian g, S env samples: id g*S + s    */
+    RT_RAYS_ENV = 2,      /* from every Gaussian g, S env samples: id g*S + s    */
+    RT_RAYS_HEMI = 3      /* from every Gaussian g over the hemisphere of its
+                             normal: local dirs[k] in g's frame, id g*K + k      */
 } rt_ray_kind;
 
 /* A ray set.  EXPLICIT: n_rays rays, ray_src[r] = original index of a
@@ -143,8 +145,16 @@ typedef enum {
  * Gaussian; sample s of Gaussian g (ray id r = g*S + s) draws Philox4x64-10
  * with counter (r,0,0,0) and key (seed,0): u0 = (x0>>11) 2^-53 picks the
  * pixel, a = (x1>>40) 2^-24 and b = (x2>>40) 2^-24 blend its corners.
- * If ray_ids (device int64[n_ids]) is set for DIRS/ENV, only those ray ids
- * are traced and outputs are indexed by position in ray_ids. */
+ * HEMI (Sec. 3.3: N_s incident directions per Gaussian over the hemisphere
+ * of its normal, Fibonacci sampling; Sec. 4.2 precomputes their visibility):
+ * K = n_dirs local directions dirs[K*3] with z along the normal (device,
+ * unit, z > 0) and normals[n*3] (device, original Gaussian order, non-zero).
+ * Ray r = g*K + k has direction d = (h_x t1 + h_y t2) + h_z n for h = dirs[k]
+ * in the frame (t1, t2, n) of g's normal normalised in float32, built by the
+ * branchless construction of Duff et al. 2017 (rt_materialize_rays gives the
+ * exact float32 rays), origin and exclusion as for DIRS.
+ * If ray_ids (device int64[n_ids]) is set for DIRS/ENV/HEMI, only those ray
+ * ids are traced and outputs are indexed by position in ray_ids. */
 typedef struct {
     int32_t kind;
     int32_t n_dirs;
@@ -157,6 +167,7 @@ typedef struct {
     uint64_t seed;
     const int64_t *ray_ids;
     int64_t n_ids;
+    const float *normals; /* HEMI only */
 } rt_rayspec;
 
 /* Number of rays of a ray set over `bvh` (n*K for DIRS, n*S for ENV, n_ids if
@@ -210,6 +221,57 @@ rt_status rt_trace_visibility(const rt_bvh *bvh, const rt_rayspec *rays, float *
  * Gaussians: T_out[n*k]. */
 rt_status rt_trace_visibility_dirs(const rt_bvh *bvh, const float *dirs, int32_t k, float *T_out,
                                    const rt_trace_opts *opts, rt_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Consumers of the visibility: per-Gaussian PBR colour (Eq. 8-10) and        */
+/* ambient occlusion                                                          */
+/* ------------------------------------------------------------------------ */
+
+/* Material and light of the PBR colour of Sec. 3.3 (all device arrays in the
+ * original Gaussian order unless stated):
+ *   albedo[n*3] in [0,1]; roughness[n] (clamped to [0.04, 1]);
+ *   sh[n*27] = coefficient j (0..8, real SH of degree 0..2) of colour channel
+ *     c at sh[(g*9 + j)*3 + c]: the per-Gaussian indirect light, clamped at 0
+ *     (NULL = no indirect light);
+ *   env[env_h*env_w*3] = the global RGB direct light, equirectangular, row i
+ *     over polar angles [i pi/h, (i+1) pi/h] from +z, column j over azimuths
+ *     [2 pi j/w, 2 pi (j+1)/w], looked up bilinearly between pixel centres
+ *     (azimuth wraps, polar angle clamps); env_h*env_w <= 8192;
+ *   cam = camera centre, host floats: wo = (cam - mu)/|cam - mu|.           */
+typedef struct {
+    const float *albedo;
+    const float *roughness;
+    const float *sh;
+    const float *env;
+    int32_t env_h, env_w;
+    float cam[3];
+    int32_t kernel; /* fused form: RT_KERNEL_AUTO, RT_KERNEL_WIDE (warp packet)
+                       or RT_KERNEL_RAY_WIDE (one thread per ray)           */
+} rt_pbr_inputs;
+
+/* Per-Gaussian PBR colour, Eq. 10, over the hemisphere ray set `rays`
+ * (RT_RAYS_HEMI, no ray_ids):
+ *   rgb[g*3+c] = sum_k (b_c/pi + f_s(wo, wi_k)) L_c(wi_k) max(n.wi_k, 0) 2pi/K,
+ *   L_c(wi) = V[g*K+k] L_direct,c(wi) + max(0, sum_j sh[g][j][c] Y_j(wi))
+ * with the simplified Disney BRDF of Eq. 9: f_s = D F G / (4 (n.wi)(n.wo)),
+ * GGX D with alpha = r^2, Schlick F with F0 = 0.04, Smith-Schlick G with
+ * k = (r+1)^2/8, normalised half vector, n.wi and n.wo clamped at 0.
+ * V[n*K] (device, the visibility of the rays as rt_trace_visibility writes
+ * it) or NULL: then the rays are traced in the same kernel and V is never
+ * written (one warp per 32 Morton-adjacent Gaussians, all K rays each).
+ * rgb[n*3] device output.  Errors: RT_ERR_INVALID_ARG (wrong ray kind,
+ * missing arrays, map too large). */
+rt_status rt_pbr_shade(const rt_bvh *bvh, const rt_rayspec *rays, const float *V, const rt_pbr_inputs *in,
+                       float *rgb, rt_stream_t stream);
+
+/* Ambient occlusion: ao[g] = (sum_k T(g, k)) / K, the mean visibility of
+ * Gaussian g over a full DIRS or HEMI ray set (no ray_ids), traced and
+ * reduced in one kernel without writing T (device output ao[n], original
+ * order; the sum runs over k in order, in float32).  opts: only `kernel` is
+ * read (RT_KERNEL_AUTO, RT_KERNEL_WIDE or RT_KERNEL_RAY_WIDE; NULL = AUTO).
+ * Errors: RT_ERR_INVALID_ARG. */
+rt_status rt_trace_ao(const rt_bvh *bvh, const rt_rayspec *rays, const rt_trace_opts *opts, float *ao,
+                      rt_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
 /* Adjoint                                                                    */

@@ -184,6 +184,13 @@ rt_status rt_rayset_dev(const rt_bvh *bvh, const rt_rayspec *rays, RaySetDev *ou
             out->dirs = rays->dirs;
             cnt = bvh->n * rays->n_dirs;
             break;
+        case RT_RAYS_HEMI:
+            if (rays->n_dirs <= 0 || !rays->dirs || (bvh->n > 0 && !rays->normals)) return RT_ERR_INVALID_ARG;
+            out->K = rays->n_dirs;
+            out->dirs = rays->dirs;
+            out->normals = rays->normals;
+            cnt = bvh->n * rays->n_dirs;
+            break;
         case RT_RAYS_ENV:
             if (rays->n_dirs <= 0 || !rays->env) return RT_ERR_INVALID_ARG;
             out->K = rays->n_dirs;

@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(128) k_backward(BvhDev b, RaySetDev rs, int64_
             const int32_t k = (int32_t)(rid - g * rs.K);
             src = b.rank[g];
             src_orig = (int32_t)g;
-            implicit_ray(rs, rid, k, __ldg(b.gauss + 4 * (int64_t)src), o, d);
+            implicit_ray(rs, rid, k, g, __ldg(b.gauss + 4 * (int64_t)src), o, d);
         }
         float3 d_origin = make_float3(0.f, 0.f, 0.f);
         const float Tr = T[r];

@@ -246,7 +246,7 @@ extern "C" rt_status rt_batch_create(const rt_batch_job *jobs, int32_t n_jobs, i
         const rt_batch_job &J = jobs[j];
         int64_t count = 0;
         RaySetDev rs;
-        rt_status r = (J.bvh && (J.rays.kind == RT_RAYS_DIRS || J.rays.kind == RT_RAYS_ENV) && !J.rays.ray_ids)
+        rt_status r = (J.bvh && J.rays.kind != RT_RAYS_EXPLICIT && !J.rays.ray_ids)
                           ? rt_rayset_dev(J.bvh, &J.rays, &rs, &count)
                           : RT_ERR_INVALID_ARG;
         if (r == RT_OK && count > 0 && !J.T_out) r = RT_ERR_INVALID_ARG;

@@ -132,6 +132,7 @@ struct RaySetDev {
     uint64_t seed;
     const int64_t *ray_ids;
     float eps;
+    const float *normals;  // HEMI: [n*3], original order
 };
 
 // Direction of env sample with ray id r (see rt3dg.h): pixel by binary
@@ -168,12 +169,44 @@ __device__ __forceinline__ float3 env_direction(const RaySetDev &rs, int64_t r) 
     return make_float3(__fdiv_rn(v[0], len), __fdiv_rn(v[1], len), __fdiv_rn(v[2], len));
 }
 
-// Ray r of an implicit set (DIRS / ENV) cast from the Gaussian at sorted
-// position p whose mean is mu: direction and origin fl(mu + fl(eps d)).
-__device__ __forceinline__ void implicit_ray(const RaySetDev &rs, int64_t r, int32_t k, float4 mu,
+// Frame (t1, t2, n) of a Gaussian's hemisphere set (Sec. 3.3): the normal
+// normalised in float32, then the branchless orthonormal basis of Duff et
+// al. 2017; every operation separately rounded (the oracle repeats them).
+struct HemiFrame {
+    float3 t1, t2, n;
+};
+
+__device__ __forceinline__ HemiFrame hemi_frame(const float *nrm) {
+    const float x = __ldg(nrm), y = __ldg(nrm + 1), z = __ldg(nrm + 2);
+    const float s = __fadd_rn(__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)), __fmul_rn(z, z));
+    const float l = __fsqrt_rn(s);
+    HemiFrame f;
+    f.n = make_float3(__fdiv_rn(x, l), __fdiv_rn(y, l), __fdiv_rn(z, l));
+    const float sg = copysignf(1.0f, f.n.z);
+    const float a = __fdiv_rn(-1.0f, __fadd_rn(sg, f.n.z));
+    const float b = __fmul_rn(__fmul_rn(f.n.x, f.n.y), a);
+    f.t1 = make_float3(__fadd_rn(1.0f, __fmul_rn(__fmul_rn(__fmul_rn(sg, f.n.x), f.n.x), a)), __fmul_rn(sg, b),
+                       -__fmul_rn(sg, f.n.x));
+    f.t2 = make_float3(b, __fadd_rn(sg, __fmul_rn(__fmul_rn(f.n.y, f.n.y), a)), -f.n.y);
+    return f;
+}
+
+// Local direction h (z along the normal) in the frame: (h.x t1 + h.y t2) + h.z n.
+__device__ __forceinline__ float3 hemi_rotate(const HemiFrame &f, const float *h) {
+    const float hx = __ldg(h), hy = __ldg(h + 1), hz = __ldg(h + 2);
+    return make_float3(__fadd_rn(__fadd_rn(__fmul_rn(hx, f.t1.x), __fmul_rn(hy, f.t2.x)), __fmul_rn(hz, f.n.x)),
+                       __fadd_rn(__fadd_rn(__fmul_rn(hx, f.t1.y), __fmul_rn(hy, f.t2.y)), __fmul_rn(hz, f.n.y)),
+                       __fadd_rn(__fadd_rn(__fmul_rn(hx, f.t1.z), __fmul_rn(hy, f.t2.z)), __fmul_rn(hz, f.n.z)));
+}
+
+// Ray r = g*K + k of an implicit set (DIRS / ENV / HEMI) cast from Gaussian g
+// (original index) whose mean is mu: direction and origin fl(mu + fl(eps d)).
+__device__ __forceinline__ void implicit_ray(const RaySetDev &rs, int64_t r, int32_t k, int64_t g, float4 mu,
                                              float3 &o, float3 &d) {
     if (rs.kind == RT_RAYS_DIRS) {
         d = make_float3(rs.dirs[3 * k], rs.dirs[3 * k + 1], rs.dirs[3 * k + 2]);
+    } else if (rs.kind == RT_RAYS_HEMI) {
+        d = hemi_rotate(hemi_frame(rs.normals + 3 * g), rs.dirs + 3 * k);
     } else {
         d = env_direction(rs, r);
     }

@@ -221,7 +221,7 @@ __device__ __forceinline__ bool get_sample(const SampleSrc &S, int64_t i, int64_
     const int64_t g = rid / S.rs.K;
     const int32_t k = (int32_t)(rid - g * S.rs.K);
     const int32_t ps = S.b.rank[g];
-    implicit_ray(S.rs, rid, k, __ldg(S.b.gauss + 4 * (int64_t)ps), p, d);
+    implicit_ray(S.rs, rid, k, g, __ldg(S.b.gauss + 4 * (int64_t)ps), p, d);
     y = S.T_target ? S.T_target[rid] : 0.0f;
     return true;
 }

@@ -233,7 +233,7 @@ __global__ void k_materialize(BvhDev b, RaySetDev rs, const int64_t *ids, int64_
         int32_t k = (int32_t)(rid - g * rs.K);
         int32_t p = b.rank[g];
         float3 o, d;
-        implicit_ray(rs, rid, k, __ldg(b.gauss + 4 * (int64_t)p), o, d);
+        implicit_ray(rs, rid, k, g, __ldg(b.gauss + 4 * (int64_t)p), o, d);
         ro[3 * i] = o.x; ro[3 * i + 1] = o.y; ro[3 * i + 2] = o.z;
         rd[3 * i] = d.x; rd[3 * i + 1] = d.y; rd[3 * i + 2] = d.z;
         if (rsrc) rsrc[i] = (int32_t)g;

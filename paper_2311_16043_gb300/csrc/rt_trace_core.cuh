@@ -541,7 +541,7 @@ __device__ __forceinline__ void trace_item(const BvhDev &b, const RaySetDev &rs,
             const float4 mu = __ldg(b.gauss + 4 * p);
             const int32_t g = __float_as_int(__ldg(b.gauss + 4 * p + 1).w);
             out_idx = (int64_t)g * rs.K + k;
-            implicit_ray(rs, out_idx, k, mu, o, d);
+            implicit_ray(rs, out_idx, k, g, mu, o, d);
             src = (int32_t)p;
         }
     } else {
@@ -567,7 +567,7 @@ __device__ __forceinline__ void trace_item(const BvhDev &b, const RaySetDev &rs,
                     const int32_t k = (int32_t)(rid - g * rs.K);
                     const int32_t p = b.rank[g];
                     const float4 mu = __ldg(b.gauss + 4 * (int64_t)p);
-                    implicit_ray(rs, rid, k, mu, o, d);
+                    implicit_ray(rs, rid, k, g, mu, o, d);
                     src = p;
                 }
             }

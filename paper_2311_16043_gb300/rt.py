@@ -22,7 +22,7 @@ RT_OK = 0
 STATUS_NAMES = {0: "RT_OK", 1: "RT_ERR_INVALID_ARG", 2: "RT_ERR_OOM", 3: "RT_ERR_CUDA",
                 4: "RT_ERR_STACK_OVERFLOW", 5: "RT_ERR_HITLOG_OVERFLOW", 6: "RT_ERR_TIMEOUT",
                 7: "RT_ERR_NOT_TRAINED", 8: "RT_ERR_UNSUPPORTED"}
-RT_RAYS_EXPLICIT, RT_RAYS_DIRS, RT_RAYS_ENV = 0, 1, 2
+RT_RAYS_EXPLICIT, RT_RAYS_DIRS, RT_RAYS_ENV, RT_RAYS_HEMI = 0, 1, 2, 3
 RT_KERNEL_AUTO, RT_KERNEL_RAY, RT_KERNEL_PACKET, RT_KERNEL_WIDE, RT_KERNEL_RAY_WIDE = 0, 1, 2, 3, 4
 
 
@@ -41,13 +41,18 @@ class rt_rayspec(C.Structure):
     _fields_ = [("kind", C.c_int32), ("n_dirs", C.c_int32), ("n_rays", C.c_int64),
                 ("ray_o", C.c_void_p), ("ray_d", C.c_void_p), ("ray_src", C.c_void_p),
                 ("dirs", C.c_void_p), ("env", C.c_void_p), ("seed", C.c_uint64),
-                ("ray_ids", C.c_void_p), ("n_ids", C.c_int64)]
+                ("ray_ids", C.c_void_p), ("n_ids", C.c_int64), ("normals", C.c_void_p)]
 
 
 class rt_trace_opts(C.Structure):
     _fields_ = [("kernel", C.c_int32), ("order_block", C.c_int32), ("block_threads", C.c_int32),
                 ("hit_cap", C.c_int32), ("counters", C.c_void_p), ("hit_ids", C.c_void_p),
                 ("hit_count", C.c_void_p)]
+
+
+class rt_pbr_inputs(C.Structure):
+    _fields_ = [("albedo", C.c_void_p), ("roughness", C.c_void_p), ("sh", C.c_void_p), ("env", C.c_void_p),
+                ("env_h", C.c_int32), ("env_w", C.c_int32), ("cam", C.c_float * 3), ("kernel", C.c_int32)]
 
 
 class rt_batch_job(C.Structure):
@@ -97,6 +102,8 @@ _SIGS = {
     "rt_surrogate_infer": (_I32, [_P, _P, _P, _F32, _P, _P, _P]),
     "rt_surrogate_infer_noalloc": (_I32, [_P, _P, _P, _F32, _P, _P, _P]),
     "rt_trace_autotune": (_I32, [_P, _P, _P, _P, _P]),
+    "rt_pbr_shade": (_I32, [_P, _P, _P, _P, _P, _P]),
+    "rt_trace_ao": (_I32, [_P, _P, _P, _P, _P]),
     "rt_batch_create": (_I32, [_P, _I32, _I32, _P, _P]),
     "rt_batch_run": (_I32, [_P, _P]),
     "rt_batch_info": (_I32, [_P, _P, _P, _P, _P]),
@@ -246,7 +253,7 @@ def rt_envmap_create(radiance, solid_angle, corners, stream=None) -> Envmap:
 
 
 def rayspec(kind=RT_RAYS_DIRS, *, dirs=None, ray_o=None, ray_d=None, ray_src=None, env=None,
-            n_samples=0, seed=0, ray_ids=None) -> rt_rayspec:
+            n_samples=0, seed=0, ray_ids=None, normals=None) -> rt_rayspec:
     rs = rt_rayspec()
     rs.kind = kind
     if kind == RT_RAYS_EXPLICIT:
@@ -261,10 +268,14 @@ def rayspec(kind=RT_RAYS_DIRS, *, dirs=None, ray_o=None, ray_d=None, ray_src=Non
         rs.n_dirs = n_samples
         rs.env = env.handle
         rs.seed = seed
+    elif kind == RT_RAYS_HEMI:
+        rs.n_dirs = dirs.shape[0]
+        rs.dirs = _ptr(dirs, torch.float32, "dirs")
+        rs.normals = _ptr(normals, torch.float32, "normals")
     if ray_ids is not None:
         rs.ray_ids = _ptr(ray_ids, torch.int64, "ray_ids")
         rs.n_ids = ray_ids.numel()
-    rs._keep = (dirs, ray_o, ray_d, ray_src, env, ray_ids)  # keep the tensors alive
+    rs._keep = (dirs, ray_o, ray_d, ray_src, env, ray_ids, normals)  # keep the tensors alive
     return rs
 
 
@@ -308,6 +319,42 @@ def rt_trace_visibility_dirs(bvh: Bvh, dirs, T_out=None, opts: rt_trace_opts | N
                                           C.byref(opts) if opts is not None else None, _stream(stream)),
            "rt_trace_visibility_dirs")
     return T_out
+
+
+def pbr_inputs(albedo, roughness, env, cam, sh=None, kernel=RT_KERNEL_AUTO) -> rt_pbr_inputs:
+    """Material and light of the PBR colour: albedo[n,3], roughness[n],
+    sh[n,9,3] or None, env[h,w,3] (device float32), cam (3 floats)."""
+    p = rt_pbr_inputs()
+    p.albedo = _ptr(albedo, torch.float32, "albedo")
+    p.roughness = _ptr(roughness, torch.float32, "roughness")
+    p.sh = _ptr(sh, torch.float32, "sh")
+    p.env = _ptr(env, torch.float32, "env")
+    p.env_h, p.env_w = int(env.shape[0]), int(env.shape[1])
+    for i in range(3):
+        p.cam[i] = float(cam[i])
+    p.kernel = kernel
+    p._keep = (albedo, roughness, sh, env)
+    return p
+
+
+def rt_pbr_shade(bvh: Bvh, rs: rt_rayspec, inputs: rt_pbr_inputs, V=None, rgb=None, stream=None):
+    """Per-Gaussian PBR colour (Eq. 10) of the hemisphere set rs: from the
+    visibility table V[n*K] or, with V=None, tracing the rays in the same
+    kernel.  Returns rgb[n, 3]."""
+    if rgb is None:
+        rgb = torch.empty((bvh.n, 3), dtype=torch.float32, device="cuda")
+    _check(lib().rt_pbr_shade(bvh.handle, C.byref(rs), _ptr(V, torch.float32, "V"), C.byref(inputs),
+                              _ptr(rgb, torch.float32, "rgb"), _stream(stream)), "rt_pbr_shade")
+    return rgb
+
+
+def rt_trace_ao(bvh: Bvh, rs: rt_rayspec, ao=None, opts: rt_trace_opts | None = None, stream=None):
+    """Mean visibility of each Gaussian over a full DIRS or HEMI ray set."""
+    if ao is None:
+        ao = torch.empty(bvh.n, dtype=torch.float32, device="cuda")
+    _check(lib().rt_trace_ao(bvh.handle, C.byref(rs), C.byref(opts) if opts is not None else None,
+                             _ptr(ao, torch.float32, "ao"), _stream(stream)), "rt_trace_ao")
+    return ao
 
 
 def rt_materialize_rays(bvh: Bvh, rs: rt_rayspec, ray_ids, stream=None):
