@@ -71,6 +71,7 @@ def parse():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-pbr", action="store_true")
+    ap.add_argument("--no-refit", action="store_true")
     ap.add_argument("--surrogate-steps", type=int, default=2000)
     ap.add_argument("--band", type=float, default=0.3)
     return ap.parse_args()
@@ -350,6 +351,46 @@ def run_pbr(rt, torch, d, sc, dev):
     return out
 
 
+def run_refit(rt, torch, d, sc, dirs, opts, dev):
+    """Refit-only rebuild on the bench scene: refit time against a full build,
+    and the trace after the means move by N(0, 1 mm) — refit (stale Morton
+    order) against a fresh build of the moved scene."""
+    def timed(f, reps):
+        f()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        torch.cuda.synchronize()
+        ev[0].record()
+        for _ in range(reps):
+            f()
+        ev[1].record()
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]) / reps
+
+    prm = rt.params()
+    n, K = sc["mean"].shape[0], dirs.shape[0]
+    T = torch.empty(n * K, dtype=torch.float32, device=dev)
+    holder = []
+
+    def build():
+        if holder:
+            holder.pop().destroy()
+        holder.append(rt.rt_build_bvh(d["mean"], d["scale"], d["quat"], d["opacity"], prm))
+
+    build_ms = timed(build, 10)
+    bvh = holder.pop()
+    refit_ms = timed(lambda: rt.rt_bvh_refit(bvh, d["mean"], d["scale"], d["quat"], d["opacity"]), 10)
+    moved = (d["mean"] + 1e-3 * torch.randn(d["mean"].shape, generator=torch.Generator(device=dev).manual_seed(7),
+                                             device=dev)).contiguous()
+    rt.rt_bvh_refit(bvh, moved, d["scale"], d["quat"], d["opacity"])
+    t_refit = timed(lambda: rt.rt_trace_visibility_dirs(bvh, dirs, T, opts), 1)
+    fresh = rt.rt_build_bvh(moved, d["scale"], d["quat"], d["opacity"], prm)
+    t_fresh = timed(lambda: rt.rt_trace_visibility_dirs(fresh, dirs, T, opts), 1)
+    fresh.destroy()
+    bvh.destroy()
+    return {"build_ms": build_ms, "refit_ms": refit_ms, "motion": "means + N(0, 1e-3^2)",
+            "trace_ms_after_refit": t_refit, "trace_ms_after_fresh_build": t_fresh}
+
+
 def run_adjoint(rt, torch, dev):
     """Differentiation workload: L = sum_r w_r T_r over the rays of the first
     1,024 Gaussians of a 4,096-Gaussian uniform scene x 16 directions, and
@@ -616,6 +657,9 @@ def main():
     pbr = None
     if not args.no_pbr and rank == 0:
         pbr = run_pbr(rt, torch, d, sc, dev)
+    refit = None
+    if not args.no_refit and rank == 0:
+        refit = run_refit(rt, torch, d, sc, dirs, opts, dev)
 
     pk, pk_kind = peaks()
     tr_ms = statistics.mean(trace_ms)
@@ -646,7 +690,7 @@ def main():
                     "kernel": KERNEL_NAMES[args.kernel]}),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": (BUILD_KERNELS_PER_STEP + 1) * args.steps,
-                "clocks": clk, "surrogate": surrogate, "adjoint": adjoint, "pbr": pbr}
+                "clocks": clk, "surrogate": surrogate, "adjoint": adjoint, "pbr": pbr, "refit": refit}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()

@@ -100,6 +100,18 @@ rt_status rt_build_bvh(const float *mean, const float *scale, const float *quat,
                        const float *opacity, int64_t n, const rt_params *params,
                        rt_stream_t stream, rt_bvh **out);
 rt_status rt_bvh_destroy(rt_bvh *bvh, rt_stream_t stream);
+/* Refit-only rebuild: the same n Gaussians (same order) with new mean, scale,
+ * quat and opacity keep the tree's topology (Morton order, binary and 4-wide
+ * structure); the Gaussian records, leaf boxes and every internal box are
+ * recomputed bottom-up (Sec. 4.1's refit step alone).  For geometry that
+ * moves during optimisation; traversal stays exact for any input (boxes
+ * always contain the supports), it only loses efficiency as the Morton order
+ * goes stale.  The scene bounds reported by rt_bvh_info stay those of the
+ * build.  Asynchronous on `stream` (the first call also derives the 4-wide
+ * tree's parent links once).  Refitting with the build's inputs reproduces
+ * the built tree bit for bit.  Errors: RT_ERR_INVALID_ARG. */
+rt_status rt_bvh_refit(rt_bvh *bvh, const float *mean, const float *scale, const float *quat,
+                       const float *opacity, rt_stream_t stream);
 /* Host outputs (any may be NULL): Gaussian count, scene bounds of the means
  * (float[3] each), device bytes held by the handle. */
 rt_status rt_bvh_info(const rt_bvh *bvh, int64_t *n, float *lo, float *hi, int64_t *device_bytes);

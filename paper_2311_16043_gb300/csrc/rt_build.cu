@@ -435,6 +435,71 @@ __global__ void k_collapse4(const float4 *__restrict__ nodes, const int2 *__rest
     }
 }
 
+// Refit links of the 4-wide tree: where each leaf and each wide node sits in
+// its wide parent (4*w + slot; the root has none).
+__global__ void k_wide_links(const float4 *__restrict__ wide, int64_t n_wide, int32_t *leaf_slot,
+                             int32_t *wide_parent) {
+    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < n_wide;
+         w += (int64_t)gridDim.x * blockDim.x) {
+        const float4 r = wide[8 * w + 6];
+        const uint32_t ref[4] = {__float_as_uint(r.x), __float_as_uint(r.y), __float_as_uint(r.z),
+                                 __float_as_uint(r.w)};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            if (ref[c] == RT_EMPTY) continue;
+            if (ref[c] & RT_LEAF_BIT) leaf_slot[ref[c] & ~RT_LEAF_BIT] = (int32_t)(4 * w + c);
+            else wide_parent[ref[c]] = (int32_t)(4 * w + c);
+        }
+        if (w == 0) wide_parent[0] = -1;
+    }
+}
+
+// Bottom-up refit of the 4-wide tree with its slots kept: each leaf stores its
+// box into its slot and bumps the node's arrival count; the arrival that
+// completes the node's children forms the union and climbs to the node's own
+// slot in its parent.  No thread waits (as k_refit).
+__global__ void k_refit_wide(const float *__restrict__ leafbox, const int32_t *__restrict__ leaf_slot,
+                             const int32_t *__restrict__ wide_parent, int64_t n, float4 *wide,
+                             uint32_t *arrivals) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        float b[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) b[c] = leafbox[6 * p + c];  // lo xyz, hi xyz
+        int32_t slot = leaf_slot[p];
+        while (slot >= 0) {
+            const int64_t w = slot >> 2;
+            const int c = slot & 3;
+            float *wf = reinterpret_cast<float *>(wide + 8 * w);
+            // SoA rows: lo.x, hi.x, lo.y, hi.y, lo.z, hi.z
+            __stcg(wf + 0 + c, b[0]); __stcg(wf + 4 + c, b[3]);
+            __stcg(wf + 8 + c, b[1]); __stcg(wf + 12 + c, b[4]);
+            __stcg(wf + 16 + c, b[2]); __stcg(wf + 20 + c, b[5]);
+            __threadfence();
+            const float4 r = __ldcg(wide + 8 * w + 6);
+            const uint32_t ref[4] = {__float_as_uint(r.x), __float_as_uint(r.y), __float_as_uint(r.z),
+                                     __float_as_uint(r.w)};
+            uint32_t m = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) m += ref[k] != RT_EMPTY;
+            if (atomicAdd(&arrivals[w], 1u) + 1u < m) break;
+            __threadfence();
+            float u[6] = {__int_as_float(0x7fc00000), __int_as_float(0x7fc00000), __int_as_float(0x7fc00000),
+                          __int_as_float(0x7fc00000), __int_as_float(0x7fc00000), __int_as_float(0x7fc00000)};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (ref[k] == RT_EMPTY) continue;
+                u[0] = fminf(u[0], __ldcg(wf + 0 + k)); u[3] = fmaxf(u[3], __ldcg(wf + 4 + k));
+                u[1] = fminf(u[1], __ldcg(wf + 8 + k)); u[4] = fmaxf(u[4], __ldcg(wf + 12 + k));
+                u[2] = fminf(u[2], __ldcg(wf + 16 + k)); u[5] = fmaxf(u[5], __ldcg(wf + 20 + k));
+            }
+#pragma unroll
+            for (int k = 0; k < 6; ++k) b[k] = u[k];
+            slot = wide_parent[w];
+        }
+    }
+}
+
 __global__ void k_export_boxes(const float4 *__restrict__ nodes, int64_t m, float *boxes,
                                int32_t *left, int32_t *right) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
@@ -506,6 +571,9 @@ extern "C" rt_status rt_build_bvh(const float *mean, const float *scale, const f
     b->bounds = (float *)(base + off_bnd);
     b->wide = (float4 *)(base + off_wide);
     b->n_wide = 0;
+    b->links = nullptr;
+    b->leaf_slot = b->wide_parent = nullptr;
+    b->wide_arrivals = nullptr;
     for (int c = 0; c < 3; ++c) b->lo[c] = b->hi[c] = 0.f;
     if (n == 0) {
         *out = b;
@@ -622,8 +690,76 @@ extern "C" rt_status rt_build_bvh(const float *mean, const float *scale, const f
     return RT_OK;
 }
 
+extern "C" rt_status rt_bvh_refit(rt_bvh *b, const float *mean, const float *scale, const float *quat,
+                                  const float *opacity, rt_stream_t stream) {
+    if (!b) return RT_ERR_INVALID_ARG;
+    const int64_t n = b->n;
+    if (n == 0) return RT_OK;
+    if (!mean || !scale || !quat || !opacity) return RT_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t ni = n > 1 ? n - 1 : 0;
+    if (b->n_wide > 0 && !b->links) {
+        const size_t o_par = align256(4 * (size_t)n), o_arr = o_par + align256(4 * (size_t)b->n_wide);
+        RT_TRY(rt_alloc(&b->links, o_arr + align256(4 * (size_t)b->n_wide), stream));
+        b->leaf_slot = (int32_t *)b->links;
+        b->wide_parent = (int32_t *)((char *)b->links + o_par);
+        b->wide_arrivals = (uint32_t *)((char *)b->links + o_arr);
+        // -1 everywhere first: a slot the links never set ends the climb
+        rt_status r = RT_OK;
+        if (cudaMemsetAsync(b->links, 0xff, o_arr, st) != cudaSuccess) r = RT_ERR_CUDA;
+        if (r == RT_OK) {
+            k_wide_links<<<grid_for(b->n_wide, 256), 256, 0, st>>>(b->wide, b->n_wide, b->leaf_slot,
+                                                                    b->wide_parent);
+            r = rt_check_launch();
+        }
+        if (r != RT_OK) {
+            rt_free(b->links, stream);
+            b->links = nullptr;
+            return r;
+        }
+    }
+    // scratch: bounds (6 u32) | leaf boxes | binary arrivals
+    const size_t s_leaf = 256, s_arr = s_leaf + align256(24 * (size_t)n);
+    void *scratch = nullptr;
+    RT_TRY(rt_alloc(&scratch, s_arr + align256(4 * (size_t)ni) + 256, stream));
+    char *sb = (char *)scratch;
+    uint32_t *bounds_u = (uint32_t *)sb;
+    float *leafbox = (float *)(sb + s_leaf);
+    uint32_t *arrivals = (uint32_t *)(sb + s_arr);
+    rt_status result = RT_OK;
+    do {
+        if (cudaMemsetAsync(bounds_u, 0xff, 12, st) != cudaSuccess ||
+            cudaMemsetAsync(bounds_u + 3, 0, 12, st) != cudaSuccess) {
+            result = RT_ERR_CUDA;
+            break;
+        }
+        k_bounds<<<grid_for(n, 256), 256, 0, st>>>(mean, n, bounds_u);
+        k_prep<<<grid_for(n, 128), 128, 0, st>>>(mean, scale, quat, opacity, b->perm, n, b->params, bounds_u,
+                                                 b->gauss, leafbox);
+        if (n > 1) {
+            if (cudaMemsetAsync(arrivals, 0, 4 * (size_t)ni, st) != cudaSuccess) {
+                result = RT_ERR_CUDA;
+                break;
+            }
+            k_refit<<<grid_for(n, 256), 256, 0, st>>>(leafbox, b->parent, n, b->nodes, arrivals);
+        }
+        if (b->n_wide > 0) {
+            if (cudaMemsetAsync(b->wide_arrivals, 0, 4 * (size_t)b->n_wide, st) != cudaSuccess) {
+                result = RT_ERR_CUDA;
+                break;
+            }
+            k_refit_wide<<<grid_for(n, 256), 256, 0, st>>>(leafbox, b->leaf_slot, b->wide_parent, n, b->wide,
+                                                           b->wide_arrivals);
+        }
+        result = rt_check_launch();
+    } while (0);
+    rt_free(scratch, stream);
+    return result;
+}
+
 extern "C" rt_status rt_bvh_destroy(rt_bvh *bvh, rt_stream_t stream) {
     if (!bvh) return RT_ERR_INVALID_ARG;
+    if (bvh->links) rt_free(bvh->links, stream);
     rt_free(bvh->block, stream);
     delete bvh;
     return RT_OK;

@@ -53,6 +53,13 @@ struct rt_bvh {
     float *bounds;           // [6] device copy of lo, hi
     float4 *wide;            // [8 * (n-1)] 4-wide nodes (collapsed binary tree)
     int64_t n_wide;          // number of 4-wide nodes (host copy)
+    // refit links, made by the first rt_bvh_refit: 4*w + slot of each leaf
+    // (sorted position) and of each wide node in its wide parent (root: -1),
+    // and per-wide-node arrival counters
+    void *links;
+    int32_t *leaf_slot;      // [n]
+    int32_t *wide_parent;    // [n_wide]
+    uint32_t *wide_arrivals; // [n_wide]
 };
 
 struct rt_envmap {

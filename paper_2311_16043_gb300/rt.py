@@ -77,6 +77,7 @@ _SIGS = {
     "rt_selftest_wait_timeout": (_I32, [_I64, _P]),
     "rt_build_bvh": (_I32, [_P, _P, _P, _P, _I64, _P, _P, _P]),
     "rt_bvh_destroy": (_I32, [_P, _P]),
+    "rt_bvh_refit": (_I32, [_P, _P, _P, _P, _P, _P]),
     "rt_bvh_info": (_I32, [_P, _P, _P, _P, _P]),
     "rt_bvh_export": (_I32, [_P, _P, _P, _P, _P, _P, _P]),
     "rt_envmap_create": (_I32, [_P, _P, _P, _I32, _I32, _P, _P]),
@@ -210,6 +211,19 @@ def rt_build_bvh(mean, scale, quat, opacity, prm: rt_params | None = None, strea
                               _ptr(quat, torch.float32, "quat"), _ptr(opacity, torch.float32, "opacity"),
                               n, C.byref(prm), _stream(stream), C.byref(h)), "rt_build_bvh")
     return Bvh(h, n, prm)
+
+
+def rt_bvh_refit(bvh: Bvh, mean, scale, quat, opacity, stream=None) -> Bvh:
+    """Refit-only rebuild: new parameters of the same Gaussians, same tree
+    topology, every box recomputed."""
+    n = bvh.n
+    for name, t, w in (("mean", mean, 3), ("scale", scale, 3), ("quat", quat, 4), ("opacity", opacity, 1)):
+        if t.numel() != n * w:
+            raise ValueError(f"{name} must hold {n} x {w} values")
+    _check(lib().rt_bvh_refit(bvh.handle, _ptr(mean, torch.float32, "mean"), _ptr(scale, torch.float32, "scale"),
+                              _ptr(quat, torch.float32, "quat"), _ptr(opacity, torch.float32, "opacity"),
+                              _stream(stream)), "rt_bvh_refit")
+    return bvh
 
 
 def rt_bvh_export(bvh: Bvh, stream=None) -> dict:
