@@ -1,0 +1,88 @@
+"""Pins of the oracle's composed-scene tracer (CPU only): one instance under
+the identity map is the plain object; a composition equals the union scene
+(every Gaussian moved to the world in FP64, brute force); and a rigid motion
+of the whole composition (instances and directions) leaves T unchanged."""
+import numpy as np
+from scipy.spatial.transform import Rotation
+
+import scenes
+
+TOL = 1e-5
+
+
+def _xform(R, t):
+    return np.concatenate([np.asarray(R, np.float64), np.asarray(t, np.float64)[:, None]], 1).astype(np.float32)
+
+
+def _composition(seed=0, n_inst=4):
+    rng = np.random.default_rng(seed)
+    objs = [scenes.uniform_scene(600, 31, lo=-0.5, hi=0.5), scenes.uniform_scene(400, 32, lo=-0.4, hi=0.4)]
+    objects, xforms = [], []
+    for i in range(n_inst):
+        R = Rotation.random(random_state=int(rng.integers(1 << 30))).as_matrix()
+        objects.append(objs[i % 2])
+        xforms.append(_xform(R, rng.uniform(-0.4, 0.4, 3)))
+    return objects, xforms
+
+
+def _world_union(objects, xforms):
+    """Every Gaussian moved into the world in FP64: mean R mu + t, rotation
+    R R_q (so Sigma_w = R Sigma R^T)."""
+    out = {"mean": [], "scale": [], "quat": [], "opacity": []}
+    for sc, xf in zip(objects, xforms):
+        X = xf.astype(np.float64)
+        R, t = X[:, :3], X[:, 3]
+        out["mean"].append(sc["mean"].astype(np.float64) @ R.T + t)
+        q = sc["quat"].astype(np.float64)
+        rq = Rotation.from_matrix(R) * Rotation.from_quat(np.concatenate([q[:, 1:], q[:, :1]], 1))
+        xyzw = rq.as_quat()
+        out["quat"].append(np.concatenate([xyzw[:, 3:], xyzw[:, :3]], 1))
+        out["scale"].append(sc["scale"].astype(np.float64))
+        out["opacity"].append(sc["opacity"].astype(np.float64))
+    return {k: np.concatenate(v) for k, v in out.items()}
+
+
+def test_identity_instance_is_the_object(orc):
+    sc = scenes.uniform_scene(2000, 5)
+    dirs = scenes.fibonacci_sphere(16)
+    eye = _xform(np.eye(3), np.zeros(3))
+    o, d, si, sl = orc.instance_world_rays([sc], [eye], dirs)
+    got = orc.trace_instances([sc], [eye], o, d, si, sl)
+    ref = orc.BvhTracer(sc).trace_dirs(dirs, t_min=1e-4)
+    o2, d2, s2 = orc.dir_rays(sc["mean"], dirs, np.arange(2000 * 16))
+    np.testing.assert_array_equal(o, o2)
+    np.testing.assert_array_equal(sl, s2)
+    full = ref["T"] > 0
+    np.testing.assert_allclose(got["T"], ref["T"], atol=1e-14)
+    np.testing.assert_array_equal(got["flags"][full], ref["flags"][full])
+
+
+def test_composition_is_the_union_scene(orc):
+    objects, xforms = _composition()
+    dirs = scenes.fibonacci_sphere(8)
+    o, d, si, sl = orc.instance_world_rays(objects, xforms, dirs)
+    got = orc.trace_instances(objects, xforms, o, d, si, sl)
+    world = _world_union(objects, xforms)
+    base = np.cumsum([0] + [sc["mean"].shape[0] for sc in objects])[:-1]
+    src = (base[si] + sl).astype(np.int32)
+    ref = orc.trace(world, o, d, src)
+    ok = (ref["flags"] == 0) & (got["flags"] == 0)
+    assert ok.mean() > 0.99
+    assert np.abs(got["T"] - ref["T"])[ok].max() <= TOL
+    assert (got["T"] < 0.5).mean() > 0.2  # the instances do shadow each other
+
+
+def test_rigid_motion_of_the_composition(orc):
+    objects, xforms = _composition(1)
+    dirs = scenes.fibonacci_sphere(8)
+    o, d, si, sl = orc.instance_world_rays(objects, xforms, dirs)
+    a = orc.trace_instances(objects, xforms, o, d, si, sl)
+    G = Rotation.random(random_state=7).as_matrix()
+    g = np.array([0.3, -1.2, 2.0])
+    moved = [_xform(G @ x[:, :3].astype(np.float64), G @ x[:, 3].astype(np.float64) + g) for x in xforms]
+    dirs2 = (dirs.astype(np.float64) @ G.T).astype(np.float32)
+    o2, d2, si2, sl2 = orc.instance_world_rays(objects, moved, dirs2)
+    b = orc.trace_instances(objects, moved, o2, d2, si2, sl2)
+    ok = (a["flags"] == 0) & (b["flags"] == 0)
+    assert ok.mean() > 0.99
+    assert np.abs(a["T"] - b["T"])[ok].max() <= TOL
