@@ -235,6 +235,49 @@ rt_status rt_trace_visibility_dirs(const rt_bvh *bvh, const float *dirs, int32_t
                                    const rt_trace_opts *opts, rt_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
+/* Composed scenes: a two-level BVH over object instances (Sec. 4.3)         */
+/* ------------------------------------------------------------------------ */
+
+/* Sec. 4.3 composes reconstructed objects into a new scene and re-traces the
+ * visibility so that objects shadow each other.  An instance places an
+ * object's tree (built in the object's local frame, kept and shared) in the
+ * world by a rigid map: world = R local + t with xform = [R | t] row-major
+ * 3x4 (host floats; R orthonormal).  Instances may share a tree; all trees
+ * must have equal rt_params. */
+typedef struct {
+    const rt_bvh *bvh;
+    float xform[12];
+} rt_instance;
+
+typedef struct rt_scene rt_scene;
+
+/* Builds the top-level tree over the instances' world boxes (host, median
+ * splits; synchronises `stream` to read each object's root box).  The scene
+ * keeps pointers to the trees: they must outlive it.  Errors:
+ * RT_ERR_INVALID_ARG (no instances, differing params, non-finite xform),
+ * RT_ERR_UNSUPPORTED (a tree without its 4-wide form). */
+rt_status rt_scene_create(const rt_instance *inst, int32_t n_inst, rt_stream_t stream, rt_scene **out);
+/* New transforms for the same instances (same trees, same order): only the
+ * top level is rebuilt; objects refitted since are re-read.  Synchronous. */
+rt_status rt_scene_update(rt_scene *scene, const rt_instance *inst, int32_t n_inst, rt_stream_t stream);
+/* Total Gaussians (sum over instances) and instance count. */
+rt_status rt_scene_info(const rt_scene *scene, int64_t *n_total, int32_t *n_inst);
+/* Visibility of the composed scene along K directions dirs[K*3] (device)
+ * from every Gaussian of every instance: T_out[(g_base_j + g)*K + k] for
+ * Gaussian g (original index) of instance j, g_base_j = Gaussians of the
+ * instances before j.  The ray starts at the Gaussian's world mean
+ * m = fl(((R_c0 mu_x + R_c1 mu_y) + R_c2 mu_z) + t_c) (each operation
+ * rounded), at fl(m + fl(origin_eps d)); it meets instance i's Gaussians
+ * in i's frame, o_i = fl(R_i^T fl(o - t_i)) and d_i = fl(R_i^T d) with
+ * component c = ((R_0c v_0 + R_1c v_1) + R_2c v_2), under Eq. 13-15 and the
+ * params of the trees; its own Gaussian is skipped; T is one product over all
+ * instances, snapped to 0 below t_min.  One thread per ray over the 4-wide
+ * trees.  Errors: RT_ERR_INVALID_ARG. */
+rt_status rt_scene_trace_dirs(const rt_scene *scene, const float *dirs, int32_t K, float *T_out,
+                              rt_stream_t stream);
+rt_status rt_scene_destroy(rt_scene *scene, rt_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
 /* Consumers of the visibility: per-Gaussian PBR colour (Eq. 8-10) and        */
 /* ambient occlusion                                                          */
 /* ------------------------------------------------------------------------ */

@@ -1,0 +1,371 @@
+// rt_scene.cu -- composed scenes: a two-level BVH over rigidly placed object
+// instances (Sec. 4.3: objects are composed into a new scene and their
+// visibility is re-traced, so that shadows fall across objects).
+//
+// Each object keeps its own tree (built once, in its local frame); the scene
+// adds a small top-level tree over the instances' world boxes, rebuilt on the
+// host whenever instances move.  A visibility ray starts at a Gaussian of
+// instance j (its world mean fl(R_j mu + t_j)), walks the top level, and at
+// every instance i whose world box it meets continues through i's tree with
+// the ray expressed in i's frame, fl(R_i^T (o - t_i)) and fl(R_i^T d); the
+// transmittance product runs across instances in one register and stops
+// below T_min.  One thread per ray (the 4-wide per-ray traversal): lanes of
+// a warp may be in different instances.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "rt_trace_core.cuh"
+
+namespace {
+
+constexpr int kTopStack = 64;
+
+struct TopNode {   // child boxes (lo xyz, hi xyz) and refs: bit 31 = instance leaf
+    float box[2][6];
+    uint32_t ref[2];
+};
+
+struct InstDev {
+    BvhDev b;
+    float R[9];        // row-major: world = R local + t
+    float t[3];
+    int64_t g_base;    // first output row of this instance's Gaussians
+    int64_t tile_base; // tiles of the instances before this one (items: tile_base * K on)
+    int64_t n_tiles;
+};
+
+// World mean of a local mean: ((R_c0 x + R_c1 y) + R_c2 z) + t_c, each
+// operation rounded (the oracle repeats it).
+__device__ __forceinline__ float3 to_world(const float *R, const float *t, float3 p) {
+    float3 w;
+    w.x = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(R[0], p.x), __fmul_rn(R[1], p.y)), __fmul_rn(R[2], p.z)), t[0]);
+    w.y = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(R[3], p.x), __fmul_rn(R[4], p.y)), __fmul_rn(R[5], p.z)), t[1]);
+    w.z = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(R[6], p.x), __fmul_rn(R[7], p.y)), __fmul_rn(R[8], p.z)), t[2]);
+    return w;
+}
+
+// R^T v: component c = ((R_0c v0 + R_1c v1) + R_2c v2), each operation rounded.
+__device__ __forceinline__ float3 rot_t(const float *R, float3 v) {
+    float3 r;
+    r.x = __fadd_rn(__fadd_rn(__fmul_rn(R[0], v.x), __fmul_rn(R[3], v.y)), __fmul_rn(R[6], v.z));
+    r.y = __fadd_rn(__fadd_rn(__fmul_rn(R[1], v.x), __fmul_rn(R[4], v.y)), __fmul_rn(R[7], v.z));
+    r.z = __fadd_rn(__fadd_rn(__fmul_rn(R[2], v.x), __fmul_rn(R[5], v.y)), __fmul_rn(R[8], v.z));
+    return r;
+}
+
+__device__ __forceinline__ bool top_slab(const float *bx, float3 oi, float3 inv) {
+    return slab(bx[0], bx[3], bx[1], bx[4], bx[2], bx[5], oi, inv);
+}
+
+__global__ void __launch_bounds__(128) k_scene_trace(const InstDev *__restrict__ inst, int n_inst,
+                                                     const TopNode *__restrict__ top, uint32_t root_ref,
+                                                     const float *__restrict__ root_box, const float *__restrict__ dirs,
+                                                     int32_t K, float eps, float t_min, int64_t total_items,
+                                                     float *__restrict__ T_out, int *status,
+                                                     unsigned long long *work) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    WorkCounts wc = {0, 0, 0};
+    LaneLog lg;
+    lg.ids = nullptr;
+    lg.cap = 0;
+    lg.count = 0;
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(work, 1ull);
+        item = __shfl_sync(FULL, item, 0);
+        if ((int64_t)item >= total_items) break;
+        int lo = 0, hi = n_inst - 1;  // last instance whose first item <= item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (inst[mid].tile_base * K <= (int64_t)item) lo = mid;
+            else hi = mid - 1;
+        }
+        const InstDev &J = inst[lo];
+        const int64_t local = (int64_t)item - J.tile_base * K;
+        const int32_t k = (int32_t)(local / J.n_tiles);
+        const int64_t p = (local - (int64_t)k * J.n_tiles) * 32 + lane;
+        if (p >= J.b.n) continue;
+        const float4 mu4 = __ldg(J.b.gauss + 4 * p);
+        const int64_t g = __float_as_int(__ldg(J.b.gauss + 4 * p + 1).w);
+        const float3 d = make_float3(__ldg(dirs + 3 * k), __ldg(dirs + 3 * k + 1), __ldg(dirs + 3 * k + 2));
+        const float3 mw = to_world(J.R, J.t, make_float3(mu4.x, mu4.y, mu4.z));
+        const float3 o = make_float3(__fadd_rn(mw.x, __fmul_rn(eps, d.x)), __fadd_rn(mw.y, __fmul_rn(eps, d.y)),
+                                     __fadd_rn(mw.z, __fmul_rn(eps, d.z)));
+        const float3 inv = safe_inv(d);
+        const float3 oi = make_float3(o.x * inv.x, o.y * inv.y, o.z * inv.z);
+        float T = 1.0f;
+        uint32_t stk[kTopStack];
+        int sp = 0;
+        if (top_slab(root_box, oi, inv)) stk[sp++] = root_ref;
+        while (sp > 0 && !(T < t_min)) {
+            const uint32_t ref = stk[--sp];
+            if (ref & RT_LEAF_BIT) {
+                const int i = (int)(ref & ~RT_LEAF_BIT);
+                const InstDev &I = inst[i];
+                const float3 x = make_float3(__fsub_rn(o.x, I.t[0]), __fsub_rn(o.y, I.t[1]), __fsub_rn(o.z, I.t[2]));
+                const float3 ol = rot_t(I.R, x), dl = rot_t(I.R, d);
+                trace_ray_wide_run<false>(I.b, ol, dl, i == lo ? (int32_t)p : -1, T, lg, wc, status);
+                continue;
+            }
+            const TopNode nd = top[ref];
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                if (!top_slab(nd.box[c], oi, inv)) continue;
+                if (sp < kTopStack) stk[sp++] = nd.ref[c];
+                else rt_set_error(status, RT_ERR_STACK_OVERFLOW);
+            }
+        }
+        T_out[(J.g_base + g) * K + k] = T < t_min ? 0.0f : T;
+    }
+}
+
+}  // namespace
+
+struct rt_scene {
+    int n_inst;
+    int64_t n_total;
+    rt_params params;
+    std::vector<const rt_bvh *> bvh;
+    std::vector<double> local_box;  // [n_inst][6] root box of each object (local frame)
+    void *dev;                      // InstDev[n_inst] | TopNode[n_inst - 1] | root box
+    uint32_t root_ref;
+    int64_t n_tiles;                // all instances
+};
+
+namespace {
+
+size_t align256s(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Root box of an object's tree (host, synchronous): the union of node 0's
+// child boxes; a one-Gaussian tree gets an unbounded box (always visited).
+rt_status root_box(const rt_bvh *b, cudaStream_t st, double out[6]) {
+    if (b->n < 2) {
+        for (int c = 0; c < 3; ++c) {
+            out[c] = -INFINITY;
+            out[3 + c] = INFINITY;
+        }
+        return RT_OK;
+    }
+    float nd[12];
+    if (cudaMemcpyAsync(nd, b->nodes, sizeof(nd), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return RT_ERR_CUDA;
+    // node layout: (L.lo.x, L.hi.x, L.lo.y, L.hi.y, L.lo.z, L.hi.z, R.lo.x, ...)
+    for (int c = 0; c < 3; ++c) {
+        out[c] = fmin((double)nd[2 * c], (double)nd[6 + 2 * c]);
+        out[3 + c] = fmax((double)nd[2 * c + 1], (double)nd[6 + 2 * c + 1]);
+    }
+    return RT_OK;
+}
+
+// World box of a rigidly placed local box, widened for the float32 rounding
+// of the rays' frame changes (a relative 1e-5 of the box's size and position).
+void world_box(const double lb[6], const float *xf, float out[6]) {
+    if (!std::isfinite(lb[0])) {
+        for (int c = 0; c < 3; ++c) {
+            out[c] = -INFINITY;
+            out[3 + c] = INFINITY;
+        }
+        return;
+    }
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int m = 0; m < 8; ++m) {
+        const double p[3] = {m & 1 ? lb[3] : lb[0], m & 2 ? lb[4] : lb[1], m & 4 ? lb[5] : lb[2]};
+        for (int r = 0; r < 3; ++r) {
+            const double v = xf[4 * r] * p[0] + xf[4 * r + 1] * p[1] + xf[4 * r + 2] * p[2] + xf[4 * r + 3];
+            lo[r] = fmin(lo[r], v);
+            hi[r] = fmax(hi[r], v);
+        }
+    }
+    double mag = 0.0;
+    for (int r = 0; r < 3; ++r) mag = fmax(mag, fmax(fabs(lo[r]), fabs(hi[r])));
+    for (int r = 0; r < 3; ++r) {
+        const double w = 1e-5 * (hi[r] - lo[r]) + 1e-5 * mag + 1e-30;
+        out[r] = nextafterf((float)(lo[r] - w), -INFINITY);
+        out[3 + r] = nextafterf((float)(hi[r] + w), INFINITY);
+    }
+}
+
+// Top-level tree by recursive median splits along the longest axis of the
+// box centres.  Returns the ref of the subtree's root and its box.
+uint32_t build_top(std::vector<int> &idx, int a, int b, const std::vector<float> &wb, std::vector<TopNode> &nodes,
+                   float box[6]) {
+    if (b - a == 1) {
+        for (int c = 0; c < 6; ++c) box[c] = wb[6 * idx[a] + c];
+        return RT_LEAF_BIT | (uint32_t)idx[a];
+    }
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    auto centre = [&](int i, int c) {
+        const double l = wb[6 * i + c], h = wb[6 * i + 3 + c];
+        return std::isfinite(l) && std::isfinite(h) ? 0.5 * (l + h) : 0.0;
+    };
+    for (int q = a; q < b; ++q)
+        for (int c = 0; c < 3; ++c) {
+            lo[c] = fmin(lo[c], centre(idx[q], c));
+            hi[c] = fmax(hi[c], centre(idx[q], c));
+        }
+    int ax = 0;
+    for (int c = 1; c < 3; ++c)
+        if (hi[c] - lo[c] > hi[ax] - lo[ax]) ax = c;
+    const int mid = (a + b) / 2;
+    std::nth_element(idx.begin() + a, idx.begin() + mid, idx.begin() + b,
+                     [&](int x, int y) { return centre(x, ax) < centre(y, ax) || (centre(x, ax) == centre(y, ax) && x < y); });
+    const uint32_t me = (uint32_t)nodes.size();
+    nodes.push_back(TopNode());
+    float bl[6], br[6];
+    const uint32_t l = build_top(idx, a, mid, wb, nodes, bl);
+    const uint32_t r = build_top(idx, mid, b, wb, nodes, br);
+    TopNode &nd = nodes[me];
+    for (int c = 0; c < 6; ++c) {
+        nd.box[0][c] = bl[c];
+        nd.box[1][c] = br[c];
+    }
+    nd.ref[0] = l;
+    nd.ref[1] = r;
+    for (int c = 0; c < 3; ++c) {
+        box[c] = fminf(bl[c], br[c]);
+        box[3 + c] = fmaxf(bl[3 + c], br[3 + c]);
+    }
+    return me;
+}
+
+rt_status upload(rt_scene *sc, const rt_instance *inst, rt_stream_t stream) {
+    const int n = sc->n_inst;
+    std::vector<InstDev> h(n);
+    std::vector<float> wb(6 * (size_t)n);
+    int64_t g_base = 0, tiles = 0;
+    for (int i = 0; i < n; ++i) {
+        memset(&h[i], 0, sizeof(InstDev));
+        const float *xf = inst[i].xform;
+        for (int r = 0; r < 3; ++r) {
+            for (int c = 0; c < 3; ++c) h[i].R[3 * r + c] = xf[4 * r + c];
+            h[i].t[r] = xf[4 * r + 3];
+        }
+        for (int q = 0; q < 12; ++q)
+            if (!std::isfinite(xf[q])) return RT_ERR_INVALID_ARG;
+        h[i].b = bvh_dev(sc->bvh[i]);
+        h[i].g_base = g_base;
+        h[i].n_tiles = (sc->bvh[i]->n + 31) / 32;
+        h[i].tile_base = tiles;
+        tiles += h[i].n_tiles;
+        g_base += sc->bvh[i]->n;
+        world_box(&sc->local_box[6 * (size_t)i], xf, &wb[6 * (size_t)i]);
+    }
+    std::vector<int> idx(n);
+    for (int i = 0; i < n; ++i) idx[i] = i;
+    std::vector<TopNode> nodes;
+    float rb[6];
+    sc->root_ref = build_top(idx, 0, n, wb, nodes, rb);
+    sc->n_tiles = tiles;
+    const size_t o_top = align256s(sizeof(InstDev) * n), o_rb = o_top + align256s(sizeof(TopNode) * (n > 1 ? n - 1 : 1));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(sc->dev, h.data(), sizeof(InstDev) * n, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        (!nodes.empty() && cudaMemcpyAsync((char *)sc->dev + o_top, nodes.data(), sizeof(TopNode) * nodes.size(),
+                                           cudaMemcpyHostToDevice, st) != cudaSuccess) ||
+        cudaMemcpyAsync((char *)sc->dev + o_rb, rb, sizeof(rb), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return RT_ERR_CUDA;
+    return RT_OK;
+}
+
+size_t scene_bytes(int n) {
+    return align256s(sizeof(InstDev) * n) + align256s(sizeof(TopNode) * (n > 1 ? n - 1 : 1)) + 256;
+}
+
+}  // namespace
+
+extern "C" rt_status rt_scene_create(const rt_instance *inst, int32_t n_inst, rt_stream_t stream, rt_scene **out) {
+    if (!out || !inst || n_inst <= 0 || n_inst > 65536) return RT_ERR_INVALID_ARG;
+    *out = nullptr;
+    for (int i = 0; i < n_inst; ++i) {
+        const rt_bvh *b = inst[i].bvh;
+        if (!b) return RT_ERR_INVALID_ARG;
+        const rt_params &p0 = inst[0].bvh->params, &p = b->params;
+        if (p.k_sigma != p0.k_sigma || p.alpha_min != p0.alpha_min || p.t_min != p0.t_min ||
+            p.origin_eps != p0.origin_eps)
+            return RT_ERR_INVALID_ARG;
+        if (b->n >= 2 && b->n_wide == 0) return RT_ERR_UNSUPPORTED;
+    }
+    rt_scene *sc = new rt_scene();
+    sc->n_inst = n_inst;
+    sc->params = inst[0].bvh->params;
+    sc->bvh.resize(n_inst);
+    sc->local_box.resize(6 * (size_t)n_inst);
+    sc->n_total = 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    rt_status r = RT_OK;
+    for (int i = 0; i < n_inst && r == RT_OK; ++i) {
+        sc->bvh[i] = inst[i].bvh;
+        sc->n_total += inst[i].bvh->n;
+        r = root_box(inst[i].bvh, st, &sc->local_box[6 * (size_t)i]);
+    }
+    sc->dev = nullptr;
+    if (r == RT_OK) r = rt_alloc(&sc->dev, scene_bytes(n_inst), stream);
+    if (r == RT_OK) r = upload(sc, inst, stream);
+    if (r != RT_OK) {
+        if (sc->dev) rt_free(sc->dev, stream);
+        delete sc;
+        return r;
+    }
+    *out = sc;
+    return RT_OK;
+}
+
+extern "C" rt_status rt_scene_update(rt_scene *sc, const rt_instance *inst, int32_t n_inst, rt_stream_t stream) {
+    if (!sc || !inst || n_inst != sc->n_inst) return RT_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int i = 0; i < n_inst; ++i) {
+        if (inst[i].bvh != sc->bvh[i]) return RT_ERR_INVALID_ARG;
+        RT_TRY(root_box(sc->bvh[i], st, &sc->local_box[6 * (size_t)i]));  // objects may have been refitted
+    }
+    return upload(sc, inst, stream);
+}
+
+extern "C" rt_status rt_scene_info(const rt_scene *sc, int64_t *n_total, int32_t *n_inst) {
+    if (!sc) return RT_ERR_INVALID_ARG;
+    if (n_total) *n_total = sc->n_total;
+    if (n_inst) *n_inst = sc->n_inst;
+    return RT_OK;
+}
+
+extern "C" rt_status rt_scene_trace_dirs(const rt_scene *sc, const float *dirs, int32_t K, float *T_out,
+                                         rt_stream_t stream) {
+    if (!sc || K <= 0 || !dirs) return RT_ERR_INVALID_ARG;
+    if (sc->n_total == 0) return RT_OK;
+    if (!T_out) return RT_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    // work items: instance by instance, all tiles of direction 0, then 1, ...
+    const int64_t items = sc->n_tiles * K;
+    const size_t o_top = align256s(sizeof(InstDev) * sc->n_inst);
+    const size_t o_rb = o_top + align256s(sizeof(TopNode) * (sc->n_inst > 1 ? sc->n_inst - 1 : 1));
+    unsigned long long *work = nullptr;
+    RT_TRY(rt_alloc((void **)&work, sizeof(unsigned long long), stream));
+    rt_status res = RT_OK;
+    if (cudaMemsetAsync(work, 0, sizeof(unsigned long long), st) != cudaSuccess) res = RT_ERR_CUDA;
+    if (res == RT_OK) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scene_trace, 128, 0) != cudaSuccess ||
+            per_sm < 1) {
+            cudaGetLastError();
+            per_sm = 1;
+        }
+        k_scene_trace<<<per_sm * rt_num_sms(), 128, 0, st>>>(
+            (const InstDev *)sc->dev, sc->n_inst, (const TopNode *)((char *)sc->dev + o_top), sc->root_ref,
+            (const float *)((char *)sc->dev + o_rb), dirs, K, sc->params.origin_eps, sc->params.t_min, items,
+            T_out, rt_status_ptr(), work);
+        res = rt_check_launch();
+    }
+    rt_free(work, stream);
+    return res;
+}
+
+extern "C" rt_status rt_scene_destroy(rt_scene *sc, rt_stream_t stream) {
+    if (!sc) return RT_ERR_INVALID_ARG;
+    if (sc->dev) rt_free(sc->dev, stream);
+    delete sc;
+    return RT_OK;
+}

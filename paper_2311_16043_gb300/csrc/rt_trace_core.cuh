@@ -422,18 +422,19 @@ __device__ __forceinline__ float trace_wide(const BvhDev &b, float3 o, float3 d,
 
 // Strategy 4: one thread per ray over the 4-wide tree with a private stack,
 // for rays without a shared direction (env-map samples, explicit rays).
+// Multiplies the running transmittance T by this tree's accepted factors and
+// stops once T < t_min (no snap: a ray may go on through other trees).
 template <bool COUNT>
-__device__ __forceinline__ float trace_ray_wide(const BvhDev &b, float3 o, float3 d, int32_t src, LaneLog &lg,
-                                                WorkCounts &wc, int *status) {
-    float T = 1.0f;
-    if (b.n <= 0) return T;
+__device__ __forceinline__ void trace_ray_wide_run(const BvhDev &b, float3 o, float3 d, int32_t src, float &T,
+                                                   LaneLog &lg, WorkCounts &wc, int *status) {
+    if (b.n <= 0) return;
     if (b.n == 1) {
         if (COUNT) wc.gauss++;
         if (src != 0 && gauss_hit(b, 0, o, d, T)) {
             if (COUNT) wc.hits++;
             log_hit(lg, b, 0);
         }
-        return T < b.t_min ? 0.0f : T;
+        return;
     }
     const float3 inv = safe_inv(d);
     const float3 oi = make_float3(o.x * inv.x, o.y * inv.y, o.z * inv.z);
@@ -485,6 +486,13 @@ __device__ __forceinline__ float trace_ray_wide(const BvhDev &b, float3 o, float
             node = stack[--sp];
         }
     }
+}
+
+template <bool COUNT>
+__device__ __forceinline__ float trace_ray_wide(const BvhDev &b, float3 o, float3 d, int32_t src, LaneLog &lg,
+                                                WorkCounts &wc, int *status) {
+    float T = 1.0f;
+    trace_ray_wide_run<COUNT>(b, o, d, src, T, lg, wc, status);
     return T < b.t_min ? 0.0f : T;
 }
 

@@ -55,6 +55,10 @@ class rt_pbr_inputs(C.Structure):
                 ("env_h", C.c_int32), ("env_w", C.c_int32), ("cam", C.c_float * 3), ("kernel", C.c_int32)]
 
 
+class rt_instance(C.Structure):
+    _fields_ = [("bvh", C.c_void_p), ("xform", C.c_float * 12)]
+
+
 class rt_batch_job(C.Structure):
     _fields_ = [("bvh", C.c_void_p), ("rays", rt_rayspec), ("T_out", C.c_void_p)]
 
@@ -104,6 +108,11 @@ _SIGS = {
     "rt_surrogate_infer_noalloc": (_I32, [_P, _P, _P, _F32, _P, _P, _P]),
     "rt_trace_autotune": (_I32, [_P, _P, _P, _P, _P]),
     "rt_pbr_shade": (_I32, [_P, _P, _P, _P, _P, _P]),
+    "rt_scene_create": (_I32, [_P, _I32, _P, _P]),
+    "rt_scene_update": (_I32, [_P, _P, _I32, _P]),
+    "rt_scene_info": (_I32, [_P, _P, _P]),
+    "rt_scene_trace_dirs": (_I32, [_P, _P, _I32, _P, _P]),
+    "rt_scene_destroy": (_I32, [_P, _P]),
     "rt_trace_ao": (_I32, [_P, _P, _P, _P, _P]),
     "rt_batch_create": (_I32, [_P, _I32, _I32, _P, _P]),
     "rt_batch_run": (_I32, [_P, _P]),
@@ -369,6 +378,67 @@ def rt_trace_ao(bvh: Bvh, rs: rt_rayspec, ao=None, opts: rt_trace_opts | None = 
     _check(lib().rt_trace_ao(bvh.handle, C.byref(rs), C.byref(opts) if opts is not None else None,
                              _ptr(ao, torch.float32, "ao"), _stream(stream)), "rt_trace_ao")
     return ao
+
+
+class Scene:
+    """A composed scene: object trees placed by rigid maps (two-level BVH)."""
+
+    def __init__(self, handle, bvhs):
+        self.handle = handle
+        self.bvhs = list(bvhs)  # the trees must outlive the scene
+        n_total = C.c_int64()
+        _check(lib().rt_scene_info(handle, C.byref(n_total), None), "rt_scene_info")
+        self.n_total = int(n_total.value)
+
+    def destroy(self):
+        if self.handle:
+            lib().rt_scene_destroy(self.handle, None)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def _instances(bvhs, xforms):
+    import numpy as np
+    arr = (rt_instance * len(bvhs))()
+    for i, (b, x) in enumerate(zip(bvhs, xforms)):
+        x = np.asarray(x, dtype=np.float32).reshape(3, 4)
+        arr[i].bvh = b.handle
+        for q in range(12):
+            arr[i].xform[q] = float(x.flat[q])
+    return arr
+
+
+def rt_scene_create(bvhs, xforms, stream=None) -> Scene:
+    """bvhs: list of Bvh (may repeat); xforms: list of 3x4 [R | t] (world =
+    R local + t)."""
+    if len(bvhs) != len(xforms) or not bvhs:
+        raise ValueError("one transform per instance")
+    h = C.c_void_p()
+    _check(lib().rt_scene_create(_instances(bvhs, xforms), len(bvhs), _stream(stream), C.byref(h)),
+           "rt_scene_create")
+    return Scene(h, bvhs)
+
+
+def rt_scene_update(scene: Scene, xforms, stream=None) -> Scene:
+    _check(lib().rt_scene_update(scene.handle, _instances(scene.bvhs, xforms), len(scene.bvhs), _stream(stream)),
+           "rt_scene_update")
+    return scene
+
+
+def rt_scene_trace_dirs(scene: Scene, dirs, T_out=None, stream=None):
+    """Visibility of every Gaussian of every instance along dirs[K]:
+    T[n_total, K], instances in order."""
+    K = dirs.shape[0]
+    if T_out is None:
+        T_out = torch.empty((scene.n_total, K), dtype=torch.float32, device="cuda")
+    _check(lib().rt_scene_trace_dirs(scene.handle, _ptr(dirs, torch.float32, "dirs"), K,
+                                     _ptr(T_out, torch.float32, "T_out"), _stream(stream)), "rt_scene_trace_dirs")
+    return T_out
 
 
 def rt_materialize_rays(bvh: Bvh, rs: rt_rayspec, ray_ids, stream=None):
