@@ -203,7 +203,10 @@ typedef enum {
                              one direction, shared stack, binary tree          */
     RT_KERNEL_WIDE = 3,   /* as PACKET over the 4-wide tree (the binary tree
                              collapsed by greedy largest-area expansion)       */
-    RT_KERNEL_RAY_WIDE = 4 /* one thread per ray over the 4-wide tree         */
+    RT_KERNEL_RAY_WIDE = 4, /* one thread per ray over the 4-wide tree        */
+    RT_KERNEL_RAY_REFILL = 5 /* as RAY_WIDE, idle lanes refilled with new rays
+                              as theirs finish (full implicit sets; otherwise
+                              RAY_WIDE)                                       */
 } rt_kernel;
 
 typedef struct {
@@ -449,13 +452,15 @@ rt_status rt_surrogate_infer_noalloc(const rt_surrogate *s, const rt_bvh *bvh, c
 /* ------------------------------------------------------------------------ */
 
 /* Picks the traversal strategy (rt_kernel) and the work order (order_block)
- * for a full implicit ray set (DIRS or ENV, no ray_ids) over `bvh`: each
+ * for a full implicit ray set (DIRS, ENV or HEMI, no ray_ids) over `bvh`: each
  * candidate traces the same four contiguous blocks of tiles of 32 Gaussians
  * spread over the Morton range (all directions; about 4M rays), timed with
- * CUDA events, best of two runs after a warm-up; the fastest is written into
- * opts->kernel and opts->order_block (other fields untouched) when it beats
- * the default strategy (RT_KERNEL_WIDE for DIRS, RT_KERNEL_RAY_WIDE for ENV)
- * by more than 3 %, else the default with its best order_block.  Results
+ * CUDA events after a warm-up run; candidates are the 4-wide strategies
+ * (the binary ones when the tree has no 4-wide form); the fastest is written
+ * into opts->kernel and opts->order_block (other fields untouched) when it
+ * beats the default strategy (RT_KERNEL_WIDE for DIRS, RT_KERNEL_RAY_REFILL
+ * for ENV and HEMI) by more than 3 %, else the default with its best
+ * order_block.  Results
  * are cached in-process per (device, log2 n, ray kind, K).  T_scratch must
  * hold rt_rayspec_count(bvh, rays) floats.  Synchronises `stream`. */
 rt_status rt_trace_autotune(const rt_bvh *bvh, const rt_rayspec *rays, float *T_scratch,

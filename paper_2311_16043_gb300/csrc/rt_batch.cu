@@ -43,11 +43,12 @@ constexpr int kTuneBlocks = 4;
 constexpr float kTuneMargin = 0.97f;
 
 // The strategy used without tuning: 4-wide packets sharing a direction for a
-// direction set, one thread per ray on the 4-wide tree for env-map rays (their
-// directions differ within a tile), binary variants when there is no 4-wide tree.
+// direction set, one thread per ray on the 4-wide tree with lane refill for
+// env-map and hemisphere rays (their directions differ within a tile), binary
+// variants when there is no 4-wide tree.
 int default_kernel(const rt_bvh *bvh, int32_t kind) {
     if (kind == RT_RAYS_DIRS) return bvh->n_wide > 0 ? RT_KERNEL_WIDE : RT_KERNEL_PACKET;
-    return bvh->n_wide > 0 ? RT_KERNEL_RAY_WIDE : RT_KERNEL_RAY;
+    return bvh->n_wide > 0 ? RT_KERNEL_RAY_REFILL : RT_KERNEL_RAY;
 }
 
 TraceJob full_job(const rt_bvh *bvh, int32_t K, int32_t order_block) {
@@ -70,12 +71,119 @@ struct BatchJobDev {
     RaySetDev rs;
     TraceJob job;
     float *T_out;
-    int32_t strat;  // 0 per-ray, 1 packet, 2 4-wide packet, 3 4-wide packet with a shared direction, 4 per-ray 4-wide
-    int64_t item_begin;
+    int32_t strat;  // 0 per-ray, 1 packet, 2 4-wide packet, 3 4-wide packet with a shared direction,
+                    // 4 per-ray 4-wide, 5 per-ray 4-wide with lane refill
+    int64_t item_begin;  // item jobs: first item of the item queue
+    int64_t slot_begin;  // refill jobs: first ray slot of the slot queue
 };
 
-__global__ void __launch_bounds__(128) k_trace_batch(const BatchJobDev *__restrict__ jobs, int n_jobs,
-                                                     int64_t total_items, int *status,
+// The lane-refill phase of the batch: the refill jobs' rays are the slots of
+// one queue (job after job, item*32 + l within a job); idle lanes take slots
+// as in trace_refill, each lane carrying its own job.
+__device__ __forceinline__ void batch_refill(const BatchJobDev *__restrict__ jobs, int first, int n_jobs,
+                                             int64_t total_slots, int *status, unsigned long long *work) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    bool has = false, exhausted = false;
+    int jl = first;
+    float3 o = make_float3(0.f, 0.f, 0.f), d = make_float3(0.f, 0.f, 1.f), inv = d, oi = o;
+    int32_t src = -1;
+    int64_t out_idx = 0;
+    float T = 1.0f;
+    uint32_t node = 0;
+    int sp = 0;
+    uint32_t stack[RT_WIDE_STACK];
+    for (;;) {
+        const unsigned idle = __ballot_sync(FULL, !has);
+        const int n_idle = __popc(idle);
+        if (!exhausted && (n_idle >= kRefillMin || n_idle == 32)) {
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(work, (unsigned long long)n_idle);
+            base = __shfl_sync(FULL, base, 0);
+            if (base + (unsigned long long)n_idle >= (unsigned long long)total_slots) exhausted = true;
+            if (!has) {
+                const int64_t slot = (int64_t)(base + (unsigned long long)__popc(idle & lt_mask));
+                if (slot < total_slots) {
+                    int lo = first, hi = n_jobs - 1;  // last refill job with slot_begin <= slot
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (jobs[mid].slot_begin <= slot) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    jl = lo;
+                    const BatchJobDev &J = jobs[jl];
+                    const int64_t local = slot - J.slot_begin;
+                    int64_t tile;
+                    int32_t k;
+                    full_item(J.job, J.rs.K, local >> 5, tile, k);
+                    const int64_t p = tile * 32 + (local & 31);
+                    if (p < J.b.n) {
+                        const float4 mu = __ldg(J.b.gauss + 4 * p);
+                        const int64_t g = __float_as_int(__ldg(J.b.gauss + 4 * p + 1).w);
+                        out_idx = g * J.rs.K + k;
+                        implicit_ray(J.rs, out_idx, k, g, mu, o, d);
+                        inv = safe_inv(d);
+                        oi = make_float3(o.x * inv.x, o.y * inv.y, o.z * inv.z);
+                        src = (int32_t)p;
+                        T = 1.0f;
+                        node = 0;
+                        sp = 0;
+                        has = true;
+                    }
+                }
+            }
+        }
+        if (__ballot_sync(FULL, has) == 0) {
+            if (exhausted) break;
+            continue;
+        }
+        if (!has) continue;
+        const BvhDev &b = jobs[jl].b;
+        const float4 *w = b.wide + 8 * (int64_t)node;
+        const float4 lx = __ldg(w), hx = __ldg(w + 1), ly = __ldg(w + 2), hy = __ldg(w + 3), lz = __ldg(w + 4),
+                     hz = __ldg(w + 5), rf = __ldg(w + 6);
+        const uint32_t r[4] = {__float_as_uint(rf.x), __float_as_uint(rf.y), __float_as_uint(rf.z),
+                               __float_as_uint(rf.w)};
+        const bool h[4] = {slab(lx.x, hx.x, ly.x, hy.x, lz.x, hz.x, oi, inv),
+                           slab(lx.y, hx.y, ly.y, hy.y, lz.y, hz.y, oi, inv),
+                           slab(lx.z, hx.z, ly.z, hy.z, lz.z, hz.z, oi, inv),
+                           slab(lx.w, hx.w, ly.w, hy.w, lz.w, hz.w, oi, inv)};
+        int next = -1;
+        bool overflow = false;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            if (!h[c]) continue;
+            if (r[c] & RT_LEAF_BIT) {
+                const int32_t p = (int32_t)(r[c] & ~RT_LEAF_BIT);
+                if (p != src) gauss_hit(b, p, o, d, T);
+            } else if (next < 0) {
+                next = (int)r[c];
+            } else if (sp < RT_WIDE_STACK) {
+                stack[sp++] = r[c];
+            } else {
+                overflow = true;
+            }
+        }
+        if (overflow) rt_set_error(status, RT_ERR_STACK_OVERFLOW);
+        bool done = overflow || T < b.t_min;
+        if (!done) {
+            if (next >= 0) node = (uint32_t)next;
+            else if (sp > 0) node = stack[--sp];
+            else done = true;
+        }
+        if (done) {
+            jobs[jl].T_out[out_idx] = T < b.t_min ? 0.0f : T;
+            has = false;
+        }
+    }
+}
+
+// Jobs [0, n_item_jobs) are consumed as 32-ray items (work[0]); jobs
+// [n_item_jobs, n_jobs) as per-ray slots with lane refill (work[1]), after a
+// warp finds the item queue empty.
+__global__ void __launch_bounds__(128) k_trace_batch(const BatchJobDev *__restrict__ jobs, int n_item_jobs, int n_jobs,
+                                                     int64_t total_items, int64_t total_slots, int *status,
                                                      unsigned long long *work) {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -94,7 +202,7 @@ __global__ void __launch_bounds__(128) k_trace_batch(const BatchJobDev *__restri
         if (lane == 0) item = atomicAdd(work, 1ull);
         item = __shfl_sync(FULL, item, 0);
         if ((int64_t)item >= total_items) break;
-        int lo = 0, hi = n_jobs - 1;  // last job with item_begin <= item
+        int lo = 0, hi = n_item_jobs - 1;  // last job with item_begin <= item
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
             if (jobs[mid].item_begin <= (int64_t)item) lo = mid;
@@ -108,6 +216,7 @@ __global__ void __launch_bounds__(128) k_trace_batch(const BatchJobDev *__restri
         else if (J.strat == 1) trace_item<1, false>(J.b, J.rs, J.job, J.T_out, aux, local, J.job.n_out, wc, rays_done, stk);
         else trace_item<0, false>(J.b, J.rs, J.job, J.T_out, aux, local, J.job.n_out, wc, rays_done, stk);
     }
+    if (total_slots > 0) batch_refill(jobs, n_item_jobs, n_jobs, total_slots, status, work + 1);
 }
 
 int persistent_grid() {
@@ -167,14 +276,17 @@ extern "C" rt_status rt_trace_autotune(const rt_bvh *bvh, const rt_rayspec *rays
     float best = 1e30f, def_ms = 1e30f;
     int best_k = def_k, best_b = 64, def_b = 64;
     rt_status res = RT_OK;
-    for (int kernel = RT_KERNEL_RAY; kernel <= RT_KERNEL_RAY_WIDE && res == RT_OK; ++kernel) {
-        if ((kernel == RT_KERNEL_WIDE || kernel == RT_KERNEL_RAY_WIDE) && bvh->n_wide == 0) continue;
+    for (int kernel = RT_KERNEL_RAY; kernel <= RT_KERNEL_RAY_REFILL && res == RT_OK; ++kernel) {
+        const bool wide = kernel == RT_KERNEL_WIDE || kernel == RT_KERNEL_RAY_WIDE || kernel == RT_KERNEL_RAY_REFILL;
+        // with a 4-wide tree the binary-tree strategies are not candidates (they
+        // trail their 4-wide forms on every measured workload)
+        if (wide != (bvh->n_wide > 0)) continue;
         // order_block only changes which rays share a warp for the packet strategies
         const int n_blocks = (kernel == RT_KERNEL_PACKET || kernel == RT_KERNEL_WIDE) ? 4 : 1;
-        const int strat = kernel == RT_KERNEL_RAY_WIDE ? 4 : kernel - 1;
+        const int strat = kernel == RT_KERNEL_RAY_REFILL ? 5 : kernel == RT_KERNEL_RAY_WIDE ? 4 : kernel - 1;
         for (int bi = 0; bi < n_blocks && res == RT_OK; ++bi) {
             float ms = 1e30f;
-            for (int rep = 0; rep < 3 && res == RT_OK; ++rep) {  // the first run warms caches
+            for (int rep = 0; rep < 2 && res == RT_OK; ++rep) {  // the first run warms caches
                 cudaEventRecord(e0, st);
                 for (int q = 0; q < nb && res == RT_OK; ++q) {
                     TraceJob job = full_job(bvh, rs.K, blocks[bi]);
@@ -273,24 +385,35 @@ extern "C" rt_status rt_batch_create(const rt_batch_job *jobs, int32_t n_jobs, i
         H.rs = rs;
         H.job = full_job(J.bvh, rs.K, o.order_block);
         H.T_out = J.T_out;
-        H.strat = o.kernel == RT_KERNEL_RAY_WIDE ? (J.bvh->n_wide > 0 ? 4 : 0)
+        H.strat = o.kernel == RT_KERNEL_RAY_REFILL ? (J.bvh->n_wide > 0 ? 5 : 0)
+                  : o.kernel == RT_KERNEL_RAY_WIDE ? (J.bvh->n_wide > 0 ? 4 : 0)
                   : o.kernel == RT_KERNEL_WIDE ? (J.bvh->n_wide > 0 ? (J.rays.kind == RT_RAYS_DIRS ? 3 : 2) : 1)
                   : o.kernel == RT_KERNEL_PACKET ? 1 : 0;
         cost[j] = (double)count * log2((double)(J.bvh->n > 1 ? J.bvh->n : 2));
     }
-    // largest estimated cost first
+    // item jobs first, then lane-refill jobs; largest estimated cost first in each
     std::vector<int> order(n_jobs);
     for (int j = 0; j < n_jobs; ++j) order[j] = j;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        const bool ra = host[a].strat == 5, rb = host[b].strat == 5;
+        return ra != rb ? rb : cost[a] > cost[b];
+    });
     std::vector<BatchJobDev> queue(n_jobs);
-    int64_t items = 0, rays = 0;
+    int64_t items = 0, slots = 0, rays = 0;
+    int n_item_jobs = 0;
     for (int q = 0; q < n_jobs; ++q) {
         queue[q] = host[order[q]];
-        queue[q].item_begin = items;
-        items += queue[q].job.n_items;
+        if (queue[q].strat == 5) {
+            queue[q].slot_begin = slots;
+            slots += queue[q].job.n_items * 32;
+        } else {
+            queue[q].item_begin = items;
+            items += queue[q].job.n_items;
+            ++n_item_jobs;
+        }
         rays += queue[q].job.n_out;
     }
-    bt->n_items = items;
+    bt->n_items = items + slots / 32;
     bt->n_rays = rays;
     const size_t tbytes = ((sizeof(BatchJobDev) * n_jobs + 255) & ~(size_t)255);
     rt_status r = rt_alloc(&bt->table, tbytes + 256, stream);
@@ -318,8 +441,8 @@ extern "C" rt_status rt_batch_create(const rt_batch_job *jobs, int32_t n_jobs, i
     int *status = rt_status_ptr();
     bool ok = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     if (ok) {
-        cudaMemsetAsync(work, 0, 8, cap);
-        k_trace_batch<<<grid, 128, 0, cap>>>(dtab, n_jobs, items, status, work);
+        cudaMemsetAsync(work, 0, 16, cap);
+        k_trace_batch<<<grid, 128, 0, cap>>>(dtab, n_item_jobs, n_jobs, items, slots, status, work);
         ok = cudaStreamEndCapture(cap, &bt->graph) == cudaSuccess;
     }
     if (ok) ok = cudaGraphInstantiate(&bt->exec, bt->graph, 0) == cudaSuccess;

@@ -29,6 +29,11 @@ __global__ void __launch_bounds__(128, RT_TRACE_MIN_BLOCKS) k_trace(BvhDev b, Ra
     int2 *stk = stk_all + ((STRAT == 2 || STRAT == 3) ? (threadIdx.x >> 5) * RT_WIDE_STACK : 0);
     WorkCounts wc = {0, 0, 0};
     unsigned long long rays_done = 0;
+    if (STRAT == 5) {  // per-ray slots with lane refill (full implicit sets)
+        trace_refill<COUNT>(b, rs, job, T_out, aux, work, wc, rays_done);
+        flush_counts<COUNT>(aux, wc, rays_done);
+        return;
+    }
     for (;;) {
         unsigned long long item = 0;
         if (lane == 0) item = atomicAdd(work, 1ull);
@@ -66,10 +71,13 @@ rt_status rt_trace_launch_job(const BvhDev &b, const RaySetDev &rs, const TraceJ
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemsetAsync(work, 0, sizeof(unsigned long long), st) != cudaSuccess) return RT_ERR_CUDA;
     const int threads = 128;
-    if (strat == 4 && b.wide) {
+    if (strat == 5 && b.wide && job.mode == MODE_FULL) {
+        int grid = persistent_blocks((const void *)k_trace<5, false>, threads);
+        k_trace<5, false><<<grid, threads, 0, st>>>(b, rs, job, T_out, aux, work);
+    } else if (strat >= 4 && b.wide) {
         int grid = persistent_blocks((const void *)k_trace<4, false>, threads);
         k_trace<4, false><<<grid, threads, 0, st>>>(b, rs, job, T_out, aux, work);
-    } else if (strat == 4) {
+    } else if (strat >= 4) {
         int grid = persistent_blocks((const void *)k_trace<0, false>, threads);
         k_trace<0, false><<<grid, threads, 0, st>>>(b, rs, job, T_out, aux, work);
     } else if (strat >= 2 && b.wide) {
@@ -100,7 +108,7 @@ rt_status rt_trace_launch(const rt_bvh *bvh, const rt_rayspec *rays, float *T_ou
     rt_trace_opts o;
     memset(&o, 0, sizeof(o));
     if (opts) o = *opts;
-    if (o.kernel < 0 || o.kernel > 4 || o.order_block < 0 || o.block_threads < 0) return RT_ERR_INVALID_ARG;
+    if (o.kernel < 0 || o.kernel > 5 || o.order_block < 0 || o.block_threads < 0) return RT_ERR_INVALID_ARG;
     if ((o.hit_ids && (o.hit_cap <= 0 || !o.hit_count)) ) return RT_ERR_INVALID_ARG;
     if (count == 0) return RT_OK;
 
@@ -123,8 +131,14 @@ rt_status rt_trace_launch(const rt_bvh *bvh, const rt_rayspec *rays, float *T_ou
     } else {
         job.n_items = (count + 31) / 32;
     }
-    int strat = o.kernel == RT_KERNEL_RAY_WIDE ? 4 : o.kernel == RT_KERNEL_WIDE ? 2 : o.kernel == RT_KERNEL_PACKET ? 1 : 0;
-    if (o.kernel == RT_KERNEL_AUTO && job.mode == MODE_FULL) strat = rays->kind == RT_RAYS_DIRS ? 2 : 4;
+    int strat = o.kernel == RT_KERNEL_RAY_REFILL ? 5 : o.kernel == RT_KERNEL_RAY_WIDE ? 4
+              : o.kernel == RT_KERNEL_WIDE ? 2 : o.kernel == RT_KERNEL_PACKET ? 1 : 0;
+    // AUTO: warp packets sharing the direction for a direction set; per-ray
+    // traversal with lane refill for env-map and hemisphere sets (directions
+    // differ across a tile)
+    if (o.kernel == RT_KERNEL_AUTO && job.mode == MODE_FULL) strat = rays->kind == RT_RAYS_DIRS ? 2 : 5;
+    // lane refill needs the 4-wide tree and a full implicit set, and keeps no hit log
+    if (strat == 5 && (bvh->n_wide == 0 || job.mode != MODE_FULL || o.hit_ids)) strat = 4;
     if (strat == 2 && bvh->n_wide == 0) strat = 1;
     if (strat == 4 && bvh->n_wide == 0) strat = 0;
     if (strat == 2 && job.mode == MODE_FULL && rays->kind == RT_RAYS_DIRS) strat = 3;  // shared direction
@@ -153,7 +167,8 @@ rt_status rt_trace_launch(const rt_bvh *bvh, const rt_rayspec *rays, float *T_ou
         int grid = persistent_blocks((const void *)k_trace<S, C>, threads);                 \
         k_trace<S, C><<<grid, threads, 0, st>>>(b, rs, job, T_out, aux, work);              \
     } while (0)
-        if (strat == 4) { if (count) RT_LAUNCH(4, true); else RT_LAUNCH(4, false); }
+        if (strat == 5) { if (count) RT_LAUNCH(5, true); else RT_LAUNCH(5, false); }
+        else if (strat == 4) { if (count) RT_LAUNCH(4, true); else RT_LAUNCH(4, false); }
         else if (strat == 3) { if (count) RT_LAUNCH(3, true); else RT_LAUNCH(3, false); }
         else if (strat == 2) { if (count) RT_LAUNCH(2, true); else RT_LAUNCH(2, false); }
         else if (strat == 1) { if (count) RT_LAUNCH(1, true); else RT_LAUNCH(1, false); }

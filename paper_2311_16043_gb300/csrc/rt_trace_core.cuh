@@ -618,3 +618,114 @@ __device__ __forceinline__ void flush_counts(const TraceAux &aux, const WorkCoun
     }
 }
 
+
+// Strategy 5: one thread per ray over the 4-wide tree, with lanes refilled as
+// their rays finish (persistent threads with dynamic ray fetch, Aila & Laine
+// 2009).  Rays are the slots item*32 + l of a full implicit set (in the job's
+// item order); whenever at least kRefillMin lanes of the warp are idle, lane
+// 0 takes that many slots with one atomic and the idle lanes start them, so a
+// warp no longer waits for its longest ray.  Each step of a lane is one node
+// visit of trace_ray_wide's loop, and a ray's visits and factors come in the
+// same order as there: the same T.  Slots past a ragged last tile are
+// skipped.  `work` counts slots.
+#ifndef RT_REFILL_MIN
+#define RT_REFILL_MIN 8
+#endif
+constexpr int kRefillMin = RT_REFILL_MIN;
+
+template <bool COUNT>
+__device__ __forceinline__ void trace_refill(const BvhDev &b, const RaySetDev &rs, const TraceJob &job, float *T_out,
+                                             const TraceAux &aux, unsigned long long *work, WorkCounts &wc,
+                                             unsigned long long &rays_done) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const unsigned long long total = (unsigned long long)job.n_items * 32ull;
+    bool has = false, exhausted = false;
+    float3 o = make_float3(0.f, 0.f, 0.f), d = make_float3(0.f, 0.f, 1.f), inv = d, oi = o;
+    int32_t src = -1;
+    int64_t out_idx = 0;
+    float T = 1.0f;
+    uint32_t node = 0;
+    int sp = 0;
+    uint32_t stack[RT_WIDE_STACK];
+    for (;;) {
+        const unsigned idle = __ballot_sync(FULL, !has);
+        const int n_idle = __popc(idle);
+        if (!exhausted && (n_idle >= kRefillMin || n_idle == 32)) {
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(work, (unsigned long long)n_idle);
+            base = __shfl_sync(FULL, base, 0);
+            if (base + (unsigned long long)n_idle >= total) exhausted = true;
+            if (!has) {
+                const unsigned long long slot = base + (unsigned long long)__popc(idle & lt_mask);
+                if (slot < total) {
+                    int64_t tile;
+                    int32_t k;
+                    full_item(job, rs.K, (int64_t)(slot >> 5), tile, k);
+                    const int64_t p = tile * 32 + (int64_t)(slot & 31ull);
+                    if (p < b.n) {
+                        const float4 mu = __ldg(b.gauss + 4 * p);
+                        const int64_t g = __float_as_int(__ldg(b.gauss + 4 * p + 1).w);
+                        out_idx = g * rs.K + k;
+                        implicit_ray(rs, out_idx, k, g, mu, o, d);
+                        inv = safe_inv(d);
+                        oi = make_float3(o.x * inv.x, o.y * inv.y, o.z * inv.z);
+                        src = (int32_t)p;
+                        T = 1.0f;
+                        node = 0;
+                        sp = 0;
+                        has = true;
+                    }
+                }
+            }
+        }
+        if (__ballot_sync(FULL, has) == 0) {
+            if (exhausted) break;
+            continue;
+        }
+        if (!has) continue;
+        // one visit of trace_ray_wide's loop
+        const float4 *w = b.wide + 8 * (int64_t)node;
+        const float4 lx = __ldg(w), hx = __ldg(w + 1), ly = __ldg(w + 2), hy = __ldg(w + 3), lz = __ldg(w + 4),
+                     hz = __ldg(w + 5), rf = __ldg(w + 6);
+        const uint32_t r[4] = {__float_as_uint(rf.x), __float_as_uint(rf.y), __float_as_uint(rf.z),
+                               __float_as_uint(rf.w)};
+        const bool h[4] = {slab(lx.x, hx.x, ly.x, hy.x, lz.x, hz.x, oi, inv),
+                           slab(lx.y, hx.y, ly.y, hy.y, lz.y, hz.y, oi, inv),
+                           slab(lx.z, hx.z, ly.z, hy.z, lz.z, hz.z, oi, inv),
+                           slab(lx.w, hx.w, ly.w, hy.w, lz.w, hz.w, oi, inv)};
+        if (COUNT) wc.box += (r[0] != RT_EMPTY) + (r[1] != RT_EMPTY) + (r[2] != RT_EMPTY) + (r[3] != RT_EMPTY);
+        int next = -1;
+        bool overflow = false;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            if (!h[c]) continue;
+            if (r[c] & RT_LEAF_BIT) {
+                const int32_t p = (int32_t)(r[c] & ~RT_LEAF_BIT);
+                if (p != src) {
+                    if (COUNT) wc.gauss++;
+                    if (gauss_hit(b, p, o, d, T) && COUNT) wc.hits++;
+                }
+            } else if (next < 0) {
+                next = (int)r[c];
+            } else if (sp < RT_WIDE_STACK) {
+                stack[sp++] = r[c];
+            } else {
+                overflow = true;
+            }
+        }
+        if (overflow) rt_set_error(aux.status, RT_ERR_STACK_OVERFLOW);
+        bool done = overflow || T < b.t_min;
+        if (!done) {
+            if (next >= 0) node = (uint32_t)next;
+            else if (sp > 0) node = stack[--sp];
+            else done = true;
+        }
+        if (done) {
+            T_out[out_idx] = T < b.t_min ? 0.0f : T;
+            rays_done++;
+            has = false;
+        }
+    }
+}

@@ -16,7 +16,10 @@ def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def test_batch_equals_single_launches(orc):
+@pytest.mark.parametrize("autotune", [True, False])
+def test_batch_equals_single_launches(orc, autotune):
+    """Without tuning the env-map jobs run with lane refill (the batch's
+    per-ray slot queue), the direction sets as warp packets."""
     from paper_2311_16043_gb300 import rt
     sizes = [700, 9000, 31, 2500, 20000]
     env = scenes.envmap(399)
@@ -33,8 +36,10 @@ def test_batch_equals_single_launches(orc):
             T = torch.full((R,), -1.0, device="cuda")
             jobs.append((bvh, rs, T))
         scs.append((sc, bvh))
-    batch = rt.rt_batch_create(jobs, autotune=True)
+    batch = rt.rt_batch_create(jobs, autotune=autotune)
     info = batch.info()
+    if not autotune:
+        assert info["kernel"] == [3, 5] * len(sizes)
     # single launches with each job's chosen strategy give the same T bit for bit
     for (bvh, rs, T), kernel in zip(jobs, info["kernel"]):
         refs.append(rt.rt_trace_visibility(bvh, rs, opts=rt.trace_opts(kernel=kernel)))
@@ -47,7 +52,7 @@ def test_batch_equals_single_launches(orc):
         for (bvh, rs, T), ref in zip(jobs, refs):
             assert torch.equal(T, ref)
     assert info["n_rays"] == sum(T.numel() for _, _, T in jobs)
-    assert set(info["kernel"]) <= {1, 2, 3, 4}
+    assert set(info["kernel"]) <= {1, 2, 3, 4, 5}
     # oracle on sampled rays of the largest scene
     sc, bvh = scs[4]
     sel = scenes.sample_ray_ids(20000 * 16, 2000, 5)
@@ -77,7 +82,7 @@ def test_autotune_picks_a_valid_shape(n, kind):
         rs = rt.rayspec(rt.RT_RAYS_ENV, env=E, n_samples=64, seed=3)
     T = torch.empty(rt.rt_rayspec_count(bvh, rs), device="cuda")
     o = rt.rt_trace_autotune(bvh, rs, T)
-    assert o.kernel in (1, 2, 3, 4) and o.order_block in (1, 16, 128, 1024)
+    assert o.kernel in (1, 2, 3, 4, 5) and o.order_block in (1, 16, 128, 1024)
     a = rt.rt_trace_visibility(bvh, rs, opts=o)
     b = rt.rt_trace_visibility(bvh, rs, opts=rt.trace_opts(kernel=1))
     torch.cuda.synchronize()

@@ -58,7 +58,7 @@ def small(orc):
     return sc, dirs, ref
 
 
-@pytest.mark.parametrize("kernel", [1, 2, 3, 4])
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5])
 def test_small_scene_all_rays(small, kernel):
     sc, dirs, ref = small
     bvh = build(sc)
@@ -75,9 +75,12 @@ def test_kernels_agree(small):
     b = trace_dirs(bvh, dirs, kernel=2)
     c = trace_dirs(bvh, dirs, kernel=3)
     e = trace_dirs(bvh, dirs, kernel=4)
+    f = trace_dirs(bvh, dirs, kernel=5)
     np.testing.assert_array_equal(a, b)
     np.testing.assert_allclose(c, a, atol=1e-6, rtol=0)
     np.testing.assert_allclose(e, a, atol=1e-6, rtol=0)
+    # lane refill runs each ray's visits of the per-ray 4-wide loop in order
+    np.testing.assert_allclose(f, e, atol=1e-6, rtol=0)
 
 
 def test_wide_tree_counts(small):
@@ -249,7 +252,7 @@ def test_tiny_scenes(orc, n):
     ids = np.arange(n * 16, dtype=np.int64)
     o, d, s = orc.dir_rays(sc["mean"], dirs, ids)
     ref = orc.trace(sc, o, d, s)
-    for kernel in (1, 2, 3, 4):
+    for kernel in (1, 2, 3, 4, 5):
         compare(trace_dirs(bvh, dirs, kernel=kernel).reshape(-1), ref, max_excluded=1.0)
 
 
@@ -262,7 +265,7 @@ def test_object_scene_300k_sample(orc):
     sel = scenes.sample_ray_ids(300_000 * 128, 4096, 7)
     o, d, s = orc.dir_rays(sc["mean"], dirs, sel)
     ref = orc.trace(sc, o, d, s)
-    for kernel in (1, 3, 4):
+    for kernel in (1, 3, 4, 5):
         T = trace_dirs(bvh, dirs, kernel=kernel).reshape(-1)
         compare(T[sel], ref, max_excluded=0.01)
         assert np.all((T >= 0) & (T <= 1))
