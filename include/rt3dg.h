@@ -95,7 +95,9 @@ typedef struct rt_bvh rt_bvh;
  * bottom-up refit of the child boxes.  n = 0 and n = 1 are valid.
  * Synchronises `stream` once (to read the scene bounds into the handle).
  * Errors: RT_ERR_INVALID_ARG (n < 0, n >= 2^31, NULL arrays with n > 0,
- * k_sigma <= 0, alpha_min outside (0,1), t_min outside [0,1)), RT_ERR_OOM. */
+ * k_sigma <= 0, alpha_min outside (0,1), t_min outside [0,1), or Gaussian
+ * inputs failing the device check: a non-finite value, a scale <= 0, a zero
+ * quaternion, an opacity outside [0,1]), RT_ERR_OOM. */
 rt_status rt_build_bvh(const float *mean, const float *scale, const float *quat,
                        const float *opacity, int64_t n, const rt_params *params,
                        rt_stream_t stream, rt_bvh **out);
@@ -109,7 +111,9 @@ rt_status rt_bvh_destroy(rt_bvh *bvh, rt_stream_t stream);
  * goes stale.  The scene bounds reported by rt_bvh_info stay those of the
  * build.  Asynchronous on `stream` (the first call also derives the 4-wide
  * tree's parent links once).  Refitting with the build's inputs reproduces
- * the built tree bit for bit.  Errors: RT_ERR_INVALID_ARG. */
+ * the built tree bit for bit.  Errors: RT_ERR_INVALID_ARG (inputs failing the
+ * check of rt_build_bvh are reported through the status word, since the call
+ * does not synchronise). */
 rt_status rt_bvh_refit(rt_bvh *bvh, const float *mean, const float *scale, const float *quat,
                        const float *opacity, rt_stream_t stream);
 /* Host outputs (any may be NULL): Gaussian count, scene bounds of the means
@@ -124,6 +128,23 @@ rt_status rt_bvh_info(const rt_bvh *bvh, int64_t *n, float *lo, float *hi, int64
  *                      then right child box (lo xyz, hi xyz).              */
 rt_status rt_bvh_export(const rt_bvh *bvh, uint64_t *keys, int32_t *left, int32_t *right,
                         int32_t *parent, float *boxes, rt_stream_t stream);
+
+/* Caller's device allocator (the paper has no counterpart).  alloc returns
+ * `bytes` of device memory usable in stream order on `stream` (NULL on
+ * failure; the block must be 256-byte aligned), free releases a block in
+ * stream order.  With an allocator set, every device allocation the library
+ * makes — handles' buffers and per-call scratch — goes through it (e.g. a
+ * framework's caching allocator); NULL restores the default (cudaMallocAsync
+ * / cudaFreeAsync on the call's stream).  Process-wide: set it while no
+ * handle exists, since a handle returns its buffers through the allocator in
+ * force when it is destroyed.  rt_surrogate_infer_noalloc allocates nothing
+ * either way.  Errors: RT_ERR_INVALID_ARG (alloc or free missing). */
+typedef struct {
+    void *(*alloc)(size_t bytes, rt_stream_t stream, void *ctx);
+    void (*free)(void *ptr, rt_stream_t stream, void *ctx);
+    void *ctx;
+} rt_allocator;
+rt_status rt_set_allocator(const rt_allocator *a);
 
 /* ------------------------------------------------------------------------ */
 /* Ray sets                                                                   */

@@ -67,9 +67,29 @@ rt_status rt_check_launch() {
     return e == cudaSuccess ? RT_OK : RT_ERR_CUDA;
 }
 
+namespace {
+rt_allocator g_alloc = {nullptr, nullptr, nullptr};  // alloc == null: stream-ordered CUDA pool
+}
+
+extern "C" rt_status rt_set_allocator(const rt_allocator *a) {
+    if (a && (!a->alloc || !a->free)) return RT_ERR_INVALID_ARG;
+    if (a) g_alloc = *a;
+    else g_alloc = rt_allocator{nullptr, nullptr, nullptr};
+    return RT_OK;
+}
+
 rt_status rt_alloc(void **p, size_t bytes, rt_stream_t s) {
     *p = nullptr;
     if (bytes == 0) bytes = 256;
+    if (g_alloc.alloc) {
+        *p = g_alloc.alloc(bytes, s, g_alloc.ctx);
+        if (!*p || ((uintptr_t)*p & 255u)) {  // the layouts need 256-byte alignment
+            if (*p) g_alloc.free(*p, s, g_alloc.ctx);
+            *p = nullptr;
+            return RT_ERR_OOM;
+        }
+        return RT_OK;
+    }
     cudaError_t e = cudaMallocAsync(p, bytes, (cudaStream_t)s);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -80,7 +100,9 @@ rt_status rt_alloc(void **p, size_t bytes, rt_stream_t s) {
 }
 
 void rt_free(void *p, rt_stream_t s) {
-    if (p) cudaFreeAsync(p, (cudaStream_t)s);
+    if (!p) return;
+    if (g_alloc.free) g_alloc.free(p, s, g_alloc.ctx);
+    else cudaFreeAsync(p, (cudaStream_t)s);
 }
 
 int rt_num_sms() {

@@ -33,6 +33,37 @@ __device__ __forceinline__ float ord2f(uint32_t u) {
     return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
 }
 
+// Input check: every value finite, scales > 0, a non-zero quaternion and
+// opacity in [0, 1]; *bad becomes non-zero otherwise.
+__global__ void k_validate(const float *__restrict__ mean, const float *__restrict__ scale,
+                           const float *__restrict__ quat, const float *__restrict__ opacity, int64_t n,
+                           unsigned *bad) {
+    bool ok = true;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float qn = 0.0f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float m = mean[3 * i + c], sc = scale[3 * i + c];
+            ok = ok && isfinite(m) && isfinite(sc) && sc > 0.0f;
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float q = quat[4 * i + c];
+            ok = ok && isfinite(q);
+            qn += q * q;
+        }
+        const float o = opacity[i];
+        ok = ok && qn > 0.0f && o >= 0.0f && o <= 1.0f;
+    }
+    if (!ok) atomicOr(bad, 1u);
+}
+
+// Records a failed input check in the status word (asynchronous callers).
+__global__ void k_report_invalid(const unsigned *bad, int *status) {
+    if (*bad) rt_set_error(status, RT_ERR_INVALID_ARG);
+}
+
 // bounds_u[0..2] = ordered min, [3..5] = ordered max (pre-set to 0xff.. / 0)
 __global__ void k_bounds(const float *__restrict__ mean, int64_t n, uint32_t *bounds_u) {
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
@@ -612,12 +643,14 @@ extern "C" rt_status rt_build_bvh(const float *mean, const float *scale, const f
     unsigned *wcnt = (unsigned *)(sb + s_cnt2);  // [0..63] level counts, [64] wide-node count (512 B region)
 
     rt_status result = RT_OK;
+    unsigned bad = 0;  // host copy of the input check (read with the bounds)
     do {
         if (cudaMemsetAsync(bounds_u, 0xff, 12, st) != cudaSuccess ||
-            cudaMemsetAsync(bounds_u + 3, 0, 12, st) != cudaSuccess) {
+            cudaMemsetAsync(bounds_u + 3, 0, 20, st) != cudaSuccess) {
             result = RT_ERR_CUDA;
             break;
         }
+        k_validate<<<grid_for(n, 256), 256, 0, st>>>(mean, scale, quat, opacity, n, bounds_u + 7);
         k_bounds<<<grid_for(n, 256), 256, 0, st>>>(mean, n, bounds_u);
         k_morton<<<grid_for(n, 256), 256, 0, st>>>(mean, n, bounds_u, b->bounds, k0, v0);
         for (int pass = 0; pass < 4; ++pass) {
@@ -674,13 +707,15 @@ extern "C" rt_status rt_build_bvh(const float *mean, const float *scale, const f
             break;
         }
         if (cudaMemcpyAsync(b->lo, b->bounds, 3 * sizeof(float), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-            cudaMemcpyAsync(b->hi, b->bounds + 3, 3 * sizeof(float), cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+            cudaMemcpyAsync(b->hi, b->bounds + 3, 3 * sizeof(float), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(&bad, bounds_u + 7, sizeof(unsigned), cudaMemcpyDeviceToHost, st) != cudaSuccess) {
             result = RT_ERR_CUDA;
             break;
         }
     } while (0);
-    rt_free(scratch, stream);
     if (result == RT_OK && cudaStreamSynchronize(st) != cudaSuccess) result = RT_ERR_CUDA;
+    rt_free(scratch, stream);
+    if (result == RT_OK && bad) result = RT_ERR_INVALID_ARG;
     if (result != RT_OK) {
         rt_free(b->block, stream);
         delete b;
@@ -729,10 +764,12 @@ extern "C" rt_status rt_bvh_refit(rt_bvh *b, const float *mean, const float *sca
     rt_status result = RT_OK;
     do {
         if (cudaMemsetAsync(bounds_u, 0xff, 12, st) != cudaSuccess ||
-            cudaMemsetAsync(bounds_u + 3, 0, 12, st) != cudaSuccess) {
+            cudaMemsetAsync(bounds_u + 3, 0, 20, st) != cudaSuccess) {
             result = RT_ERR_CUDA;
             break;
         }
+        k_validate<<<grid_for(n, 256), 256, 0, st>>>(mean, scale, quat, opacity, n, bounds_u + 7);
+        k_report_invalid<<<1, 1, 0, st>>>(bounds_u + 7, rt_status_ptr());
         k_bounds<<<grid_for(n, 256), 256, 0, st>>>(mean, n, bounds_u);
         k_prep<<<grid_for(n, 128), 128, 0, st>>>(mean, scale, quat, opacity, b->perm, n, b->params, bounds_u,
                                                  b->gauss, leafbox);

@@ -55,6 +55,14 @@ class rt_pbr_inputs(C.Structure):
                 ("env_h", C.c_int32), ("env_w", C.c_int32), ("cam", C.c_float * 3), ("kernel", C.c_int32)]
 
 
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
+class rt_allocator(C.Structure):
+    _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("ctx", C.c_void_p)]
+
+
 class rt_instance(C.Structure):
     _fields_ = [("bvh", C.c_void_p), ("xform", C.c_float * 12)]
 
@@ -79,6 +87,7 @@ _SIGS = {
     "rt_status_last": (_I32, []),
     "rt_status_clear": (_I32, []),
     "rt_selftest_wait_timeout": (_I32, [_I64, _P]),
+    "rt_set_allocator": (_I32, [_P]),
     "rt_build_bvh": (_I32, [_P, _P, _P, _P, _I64, _P, _P, _P]),
     "rt_bvh_destroy": (_I32, [_P, _P]),
     "rt_bvh_refit": (_I32, [_P, _P, _P, _P, _P, _P]),
@@ -378,6 +387,33 @@ def rt_trace_ao(bvh: Bvh, rs: rt_rayspec, ao=None, opts: rt_trace_opts | None = 
     _check(lib().rt_trace_ao(bvh.handle, C.byref(rs), C.byref(opts) if opts is not None else None,
                              _ptr(ao, torch.float32, "ao"), _stream(stream)), "rt_trace_ao")
     return ao
+
+
+_ALLOCATOR = None  # keeps the ctypes callbacks alive while installed
+
+
+def use_torch_allocator(on: bool = True) -> None:
+    """Route the library's device allocations through torch's caching
+    allocator (on=True) or back to the stream-ordered CUDA pool (on=False).
+    Switch while no library handle exists."""
+    global _ALLOCATOR
+    if not on:
+        _check(lib().rt_set_allocator(None), "rt_set_allocator")
+        _ALLOCATOR = None
+        return
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+        except Exception:
+            return None
+
+    def _free(ptr, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    a = rt_allocator(_ALLOC_FN(_alloc), _FREE_FN(_free), None)
+    _check(lib().rt_set_allocator(C.byref(a)), "rt_set_allocator")
+    _ALLOCATOR = a
 
 
 class Scene:

@@ -1,0 +1,86 @@
+"""GPU checks of the boundary's host-facing contracts: the caller's
+allocator (torch's caching allocator through rt_set_allocator) and the
+device check of Gaussian inputs (synchronous error from the build, status
+word from the refit)."""
+import numpy as np
+import pytest
+import torch
+
+import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev(sc):
+    return {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in sc.items()}
+
+
+def test_torch_caching_allocator():
+    from paper_2311_16043_gb300 import rt
+    sc = scenes.uniform_scene(20_000, 3)
+    d = _dev(sc)
+    dirs = torch.from_numpy(scenes.fibonacci_sphere(16)).cuda()
+    bvh = rt.rt_build_bvh(d["mean"], d["scale"], d["quat"], d["opacity"])
+    ref = rt.rt_trace_visibility_dirs(bvh, dirs)
+    torch.cuda.synchronize()
+    bvh.destroy()
+    rt.use_torch_allocator(True)
+    try:
+        before = torch.cuda.memory_allocated()
+        bvh = rt.rt_build_bvh(d["mean"], d["scale"], d["quat"], d["opacity"])
+        torch.cuda.synchronize()
+        held = torch.cuda.memory_allocated() - before
+        assert held >= bvh.info()["device_bytes"]   # the tree lives in torch's pool
+        got = rt.rt_trace_visibility_dirs(bvh, dirs)  # per-call scratch goes through it too
+        torch.cuda.synchronize()
+        assert torch.equal(got, ref)
+        del got
+        bvh.destroy()
+        torch.cuda.synchronize()
+        assert torch.cuda.memory_allocated() == before
+    finally:
+        rt.use_torch_allocator(False)
+    assert rt.rt_status_last() == 0
+
+
+@pytest.mark.parametrize("field,index,value", [("mean", (5, 1), np.nan), ("scale", (7, 0), 0.0),
+                                               ("scale", (7, 2), -1.0), ("quat", (3,), 0.0),
+                                               ("opacity", (9,), 1.5), ("opacity", (9,), np.inf)])
+def test_build_rejects_bad_inputs(field, index, value):
+    from paper_2311_16043_gb300 import rt
+    sc = scenes.uniform_scene(1000, 4)
+    sc[field] = sc[field].copy()
+    sc[field][index] = value
+    d = _dev(sc)
+    with pytest.raises(rt.RTError) as e:
+        rt.rt_build_bvh(d["mean"], d["scale"], d["quat"], d["opacity"])
+    assert e.value.code == 1  # RT_ERR_INVALID_ARG
+    torch.cuda.synchronize()
+    assert rt.rt_status_last() == 0
+
+
+def test_build_accepts_edge_values():
+    from paper_2311_16043_gb300 import rt
+    sc = scenes.uniform_scene(1000, 4)
+    sc["opacity"][:3] = [0.0, 1.0, 1.0]
+    d = _dev(sc)
+    bvh = rt.rt_build_bvh(d["mean"], d["scale"], d["quat"], d["opacity"])
+    T = rt.rt_trace_visibility_dirs(bvh, torch.from_numpy(scenes.fibonacci_sphere(8)).cuda())
+    torch.cuda.synchronize()
+    assert rt.rt_status_last() == 0 and bool(torch.all((T >= 0) & (T <= 1)))
+
+
+def test_refit_reports_bad_inputs_through_the_status_word():
+    from paper_2311_16043_gb300 import rt
+    sc = scenes.uniform_scene(1000, 5)
+    d = _dev(sc)
+    bvh = rt.rt_build_bvh(d["mean"], d["scale"], d["quat"], d["opacity"])
+    bad = d["scale"].clone()
+    bad[11, 1] = float("nan")
+    rt.rt_bvh_refit(bvh, d["mean"], bad, d["quat"], d["opacity"])
+    torch.cuda.synchronize()
+    assert rt.rt_status_last() == 1
+    rt.rt_status_clear()
+    rt.rt_bvh_refit(bvh, d["mean"], d["scale"], d["quat"], d["opacity"])
+    torch.cuda.synchronize()
+    assert rt.rt_status_last() == 0
