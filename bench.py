@@ -50,7 +50,8 @@ WORKLOADS = {
     # under seeded rigid maps, two-level BVH, true inter-object occlusion
     "composed16_objects_k128": ("composed", 2_000_000, 60, 128),
 }
-KERNEL_NAMES = ["auto", "per-ray binary", "packet binary", "packet 4-wide", "per-ray 4-wide"]
+KERNEL_NAMES = ["auto", "per-ray binary", "packet binary", "packet 4-wide", "per-ray 4-wide",
+                "per-ray 4-wide, lane refill", "warp per ray"]
 ENV_SAMPLES = 512
 METRIC = "traced rays/s & ms per 2M-Gaussian visibility precompute; surrogate speedup at MAE"
 TRACE_SOURCES = ["paper_2311_16043_gb300/csrc/rt_trace.cu", "paper_2311_16043_gb300/csrc/rt_trace_core.cuh"]
@@ -66,8 +67,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="object_2m_k128")
-    ap.add_argument("--kernel", type=int, default=0, choices=range(5),
-                    help="0 auto, 1 per-ray binary, 2 packet binary, 3 packet 4-wide, 4 per-ray 4-wide")
+    ap.add_argument("--kernel", type=int, default=0, choices=range(7),
+                    help="0 auto, 1 per-ray binary, 2 packet binary, 3 packet 4-wide, 4 per-ray 4-wide, "
+                         "5 per-ray 4-wide with lane refill, 6 warp per ray")
     ap.add_argument("--order-block", type=int, default=0)
     ap.add_argument("--cpu-rays", type=int, default=2048, help="oracle sample for cpu_baseline")
     ap.add_argument("--cpu-lbvh-rays", type=int, default=1 << 20, help="sample for the CPU BVH tracer baseline")

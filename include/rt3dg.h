@@ -225,9 +225,12 @@ typedef enum {
     RT_KERNEL_WIDE = 3,   /* as PACKET over the 4-wide tree (the binary tree
                              collapsed by greedy largest-area expansion)       */
     RT_KERNEL_RAY_WIDE = 4, /* one thread per ray over the 4-wide tree        */
-    RT_KERNEL_RAY_REFILL = 5 /* as RAY_WIDE, idle lanes refilled with new rays
+    RT_KERNEL_RAY_REFILL = 5, /* as RAY_WIDE, idle lanes refilled with new rays
                               as theirs finish (full implicit sets; otherwise
                               RAY_WIDE)                                       */
+    RT_KERNEL_WARP_RAY = 6   /* one warp per ray over the 4-wide tree: the lanes
+                              expand up to 32 of the ray's nodes at once (few
+                              or latency-bound rays; no hit log)             */
 } rt_kernel;
 
 typedef struct {
@@ -445,8 +448,10 @@ rt_status rt_surrogate_train(rt_surrogate *s, const rt_bvh *bvh, const rt_rayspe
                              float *loss_curve, rt_stream_t stream);
 /* Visibility of an implicit ray set over `bvh` (DIRS or ENV, optionally a
  * ray_ids subset) from the surrogate: T_out[i] = p.  If band > 0, rays with
- * |p - 0.5| < band are traced on `bvh` instead (the fallback) and T_out holds
- * the traced value; n_fallback (device int64[1], may be NULL) receives their
+ * |p - 0.5| < band are traced on `bvh` instead (the fallback: one warp per
+ * ray, RT_KERNEL_WARP_RAY) and T_out holds the traced value, bit-equal to
+ * rt_trace_visibility with that kernel; n_fallback (device int64[1], may be
+ * NULL) receives their
  * number.  The scene bounds used to normalise origins are the surrogate's.
  * Errors: RT_ERR_INVALID_ARG. */
 rt_status rt_surrogate_infer(const rt_surrogate *s, const rt_bvh *bvh, const rt_rayspec *rays,

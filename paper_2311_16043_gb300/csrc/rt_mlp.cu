@@ -51,6 +51,14 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     return *reinterpret_cast<uint32_t *>(&h);
 }
 __device__ __forceinline__ float bf16_round(float a) { return __bfloat162float(__float2bfloat16_rn(a)); }
+// bf16 pair of max(a, 0), max(b, 0) (a in the low half): one conversion with
+// the ReLU folded in; rounding commutes with max(., 0), so the bits equal
+// pack_bf16(fmaxf(a, 0), fmaxf(b, 0)) for finite inputs.
+__device__ __forceinline__ uint32_t pack_bf16_relu(float a, float b) {
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(b), "f"(a));
+    return d;
+}
 __device__ __forceinline__ float bf16_lo(uint32_t u) { return __uint_as_float(u << 16); }
 __device__ __forceinline__ float bf16_hi(uint32_t u) { return __uint_as_float(u & 0xffff0000u); }
 
@@ -110,11 +118,17 @@ __device__ __forceinline__ void encode(float3 p, float3 d, const float *lo, cons
     for (int c = 0; c < 6; ++c) {
         f[13 * c] = xh[c];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) {
+        for (int k = 0; k < 6; k += 2) {
+            // even k from the exactly reduced argument; odd k by one
+            // double-angle step from it, sin 2a = 2 sin a cos a and
+            // cos 2a = (cos a - sin a)(cos a + sin a): ~2 float32 ulp,
+            // far below the bf16 spacing the features are rounded to
             float sv, cv;
             sincospi_k(xh[c], xl[c], k, sv, cv);
             f[13 * c + 1 + 2 * k] = sv;
             f[13 * c + 2 + 2 * k] = cv;
+            f[13 * c + 3 + 2 * k] = 2.0f * (sv * cv);
+            f[13 * c + 4 + 2 * k] = (cv - sv) * (cv + sv);
         }
     }
     f[78] = 0.0f;
@@ -142,6 +156,19 @@ __device__ __forceinline__ void store_chunk(uint8_t *img, int r, int c0, const f
         u.y = pack_bf16(v[8 * q + 2], v[8 * q + 3]);
         u.z = pack_bf16(v[8 * q + 4], v[8 * q + 5]);
         u.w = pack_bf16(v[8 * q + 6], v[8 * q + 7]);
+        *reinterpret_cast<uint4 *>(img + img_off(r, c0 + 8 * q, H)) = u;
+    }
+}
+
+// As store_chunk with the ReLU applied in the conversion.
+__device__ __forceinline__ void store_chunk_relu(uint8_t *img, int r, int c0, const float (&v)[32]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        uint4 u;
+        u.x = pack_bf16_relu(v[8 * q + 0], v[8 * q + 1]);
+        u.y = pack_bf16_relu(v[8 * q + 2], v[8 * q + 3]);
+        u.z = pack_bf16_relu(v[8 * q + 4], v[8 * q + 5]);
+        u.w = pack_bf16_relu(v[8 * q + 6], v[8 * q + 7]);
         *reinterpret_cast<uint4 *>(img + img_off(r, c0 + 8 * q, H)) = u;
     }
 }
@@ -327,12 +354,12 @@ __global__ void __launch_bounds__(128 * INF_WG, 1) k_mlp_infer(MlpDev net, Sampl
                 float v[32];
                 tmem_ld32(lane_addr + 32 * cc, v);
 #pragma unroll
-                for (int k = 0; k < 32; ++k) v[k] = fmaxf(v[k] + bl[32 * cc + k], 0.0f);
+                for (int k = 0; k < 32; ++k) v[k] += bl[32 * cc + k];
                 if (l < 3) {
-                    store_chunk(act, tl, 32 * cc, v);
+                    store_chunk_relu(act, tl, 32 * cc, v);
                 } else {
 #pragma unroll
-                    for (int k = 0; k < 32; ++k) z5 = fmaf(bias[512 + 32 * cc + k], bf16_round(v[k]), z5);
+                    for (int k = 0; k < 32; ++k) z5 = fmaf(bias[512 + 32 * cc + k], bf16_round(fmaxf(v[k], 0.0f)), z5);
                 }
             }
         }

@@ -34,6 +34,35 @@ __global__ void __launch_bounds__(128, RT_TRACE_MIN_BLOCKS) k_trace(BvhDev b, Ra
         flush_counts<COUNT>(aux, wc, rays_done);
         return;
     }
+    if (STRAT == 6) {  // one warp per ray: an item is one ray
+        __shared__ uint32_t wstk_all[STRAT == 6 ? 4 * kWarpStack : 1];
+        uint32_t *wstk = wstk_all + (threadIdx.x >> 5) * kWarpStack;
+        for (;;) {
+            unsigned long long item = 0;
+            if (lane == 0) item = atomicAdd(work, 1ull);
+            item = __shfl_sync(FULL, item, 0);
+            int64_t n_out = job.mode == MODE_FULL ? job.n_items * 32 : job.n_out;  // slots
+            if (job.dyn_count) {
+                const int64_t c = (int64_t)*job.dyn_count;
+                n_out = c < n_out ? c : n_out;
+            }
+            if ((int64_t)item >= n_out) break;
+            float3 o, d;
+            int32_t src;
+            int64_t out_idx;
+            if (!ray_of(b, rs, job, (int64_t)item, o, d, src, out_idx, aux.status)) {
+                if (lane == 0 && out_idx >= 0) T_out[out_idx] = __int_as_float(0x7fc00000);
+                continue;
+            }
+            const float T = trace_warp_ray<COUNT>(b, o, d, src, wstk, wc, aux.status);
+            if (lane == 0) {
+                T_out[out_idx] = T;
+                rays_done++;
+            }
+        }
+        flush_counts<COUNT>(aux, wc, rays_done);
+        return;
+    }
     for (;;) {
         unsigned long long item = 0;
         if (lane == 0) item = atomicAdd(work, 1ull);
@@ -71,7 +100,10 @@ rt_status rt_trace_launch_job(const BvhDev &b, const RaySetDev &rs, const TraceJ
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemsetAsync(work, 0, sizeof(unsigned long long), st) != cudaSuccess) return RT_ERR_CUDA;
     const int threads = 128;
-    if (strat == 5 && b.wide && job.mode == MODE_FULL) {
+    if (strat == 6 && b.wide) {
+        int grid = persistent_blocks((const void *)k_trace<6, false>, threads);
+        k_trace<6, false><<<grid, threads, 0, st>>>(b, rs, job, T_out, aux, work);
+    } else if (strat == 5 && b.wide && job.mode == MODE_FULL) {
         int grid = persistent_blocks((const void *)k_trace<5, false>, threads);
         k_trace<5, false><<<grid, threads, 0, st>>>(b, rs, job, T_out, aux, work);
     } else if (strat >= 4 && b.wide) {
@@ -108,7 +140,7 @@ rt_status rt_trace_launch(const rt_bvh *bvh, const rt_rayspec *rays, float *T_ou
     rt_trace_opts o;
     memset(&o, 0, sizeof(o));
     if (opts) o = *opts;
-    if (o.kernel < 0 || o.kernel > 5 || o.order_block < 0 || o.block_threads < 0) return RT_ERR_INVALID_ARG;
+    if (o.kernel < 0 || o.kernel > 6 || o.order_block < 0 || o.block_threads < 0) return RT_ERR_INVALID_ARG;
     if ((o.hit_ids && (o.hit_cap <= 0 || !o.hit_count)) ) return RT_ERR_INVALID_ARG;
     if (count == 0) return RT_OK;
 
@@ -131,8 +163,11 @@ rt_status rt_trace_launch(const rt_bvh *bvh, const rt_rayspec *rays, float *T_ou
     } else {
         job.n_items = (count + 31) / 32;
     }
-    int strat = o.kernel == RT_KERNEL_RAY_REFILL ? 5 : o.kernel == RT_KERNEL_RAY_WIDE ? 4
-              : o.kernel == RT_KERNEL_WIDE ? 2 : o.kernel == RT_KERNEL_PACKET ? 1 : 0;
+    int strat = o.kernel == RT_KERNEL_WARP_RAY ? 6 : o.kernel == RT_KERNEL_RAY_REFILL ? 5
+              : o.kernel == RT_KERNEL_RAY_WIDE ? 4 : o.kernel == RT_KERNEL_WIDE ? 2
+              : o.kernel == RT_KERNEL_PACKET ? 1 : 0;
+    // one warp per ray needs the 4-wide tree and keeps no hit log
+    if (strat == 6 && (bvh->n_wide == 0 || o.hit_ids)) strat = bvh->n_wide ? 4 : 0;
     // AUTO: warp packets sharing the direction for a direction set; per-ray
     // traversal with lane refill for env-map and hemisphere sets (directions
     // differ across a tile)
@@ -167,7 +202,8 @@ rt_status rt_trace_launch(const rt_bvh *bvh, const rt_rayspec *rays, float *T_ou
         int grid = persistent_blocks((const void *)k_trace<S, C>, threads);                 \
         k_trace<S, C><<<grid, threads, 0, st>>>(b, rs, job, T_out, aux, work);              \
     } while (0)
-        if (strat == 5) { if (count) RT_LAUNCH(5, true); else RT_LAUNCH(5, false); }
+        if (strat == 6) { if (count) RT_LAUNCH(6, true); else RT_LAUNCH(6, false); }
+        else if (strat == 5) { if (count) RT_LAUNCH(5, true); else RT_LAUNCH(5, false); }
         else if (strat == 4) { if (count) RT_LAUNCH(4, true); else RT_LAUNCH(4, false); }
         else if (strat == 3) { if (count) RT_LAUNCH(3, true); else RT_LAUNCH(3, false); }
         else if (strat == 2) { if (count) RT_LAUNCH(2, true); else RT_LAUNCH(2, false); }
@@ -208,8 +244,16 @@ rt_status rt_trace_launch_list(const rt_bvh *bvh, const rt_rayspec *rays, const 
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemsetAsync(work, 0, sizeof(unsigned long long), st) != cudaSuccess) return RT_ERR_CUDA;
     const int threads = 128;
-    int grid = persistent_blocks((const void *)k_trace<0, false>, threads);
-    k_trace<0, false><<<grid, threads, 0, st>>>(bvh_dev(bvh), rs, job, T_out, aux, work);
+    // the listed rays are few and scattered: one warp per ray over the 4-wide
+    // tree (its lanes expand the ray's nodes in parallel), which cuts the
+    // latency of the longest traversal
+    if (bvh->n_wide > 0) {
+        int grid = persistent_blocks((const void *)k_trace<6, false>, threads);
+        k_trace<6, false><<<grid, threads, 0, st>>>(bvh_dev(bvh), rs, job, T_out, aux, work);
+    } else {
+        int grid = persistent_blocks((const void *)k_trace<0, false>, threads);
+        k_trace<0, false><<<grid, threads, 0, st>>>(bvh_dev(bvh), rs, job, T_out, aux, work);
+    }
     return rt_check_launch();
 }
 

@@ -525,6 +525,52 @@ __device__ __forceinline__ void full_item(const TraceJob &job, int32_t K, int64_
 }
 
 
+// Ray r of a job in slot order: MODE_FULL slot r (item r/32, lane r%32;
+// false past a ragged last tile, out_idx = -1), MODE_EXPLICIT / MODE_IDS
+// entry r (an invalid id records RT_ERR_INVALID_ARG and returns false with
+// out_idx set).
+__device__ __forceinline__ bool ray_of(const BvhDev &b, const RaySetDev &rs, const TraceJob &job, int64_t r,
+                                       float3 &o, float3 &d, int32_t &src, int64_t &out_idx, int *status) {
+    src = -1;
+    out_idx = -1;
+    o = make_float3(0.f, 0.f, 0.f);
+    d = make_float3(0.f, 0.f, 1.f);
+    if (job.mode == MODE_FULL) {
+        int64_t tile;
+        int32_t k;
+        full_item(job, rs.K, r >> 5, tile, k);
+        const int64_t p = tile * 32 + (r & 31);
+        if (p >= b.n) return false;
+        const float4 mu = __ldg(b.gauss + 4 * p);
+        const int64_t g = __float_as_int(__ldg(b.gauss + 4 * p + 1).w);
+        out_idx = g * rs.K + k;
+        implicit_ray(rs, out_idx, k, g, mu, o, d);
+        src = (int32_t)p;
+        return true;
+    }
+    out_idx = job.out_index ? job.out_index[r] : r;
+    if (job.mode == MODE_EXPLICIT) {
+        o = make_float3(rs.ray_o[3 * r], rs.ray_o[3 * r + 1], rs.ray_o[3 * r + 2]);
+        d = make_float3(rs.ray_d[3 * r], rs.ray_d[3 * r + 1], rs.ray_d[3 * r + 2]);
+        if (rs.ray_src) {
+            const int32_t sg = rs.ray_src[r];
+            src = (sg >= 0 && sg < b.n) ? b.rank[sg] : -1;
+        }
+        return true;
+    }
+    const int64_t rid = rs.ray_ids[r];
+    if (rid < 0 || rid >= rs.n_rays) {
+        rt_set_error(status, RT_ERR_INVALID_ARG);
+        return false;
+    }
+    const int64_t g = rid / rs.K;
+    const int32_t k = (int32_t)(rid - g * rs.K);
+    const int32_t p = b.rank[g];
+    implicit_ray(rs, rid, k, g, __ldg(b.gauss + 4 * (int64_t)p), o, d);
+    src = p;
+    return true;
+}
+
 // One work item (32 rays) of a trace job: build each lane's ray, traverse,
 // write T (and the hit log).  Shared by the single-scene and batched kernels.
 // STRAT: 0 per-ray binary, 1 packet binary, 2 packet 4-wide, 3 packet 4-wide
@@ -728,4 +774,96 @@ __device__ __forceinline__ void trace_refill(const BvhDev &b, const RaySetDev &r
             has = false;
         }
     }
+}
+
+// Strategy 6: one warp per ray over the 4-wide tree, for few or latency-bound
+// rays (fallback lists, small sets).  The lanes take up to 32 entries off the
+// top of a shared stack, visit those nodes in parallel, multiply the factors
+// of their leaf hits into lane-local partial products and push the hit
+// internal children (warp prefix sum); T is the product of the partials,
+// formed by a warp butterfly after every step for the early exit.  A step
+// takes k = min(32, size, (cap - size)/3) entries, so the stack never exceeds
+// cap (RT_ERR_STACK_OVERFLOW if no entry can be taken).  Same accepted set as
+// the per-ray traversals; the product is formed in another order.
+constexpr int kWarpStack = 2048;
+
+__device__ __forceinline__ float warp_product(float v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v *= __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+template <bool COUNT>
+__device__ __forceinline__ float trace_warp_ray(const BvhDev &b, float3 o, float3 d, int32_t src, uint32_t *wstk,
+                                                WorkCounts &wc, int *status) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    float Tl = 1.0f;
+    if (b.n <= 0) return 1.0f;
+    if (b.n == 1) {
+        if (lane == 0 && src != 0) {
+            if (COUNT) wc.gauss++;
+            if (gauss_hit(b, 0, o, d, Tl) && COUNT) wc.hits++;
+        }
+        const float T = __shfl_sync(FULL, Tl, 0);
+        return T < b.t_min ? 0.0f : T;
+    }
+    const float3 inv = safe_inv(d);
+    const float3 oi = make_float3(o.x * inv.x, o.y * inv.y, o.z * inv.z);
+    if (lane == 0) wstk[0] = 0u;
+    int size = 1;
+    __syncwarp();
+    for (;;) {
+        int k = min(32, min(size, (kWarpStack - size) / 3));
+        if (k <= 0) {
+            if (size > 0) rt_set_error(status, RT_ERR_STACK_OVERFLOW);
+            break;
+        }
+        const bool active = lane < k;
+        const uint32_t node = active ? wstk[size - 1 - lane] : 0u;
+        size -= k;
+        __syncwarp();
+        uint32_t push[4];
+        int n_push = 0;
+        if (active) {
+            const float4 *w = b.wide + 8 * (int64_t)node;
+            const float4 lx = __ldg(w), hx = __ldg(w + 1), ly = __ldg(w + 2), hy = __ldg(w + 3),
+                         lz = __ldg(w + 4), hz = __ldg(w + 5), rf = __ldg(w + 6);
+            const uint32_t r[4] = {__float_as_uint(rf.x), __float_as_uint(rf.y), __float_as_uint(rf.z),
+                                   __float_as_uint(rf.w)};
+            const bool h[4] = {slab(lx.x, hx.x, ly.x, hy.x, lz.x, hz.x, oi, inv),
+                               slab(lx.y, hx.y, ly.y, hy.y, lz.y, hz.y, oi, inv),
+                               slab(lx.z, hx.z, ly.z, hy.z, lz.z, hz.z, oi, inv),
+                               slab(lx.w, hx.w, ly.w, hy.w, lz.w, hz.w, oi, inv)};
+            if (COUNT) wc.box += (r[0] != RT_EMPTY) + (r[1] != RT_EMPTY) + (r[2] != RT_EMPTY) + (r[3] != RT_EMPTY);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                if (!h[c]) continue;
+                if (r[c] & RT_LEAF_BIT) {
+                    const int32_t p = (int32_t)(r[c] & ~RT_LEAF_BIT);
+                    if (p != src) {
+                        if (COUNT) wc.gauss++;
+                        if (gauss_hit(b, p, o, d, Tl) && COUNT) wc.hits++;
+                    }
+                } else {
+                    push[n_push++] = r[c];
+                }
+            }
+        }
+        // warp prefix sum of the pushes, then write them above the stack top
+        int pre = n_push;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int v = __shfl_up_sync(FULL, pre, off);
+            if (lane >= off) pre += v;
+        }
+        const int total = __shfl_sync(FULL, pre, 31);
+        const int base = size + pre - n_push;
+        for (int q = 0; q < n_push; ++q) wstk[base + q] = push[q];
+        size += total;
+        __syncwarp();
+        if (warp_product(Tl) < b.t_min || size == 0) break;
+    }
+    const float T = warp_product(Tl);
+    return T < b.t_min ? 0.0f : T;
 }

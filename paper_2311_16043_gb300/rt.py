@@ -23,7 +23,8 @@ STATUS_NAMES = {0: "RT_OK", 1: "RT_ERR_INVALID_ARG", 2: "RT_ERR_OOM", 3: "RT_ERR
                 4: "RT_ERR_STACK_OVERFLOW", 5: "RT_ERR_HITLOG_OVERFLOW", 6: "RT_ERR_TIMEOUT",
                 7: "RT_ERR_NOT_TRAINED", 8: "RT_ERR_UNSUPPORTED"}
 RT_RAYS_EXPLICIT, RT_RAYS_DIRS, RT_RAYS_ENV, RT_RAYS_HEMI = 0, 1, 2, 3
-RT_KERNEL_AUTO, RT_KERNEL_RAY, RT_KERNEL_PACKET, RT_KERNEL_WIDE, RT_KERNEL_RAY_WIDE, RT_KERNEL_RAY_REFILL = 0, 1, 2, 3, 4, 5
+(RT_KERNEL_AUTO, RT_KERNEL_RAY, RT_KERNEL_PACKET, RT_KERNEL_WIDE, RT_KERNEL_RAY_WIDE, RT_KERNEL_RAY_REFILL,
+ RT_KERNEL_WARP_RAY) = 0, 1, 2, 3, 4, 5, 6
 
 
 class RTError(RuntimeError):

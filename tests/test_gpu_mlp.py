@@ -172,8 +172,8 @@ def test_training_and_fallback():
     assert curve[-50:].mean() < 0.8 * curve[:5].mean(), (curve[:5], curve[-50:])
     held = scenes.rotated_fibonacci(32, 51)
     rs_h = rt.rayspec(rt.RT_RAYS_DIRS, dirs=_dev(held))
-    # fallback rays are traced one thread per ray: compare with that traversal
-    T_h = rt.rt_trace_visibility(bvh, rs_h, opts=rt.trace_opts(kernel=rt.RT_KERNEL_RAY))
+    # fallback rays are traced one warp per ray: compare with that traversal
+    T_h = rt.rt_trace_visibility(bvh, rs_h, opts=rt.trace_opts(kernel=rt.RT_KERNEL_WARP_RAY))
     p = rt.rt_surrogate_infer(s, bvh, rs_h, band=0.0)
     nfb = torch.zeros(1, dtype=torch.int64, device="cuda")
     q = rt.rt_surrogate_infer(s, bvh, rs_h, band=0.3, n_fallback=nfb)

@@ -58,7 +58,7 @@ def small(orc):
     return sc, dirs, ref
 
 
-@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5, 6])
 def test_small_scene_all_rays(small, kernel):
     sc, dirs, ref = small
     bvh = build(sc)
@@ -81,6 +81,9 @@ def test_kernels_agree(small):
     np.testing.assert_allclose(e, a, atol=1e-6, rtol=0)
     # lane refill runs each ray's visits of the per-ray 4-wide loop in order
     np.testing.assert_allclose(f, e, atol=1e-6, rtol=0)
+    # one warp per ray: the same accepted set, another product order
+    w = trace_dirs(bvh, dirs, kernel=6)
+    np.testing.assert_allclose(w, e, atol=1e-6, rtol=0)
 
 
 def test_wide_tree_counts(small):
@@ -166,7 +169,7 @@ def test_explicit_rays_and_counters(orc):
     ref = orc.trace(sc, ro, rd, src)
     bvh = build(sc)
     outs, cnts = [], []
-    for kernel in (1, 2, 3, 4):
+    for kernel in (1, 2, 3, 4, 6):
         cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
         rs = rt.rayspec(rt.RT_RAYS_EXPLICIT, ray_o=_dev(ro), ray_d=_dev(rd), ray_src=_dev(src))
         T = rt.rt_trace_visibility(bvh, rs, opts=rt.trace_opts(kernel=kernel, counters=cnt))
@@ -176,6 +179,8 @@ def test_explicit_rays_and_counters(orc):
     compare(outs[0], ref)
     compare(outs[2], ref)
     compare(outs[3], ref)
+    compare(outs[4], ref)  # one warp per ray
+    assert cnts[4][3] == R
     np.testing.assert_array_equal(outs[0], outs[1])
     np.testing.assert_array_equal(cnts[0], cnts[1])
     assert cnts[0][3] == R
@@ -218,6 +223,28 @@ def test_id_subset_matches_full_trace(small):
     np.testing.assert_array_equal(T.cpu().numpy().astype(np.float64), full[sel])
 
 
+def test_warp_per_ray_id_subset(small):
+    """One warp per ray on an id list, including an invalid id (NaN output,
+    status set): the same values as the full trace with that kernel."""
+    from paper_2311_16043_gb300 import rt
+    sc, dirs, _ = small
+    bvh = build(sc)
+    full = trace_dirs(bvh, dirs, kernel=6).reshape(-1)
+    sel = scenes.sample_ray_ids(4096 * 32, 777, 9)
+    rs = rt.rayspec(rt.RT_RAYS_DIRS, dirs=_dev(dirs), ray_ids=_dev(sel))
+    T = rt.rt_trace_visibility(bvh, rs, opts=rt.trace_opts(kernel=6))
+    torch.cuda.synchronize()
+    assert rt.rt_status_last() == 0
+    np.testing.assert_array_equal(T.cpu().numpy().astype(np.float64), full[sel])
+    bad = sel.copy()
+    bad[5] = 4096 * 32
+    T = rt.rt_trace_visibility(bvh, rt.rayspec(rt.RT_RAYS_DIRS, dirs=_dev(dirs), ray_ids=_dev(bad)),
+                               opts=rt.trace_opts(kernel=6))
+    torch.cuda.synchronize()
+    assert rt.rt_status_last() == 1 and np.isnan(T[5].item())
+    rt.rt_status_clear()
+
+
 def test_materialized_rays_bit_exact(orc, small):
     from paper_2311_16043_gb300 import rt
     sc, dirs, _ = small
@@ -252,7 +279,7 @@ def test_tiny_scenes(orc, n):
     ids = np.arange(n * 16, dtype=np.int64)
     o, d, s = orc.dir_rays(sc["mean"], dirs, ids)
     ref = orc.trace(sc, o, d, s)
-    for kernel in (1, 2, 3, 4, 5):
+    for kernel in (1, 2, 3, 4, 5, 6):
         compare(trace_dirs(bvh, dirs, kernel=kernel).reshape(-1), ref, max_excluded=1.0)
 
 
