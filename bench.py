@@ -606,7 +606,9 @@ def run_reference(args, rank, world):
     if isinstance(sc, list):  # batched scenes: sample rays of the largest scene
         sc = max(sc, key=lambda x: x["mean"].shape[0])
     n, K = sc["mean"].shape[0], dirs.shape[0]
-    m = max(32, min(args.cpu_rays, int(4e8 // max(n, 1))))  # ~4e8 ray-Gaussian tests per step
+    # at least 64 rays per host core (the oracle hands out rays in chunks of
+    # 64), else ~4e8 ray-Gaussian tests per step
+    m = max(64 * (os.cpu_count() or 1), min(args.cpu_rays, int(4e8 // max(n, 1))))
     rates = []
     for i in range(args.warmup + args.steps):
         r, dt = oracle_rate(sc, dirs, m, seed=1000 + i)
