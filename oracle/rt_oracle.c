@@ -49,7 +49,7 @@
  *                      rounding emulated where the GPU stores bf16, FP64
  *                      accumulation.
  *
- * Readings where the paper is silent (each is listed in the design doc):
+ * Readings where the paper is silent:
  *   - accept Gaussian j on a ray iff t* > 0, m^2 <= k_sigma^2 and
  *     alpha >= alpha_min (alpha = o * exp(-m^2/2)); no clamp of alpha;
  *   - the ray's own source Gaussian is excluded by index;
