@@ -271,7 +271,10 @@ rt_status launch_reduce(const rt_bvh *bvh, const RaySetDev &rs, const ShadeDev &
         k_trace_reduce<ST, MODE><<<grid, 128, smem, st>>>(b, rs, S, out, rt_status_ptr(), work); \
         res = rt_check_launch();                                                          \
     } while (0)
-        if (b.wide == nullptr) res = RT_ERR_UNSUPPORTED;
+        // a tree of fewer than 2 Gaussians has no 4-wide form: strategy 4
+        // handles it without touching one
+        if (b.wide == nullptr && b.n >= 2) res = RT_ERR_UNSUPPORTED;
+        else if (b.wide == nullptr) RT_REDUCE(4);
         else if (strat == 3) RT_REDUCE(3);
         else if (strat == 2) RT_REDUCE(2);
         else RT_REDUCE(4);

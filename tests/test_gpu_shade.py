@@ -227,6 +227,28 @@ def test_ao_matches_oracle(orc, kind):
             assert (ao - T.view(n, K).mean(1)).abs().max().item() <= 1e-6
 
 
+@pytest.mark.parametrize("n", [1, 2, 45])
+def test_fused_tiny_scenes(orc, n):
+    """Fused colour and AO on scenes of 1, 2 and 45 Gaussians (no 4-wide
+    tree for one Gaussian; a ragged warp) against the table path."""
+    from paper_2311_16043_gb300 import rt
+    sc = scenes.uniform_scene(n, 31, lo=-0.05, hi=0.05)
+    nrm = scenes.shortest_axis_normals(sc["scale"], sc["quat"])
+    hemi = scenes.fibonacci_hemisphere(16)
+    m, env = _material(n, 3)
+    bvh = _build(sc)
+    rs = _hemi_spec(nrm, hemi)
+    inp = _inputs(m, env, (0.5, 0.5, 2.0))
+    V = rt.rt_trace_visibility(bvh, rs, opts=rt.trace_opts(kernel=4))
+    a = rt.rt_pbr_shade(bvh, rs, inp, V=V)
+    b = rt.rt_pbr_shade(bvh, rs, inp)
+    ao = rt.rt_trace_ao(bvh, rs)
+    torch.cuda.synchronize()
+    assert rt.rt_status_last() == 0
+    torch.testing.assert_close(b, a, rtol=1e-5, atol=1e-7)
+    assert (ao - V.view(n, 16).mean(1)).abs().max().item() <= 1e-6
+
+
 def test_shade_argument_errors():
     from paper_2311_16043_gb300 import rt
     sc = scenes.uniform_scene(100, 3)
