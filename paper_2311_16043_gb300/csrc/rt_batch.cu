@@ -145,10 +145,8 @@ __device__ __forceinline__ void batch_refill(const BatchJobDev *__restrict__ job
                      hz = __ldg(w + 5), rf = __ldg(w + 6);
         const uint32_t r[4] = {__float_as_uint(rf.x), __float_as_uint(rf.y), __float_as_uint(rf.z),
                                __float_as_uint(rf.w)};
-        const bool h[4] = {slab(lx.x, hx.x, ly.x, hy.x, lz.x, hz.x, oi, inv),
-                           slab(lx.y, hx.y, ly.y, hy.y, lz.y, hz.y, oi, inv),
-                           slab(lx.z, hx.z, ly.z, hy.z, lz.z, hz.z, oi, inv),
-                           slab(lx.w, hx.w, ly.w, hy.w, lz.w, hz.w, oi, inv)};
+        bool h[4];
+        slab4(lx, hx, ly, hy, lz, hz, oi, inv, h);
         int next = -1;
         bool overflow = false;
 #pragma unroll

@@ -77,6 +77,52 @@ __device__ __forceinline__ bool slab_sorted(float nx, float fx, float ny, float 
     return tnear <= fmaf(fabsf(tfar), 1e-6f, tfar);
 }
 
+// slab for two children at once (children a, b of a 4-wide node, lo/hi as
+// (a, b) pairs), packed FMAs as in slab_sorted2; same results as two slab
+// calls.
+__device__ __forceinline__ void slab2(float2 lx, float2 hx, float2 ly, float2 hy, float2 lz, float2 hz, float2 ix,
+                                      float2 iy, float2 iz, float2 ox, float2 oy, float2 oz, bool &ha, bool &hb) {
+    const float2 tx0 = __ffma2_rn(lx, ix, ox), tx1 = __ffma2_rn(hx, ix, ox);
+    const float2 ty0 = __ffma2_rn(ly, iy, oy), ty1 = __ffma2_rn(hy, iy, oy);
+    const float2 tz0 = __ffma2_rn(lz, iz, oz), tz1 = __ffma2_rn(hz, iz, oz);
+    const float na = fmaxf(fmaxf(fminf(tx0.x, tx1.x), fminf(ty0.x, ty1.x)), fmaxf(fminf(tz0.x, tz1.x), 0.0f));
+    const float fa = fminf(fminf(fmaxf(tx0.x, tx1.x), fmaxf(ty0.x, ty1.x)), fmaxf(tz0.x, tz1.x));
+    const float nb = fmaxf(fmaxf(fminf(tx0.y, tx1.y), fminf(ty0.y, ty1.y)), fmaxf(fminf(tz0.y, tz1.y), 0.0f));
+    const float fb = fminf(fminf(fmaxf(tx0.y, tx1.y), fmaxf(ty0.y, ty1.y)), fmaxf(tz0.y, tz1.y));
+    ha = na <= fmaf(fabsf(fa), 1e-6f, fa);
+    hb = nb <= fmaf(fabsf(fb), 1e-6f, fb);
+}
+
+// The four children of a 4-wide node (rows lo.x, hi.x, lo.y, hi.y, lo.z,
+// hi.z as float4) against a ray: two slab2 calls.
+__device__ __forceinline__ void slab4(float4 lx, float4 hx, float4 ly, float4 hy, float4 lz, float4 hz, float3 oi,
+                                      float3 inv, bool (&h)[4]) {
+    const float2 ix = make_float2(inv.x, inv.x), iy = make_float2(inv.y, inv.y), iz = make_float2(inv.z, inv.z);
+    const float2 ox = make_float2(-oi.x, -oi.x), oy = make_float2(-oi.y, -oi.y), oz = make_float2(-oi.z, -oi.z);
+    slab2(make_float2(lx.x, lx.y), make_float2(hx.x, hx.y), make_float2(ly.x, ly.y), make_float2(hy.x, hy.y),
+          make_float2(lz.x, lz.y), make_float2(hz.x, hz.y), ix, iy, iz, ox, oy, oz, h[0], h[1]);
+    slab2(make_float2(lx.z, lx.w), make_float2(hx.z, hx.w), make_float2(ly.z, ly.w), make_float2(hy.z, hy.w),
+          make_float2(lz.z, lz.w), make_float2(hz.z, hz.w), ix, iy, iz, ox, oy, oz, h[2], h[3]);
+}
+
+// slab_sorted for two children at once: the plane distances of both along
+// an axis come from one packed FMA (fma.rn.f32x2 rounds each half as fmaf),
+// so the results equal two slab_sorted calls and each packed instruction
+// does the work of two issued ones.  i* = (inv, inv), o* = (-oi, -oi).
+__device__ __forceinline__ void slab_sorted2(float2 nx, float2 fx, float2 ny, float2 fy, float2 nz, float2 fz,
+                                             float2 ix, float2 iy, float2 iz, float2 ox, float2 oy, float2 oz,
+                                             bool &ha, bool &hb) {
+    const float2 tnx = __ffma2_rn(nx, ix, ox), tfx = __ffma2_rn(fx, ix, ox);
+    const float2 tny = __ffma2_rn(ny, iy, oy), tfy = __ffma2_rn(fy, iy, oy);
+    const float2 tnz = __ffma2_rn(nz, iz, oz), tfz = __ffma2_rn(fz, iz, oz);
+    const float na = fmaxf(fmaxf(tnx.x, tny.x), fmaxf(tnz.x, 0.0f));
+    const float fa = fminf(fminf(tfx.x, tfy.x), tfz.x);
+    const float nb = fmaxf(fmaxf(tnx.y, tny.y), fmaxf(tnz.y, 0.0f));
+    const float fb = fminf(fminf(tfx.y, tfy.y), tfz.y);
+    ha = na <= fmaf(fabsf(fa), 1e-6f, fa);
+    hb = nb <= fmaf(fabsf(fb), 1e-6f, fb);
+}
+
 // Peak response of the Gaussian at sorted position p along the ray
 // (Eq. 13-14 with Sigma^-1).  In the whitened frame u = W (x - mu) the squared
 // Mahalanobis distance along the ray is |u_o + t u_d|^2, minimised at
@@ -89,15 +135,29 @@ __device__ __forceinline__ bool slab_sorted(float nx, float fx, float ny, float 
 // ~4e-7).  Returns true if the Gaussian is accepted (t* > 0, m^2 <= K^2,
 // alpha >= alpha_min), with alpha and e.  The forward and the adjoint both use
 // this routine, so they make the same decisions.
+// two_diff of two components at once; fma(b, -1, a) rounds a - b once, as
+// a subtraction does, so the halves equal two two_diff calls.
+__device__ __forceinline__ void two_diff2(float2 a, float2 b, float2 &hi, float2 &lo) {
+    const float2 m1 = make_float2(-1.0f, -1.0f);
+    const float2 s = __ffma2_rn(b, m1, a);   // a - b
+    const float2 bb = __ffma2_rn(a, m1, s);  // s - a
+    const float2 t = __ffma2_rn(bb, m1, s);  // s - bb
+    const float2 u = __ffma2_rn(t, m1, a);   // a - (s - bb)
+    const float2 v = __fadd2_rn(b, bb);      // b + bb
+    lo = __ffma2_rn(v, m1, u);               // u - v
+    hi = s;
+}
+
 __device__ __forceinline__ bool gauss_eval(const BvhDev &b, int32_t p, float3 o, float3 d, float &alpha,
                                            float3 &e) {
     const float4 g0 = __ldg(b.gauss + 4 * p);
     const float4 g1 = __ldg(b.gauss + 4 * p + 1);
     const float4 g2 = __ldg(b.gauss + 4 * p + 2);
     const float4 g3 = __ldg(b.gauss + 4 * p + 3);
-    float hx, lx, hy, ly, hz, lz;
-    two_diff(o.x, g0.x, hx, lx);
-    two_diff(o.y, g0.y, hy, ly);
+    float2 hxy, lxy;
+    two_diff2(make_float2(o.x, o.y), make_float2(g0.x, g0.y), hxy, lxy);
+    const float hx = hxy.x, hy = hxy.y;
+    float hz, lz;
     two_diff(o.z, g0.z, hz, lz);
     const float3 w0 = make_float3(g1.x, g1.y, g1.z);
     const float3 w1 = make_float3(g2.x, g2.y, g2.z);
@@ -107,7 +167,8 @@ __device__ __forceinline__ bool gauss_eval(const BvhDev &b, int32_t p, float3 o,
     const float3 uo = make_float3(dot3(w0, dh), dot3(w1, dh), dot3(w2, dh));
     const float t = __fdividef(-dot3(uo, ud), dot3(ud, ud));
     if (!(t > 0.0f)) return false;
-    e = make_float3(fmaf(t, d.x, hx) + lx, fmaf(t, d.y, hy) + ly, fmaf(t, d.z, hz) + lz);
+    const float2 exy = __fadd2_rn(__ffma2_rn(make_float2(t, t), make_float2(d.x, d.y), hxy), lxy);
+    e = make_float3(exy.x, exy.y, fmaf(t, d.z, hz) + lz);
     const float3 u = make_float3(dot3(w0, e), dot3(w1, e), dot3(w2, e));
     const float m2 = dot3(u, u);
     if (!(m2 <= b.k2)) return false;
@@ -337,6 +398,8 @@ __device__ __forceinline__ float trace_wide(const BvhDev &b, float3 o, float3 d,
     const float3 inv = safe_inv(d);
     const float3 oi = make_float3(o.x * inv.x, o.y * inv.y, o.z * inv.z);
     const int sx = inv.x < 0.0f, sy = inv.y < 0.0f, sz = inv.z < 0.0f;
+    const float2 ix2 = make_float2(inv.x, inv.x), iy2 = make_float2(inv.y, inv.y), iz2 = make_float2(inv.z, inv.z);
+    const float2 ox2 = make_float2(-oi.x, -oi.x), oy2 = make_float2(-oi.y, -oi.y), oz2 = make_float2(-oi.z, -oi.z);
     uint32_t alive = __ballot_sync(FULL, valid);
     int sp = 0;
     uint32_t node = 0, mask = alive;
@@ -352,19 +415,23 @@ __device__ __forceinline__ float trace_wide(const BvhDev &b, float3 o, float3 d,
             const float4 nx = __ldg(w + sx), fx = __ldg(w + 1 - sx), ny = __ldg(w + 2 + sy),
                          fy = __ldg(w + 3 - sy), nz = __ldg(w + 4 + sz), fz = __ldg(w + 5 - sz);
             if (mine) {
-                h0 = slab_sorted(nx.x, fx.x, ny.x, fy.x, nz.x, fz.x, oi, inv);
-                h1 = slab_sorted(nx.y, fx.y, ny.y, fy.y, nz.y, fz.y, oi, inv);
-                h2 = slab_sorted(nx.z, fx.z, ny.z, fy.z, nz.z, fz.z, oi, inv);
-                h3 = slab_sorted(nx.w, fx.w, ny.w, fy.w, nz.w, fz.w, oi, inv);
+                slab_sorted2(make_float2(nx.x, nx.y), make_float2(fx.x, fx.y), make_float2(ny.x, ny.y),
+                             make_float2(fy.x, fy.y), make_float2(nz.x, nz.y), make_float2(fz.x, fz.y), ix2, iy2, iz2,
+                             ox2, oy2, oz2, h0, h1);
+                slab_sorted2(make_float2(nx.z, nx.w), make_float2(fx.z, fx.w), make_float2(ny.z, ny.w),
+                             make_float2(fy.z, fy.w), make_float2(nz.z, nz.w), make_float2(fz.z, fz.w), ix2, iy2, iz2,
+                             ox2, oy2, oz2, h2, h3);
             }
         } else {
             const float4 lx = __ldg(w), hx = __ldg(w + 1), ly = __ldg(w + 2), hy = __ldg(w + 3),
                          lz = __ldg(w + 4), hz = __ldg(w + 5);
             if (mine) {
-                h0 = slab(lx.x, hx.x, ly.x, hy.x, lz.x, hz.x, oi, inv);
-                h1 = slab(lx.y, hx.y, ly.y, hy.y, lz.y, hz.y, oi, inv);
-                h2 = slab(lx.z, hx.z, ly.z, hy.z, lz.z, hz.z, oi, inv);
-                h3 = slab(lx.w, hx.w, ly.w, hy.w, lz.w, hz.w, oi, inv);
+                bool h[4];
+                slab4(lx, hx, ly, hy, lz, hz, oi, inv, h);
+                h0 = h[0];
+                h1 = h[1];
+                h2 = h[2];
+                h3 = h[3];
             }
         }
         if (COUNT && mine) wc.box += (r0 != RT_EMPTY) + (r1 != RT_EMPTY) + (r2 != RT_EMPTY) + (r3 != RT_EMPTY);
@@ -447,10 +514,8 @@ __device__ __forceinline__ void trace_ray_wide_run(const BvhDev &b, float3 o, fl
                      hz = __ldg(w + 5), rf = __ldg(w + 6);
         const uint32_t r[4] = {__float_as_uint(rf.x), __float_as_uint(rf.y), __float_as_uint(rf.z),
                                __float_as_uint(rf.w)};
-        const bool h[4] = {slab(lx.x, hx.x, ly.x, hy.x, lz.x, hz.x, oi, inv),
-                           slab(lx.y, hx.y, ly.y, hy.y, lz.y, hz.y, oi, inv),
-                           slab(lx.z, hx.z, ly.z, hy.z, lz.z, hz.z, oi, inv),
-                           slab(lx.w, hx.w, ly.w, hy.w, lz.w, hz.w, oi, inv)};
+        bool h[4];
+        slab4(lx, hx, ly, hy, lz, hz, oi, inv, h);
         if (COUNT) wc.box += (r[0] != RT_EMPTY) + (r[1] != RT_EMPTY) + (r[2] != RT_EMPTY) + (r[3] != RT_EMPTY);
         int next = -1;
         bool overflow = false;
@@ -737,10 +802,8 @@ __device__ __forceinline__ void trace_refill(const BvhDev &b, const RaySetDev &r
                      hz = __ldg(w + 5), rf = __ldg(w + 6);
         const uint32_t r[4] = {__float_as_uint(rf.x), __float_as_uint(rf.y), __float_as_uint(rf.z),
                                __float_as_uint(rf.w)};
-        const bool h[4] = {slab(lx.x, hx.x, ly.x, hy.x, lz.x, hz.x, oi, inv),
-                           slab(lx.y, hx.y, ly.y, hy.y, lz.y, hz.y, oi, inv),
-                           slab(lx.z, hx.z, ly.z, hy.z, lz.z, hz.z, oi, inv),
-                           slab(lx.w, hx.w, ly.w, hy.w, lz.w, hz.w, oi, inv)};
+        bool h[4];
+        slab4(lx, hx, ly, hy, lz, hz, oi, inv, h);
         if (COUNT) wc.box += (r[0] != RT_EMPTY) + (r[1] != RT_EMPTY) + (r[2] != RT_EMPTY) + (r[3] != RT_EMPTY);
         int next = -1;
         bool overflow = false;
@@ -831,10 +894,8 @@ __device__ __forceinline__ float trace_warp_ray(const BvhDev &b, float3 o, float
                          lz = __ldg(w + 4), hz = __ldg(w + 5), rf = __ldg(w + 6);
             const uint32_t r[4] = {__float_as_uint(rf.x), __float_as_uint(rf.y), __float_as_uint(rf.z),
                                    __float_as_uint(rf.w)};
-            const bool h[4] = {slab(lx.x, hx.x, ly.x, hy.x, lz.x, hz.x, oi, inv),
-                               slab(lx.y, hx.y, ly.y, hy.y, lz.y, hz.y, oi, inv),
-                               slab(lx.z, hx.z, ly.z, hy.z, lz.z, hz.z, oi, inv),
-                               slab(lx.w, hx.w, ly.w, hy.w, lz.w, hz.w, oi, inv)};
+            bool h[4];
+            slab4(lx, hx, ly, hy, lz, hz, oi, inv, h);
             if (COUNT) wc.box += (r[0] != RT_EMPTY) + (r[1] != RT_EMPTY) + (r[2] != RT_EMPTY) + (r[3] != RT_EMPTY);
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
