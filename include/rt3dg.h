@@ -187,7 +187,8 @@ typedef enum {
  * branchless construction of Duff et al. 2017 (rt_materialize_rays gives the
  * exact float32 rays), origin and exclusion as for DIRS.
  * If ray_ids (device int64[n_ids]) is set for DIRS/ENV/HEMI, only those ray
- * ids are traced and outputs are indexed by position in ray_ids. */
+ * ids are traced and outputs are indexed by position in ray_ids (a non-NULL
+ * ray_ids with n_ids = 0 is the empty subset; NULL means every ray). */
 typedef struct {
     int32_t kind;
     int32_t n_dirs;

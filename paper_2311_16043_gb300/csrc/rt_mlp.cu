@@ -981,7 +981,11 @@ extern "C" rt_status rt_surrogate_infer(const rt_surrogate *s, const rt_bvh *bvh
     RaySetDev rs;
     int64_t m = 0;
     RT_TRY(rt_rayset_dev(bvh, rays, &rs, &m));
-    if (m == 0) return RT_OK;
+    if (m == 0) {
+        if (n_fallback && cudaMemsetAsync(n_fallback, 0, sizeof(int64_t), (cudaStream_t)stream) != cudaSuccess)
+            return RT_ERR_CUDA;
+        return RT_OK;
+    }
     if (!T_out) return RT_ERR_INVALID_ARG;
     RT_TRY(set_smem_attrs());
     cudaStream_t st = (cudaStream_t)stream;
@@ -1093,7 +1097,11 @@ extern "C" rt_status rt_surrogate_infer_noalloc(const rt_surrogate *s, const rt_
     int64_t m = 0;
     RT_TRY(rt_rayset_dev(bvh, rays, &rs, &m));
     if (m > kNoAllocMaxRays) return RT_ERR_INVALID_ARG;  // beyond the fixed scratch capacity
-    if (m == 0) return RT_OK;
+    if (m == 0) {
+        if (n_fallback && cudaMemsetAsync(n_fallback, 0, sizeof(int64_t), (cudaStream_t)stream) != cudaSuccess)
+            return RT_ERR_CUDA;
+        return RT_OK;
+    }
     if (!T_out) return RT_ERR_INVALID_ARG;
     int64_t *scratch = nullptr;
     RT_TRY(noalloc_scratch(&scratch));

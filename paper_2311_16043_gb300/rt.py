@@ -308,8 +308,20 @@ def rayspec(kind=RT_RAYS_DIRS, *, dirs=None, ray_o=None, ray_d=None, ray_src=Non
     if ray_ids is not None:
         rs.ray_ids = _ptr(ray_ids, torch.int64, "ray_ids")
         rs.n_ids = ray_ids.numel()
+        if rs.n_ids == 0:  # an empty subset: a non-null list of length 0 (null means every ray)
+            rs.ray_ids = _empty_list_ptr()
     rs._keep = (dirs, ray_o, ray_d, ray_src, env, ray_ids, normals)  # keep the tensors alive
     return rs
+
+
+_EMPTY_LIST = None
+
+
+def _empty_list_ptr():
+    global _EMPTY_LIST
+    if _EMPTY_LIST is None:
+        _EMPTY_LIST = torch.zeros(1, dtype=torch.int64, device="cuda")
+    return _EMPTY_LIST.data_ptr()
 
 
 def rt_rayspec_count(bvh: Bvh, rs: rt_rayspec) -> int:

@@ -388,3 +388,32 @@ def test_bench_workload_sampled(orc):
     maxerr, excluded = compare(T[sel], ref, max_excluded=0.06)
     print(f"2M scene: max |dT| {maxerr:.2e} over {512 - excluded} rays, {excluded} in a rounding band")
     assert np.all((T >= 0) & (T <= 1))
+
+
+def test_empty_ray_sets():
+    """Zero rays in every form (explicit, id list, surrogate batch, PBR and AO
+    over an empty scene) with every traversal: nothing written, no error."""
+    from paper_2311_16043_gb300 import rt
+    sc = scenes.uniform_scene(500, 2)
+    bvh = build(sc)
+    dirs = _dev(scenes.fibonacci_sphere(8))
+    empty_f = torch.empty((0, 3), dtype=torch.float32, device="cuda")
+    empty_i = torch.empty(0, dtype=torch.int64, device="cuda")
+    for kernel in range(7):
+        T = rt.rt_trace_visibility(bvh, rt.rayspec(rt.RT_RAYS_EXPLICIT, ray_o=empty_f, ray_d=empty_f),
+                                   opts=rt.trace_opts(kernel=kernel))
+        assert T.numel() == 0
+        T = rt.rt_trace_visibility(bvh, rt.rayspec(rt.RT_RAYS_DIRS, dirs=dirs, ray_ids=empty_i),
+                                   opts=rt.trace_opts(kernel=kernel))
+        assert T.numel() == 0
+    s = rt.rt_surrogate_create(rt.mlp_cfg(batch=1024), seed=1)
+    nfb = torch.full((1,), 7, dtype=torch.int64, device="cuda")
+    p = rt.rt_surrogate_infer(s, bvh, rt.rayspec(rt.RT_RAYS_DIRS, dirs=dirs, ray_ids=empty_i), band=0.3,
+                              n_fallback=nfb)
+    assert p.numel() == 0 and int(nfb.item()) == 0
+    none = {k: v[:0] for k, v in sc.items()}
+    b0 = build(none)
+    assert rt.rt_trace_visibility_dirs(b0, dirs).numel() == 0
+    assert rt.rt_trace_ao(b0, rt.rayspec(rt.RT_RAYS_DIRS, dirs=dirs)).numel() == 0
+    torch.cuda.synchronize()
+    assert rt.rt_status_last() == 0
