@@ -262,6 +262,25 @@ rt_status rt_trace_visibility(const rt_bvh *bvh, const rt_rayspec *rays, float *
 rt_status rt_trace_visibility_dirs(const rt_bvh *bvh, const float *dirs, int32_t k, float *T_out,
                                    const rt_trace_opts *opts, rt_stream_t stream);
 
+/* The whole visibility precompute from host memory in one call (Sec. 4.2:
+ * every Gaussian's visibility along the K directions): copies mean[n*3],
+ * scale[n*3], quat[n*4], opacity[n] and dirs[k*3] (host float32, the layouts
+ * of rt_build_bvh and rt_trace_visibility_dirs) to the device, builds the
+ * tree, traces the n*k rays into a device table and copies it to
+ * T_host[n*k] (row-major [n, k], caller's Gaussian order).  Device buffers
+ * come from the library's allocator (rt_set_allocator) and are released in
+ * stream order.  Host buffers should be page-locked for the copies to run
+ * asynchronously (pageable memory is staged by CUDA).  Synchronises `stream`
+ * once, inside the build; T_host holds the result once `stream` has been
+ * synchronised.  n = 0 or k = 0 writes nothing.  Errors: those of
+ * rt_build_bvh and rt_trace_visibility_dirs; RT_ERR_INVALID_ARG (NULL arrays
+ * with n*k > 0, k < 0, n*k >= 2^40), RT_ERR_OOM, RT_ERR_CUDA (a copy could
+ * not be enqueued). */
+rt_status rt_visibility_dirs_host(const float *mean, const float *scale, const float *quat,
+                                  const float *opacity, int64_t n, const float *dirs, int32_t k,
+                                  const rt_params *params, const rt_trace_opts *opts, float *T_host,
+                                  rt_stream_t stream);
+
 /* ------------------------------------------------------------------------ */
 /* Composed scenes: a two-level BVH over object instances (Sec. 4.3)         */
 /* ------------------------------------------------------------------------ */

@@ -276,6 +276,59 @@ extern "C" rt_status rt_trace_visibility_dirs(const rt_bvh *bvh, const float *di
 }
 
 // ---------------------------------------------------------------------------
+// The precompute from host buffers: copies in, build, trace, copy out, all on
+// one stream.
+// ---------------------------------------------------------------------------
+extern "C" rt_status rt_visibility_dirs_host(const float *mean, const float *scale, const float *quat,
+                                             const float *opacity, int64_t n, const float *dirs, int32_t k,
+                                             const rt_params *params, const rt_trace_opts *opts, float *T_host,
+                                             rt_stream_t stream) {
+    if (n < 0 || k < 0 || n >= (int64_t(1) << 31)) return RT_ERR_INVALID_ARG;
+    const int64_t R = n * (int64_t)k;
+    if (R == 0) return RT_OK;
+    if (R >= (int64_t(1) << 40) || !mean || !scale || !quat || !opacity || !dirs || !T_host)
+        return RT_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t b3 = up(size_t(n) * 12), b4 = up(size_t(n) * 16), b1 = up(size_t(n) * 4), bd = up(size_t(k) * 12);
+    void *blk = nullptr;
+    rt_status s = rt_alloc(&blk, 2 * b3 + b4 + b1 + bd, stream);
+    if (s != RT_OK) return s;
+    char *base = (char *)blk;
+    float *d_mean = (float *)base, *d_scale = (float *)(base + b3), *d_quat = (float *)(base + 2 * b3),
+          *d_opac = (float *)(base + 2 * b3 + b4), *d_dirs = (float *)(base + 2 * b3 + b4 + b1);
+    const struct { void *dst; const void *src; size_t bytes; } in[5] = {
+        {d_mean, mean, size_t(n) * 12}, {d_scale, scale, size_t(n) * 12}, {d_quat, quat, size_t(n) * 16},
+        {d_opac, opacity, size_t(n) * 4}, {d_dirs, dirs, size_t(k) * 12}};
+    for (const auto &c : in) {
+        if (cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+            cudaGetLastError();
+            rt_free(blk, stream);
+            return RT_ERR_CUDA;
+        }
+    }
+    rt_bvh *bvh = nullptr;
+    s = rt_build_bvh(d_mean, d_scale, d_quat, d_opac, n, params, stream, &bvh);
+    if (s != RT_OK) {
+        rt_free(blk, stream);
+        return s;
+    }
+    float *d_T = nullptr;
+    s = rt_alloc((void **)&d_T, size_t(R) * 4, stream);
+    if (s == RT_OK) {
+        s = rt_trace_visibility_dirs(bvh, d_dirs, k, d_T, opts, stream);
+        if (s == RT_OK && cudaMemcpyAsync(T_host, d_T, size_t(R) * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+            cudaGetLastError();
+            s = RT_ERR_CUDA;
+        }
+        rt_free(d_T, stream);
+    }
+    rt_bvh_destroy(bvh, stream);
+    rt_free(blk, stream);
+    return s;
+}
+
+// ---------------------------------------------------------------------------
 // Materialised rays of an implicit set (for inspection and the adjoint)
 // ---------------------------------------------------------------------------
 namespace {

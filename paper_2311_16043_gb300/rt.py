@@ -100,6 +100,7 @@ _SIGS = {
     "rt_materialize_rays": (_I32, [_P, _P, _P, _I64, _P, _P, _P, _P]),
     "rt_trace_visibility": (_I32, [_P, _P, _P, _P, _P]),
     "rt_trace_visibility_dirs": (_I32, [_P, _P, _I32, _P, _P, _P]),
+    "rt_visibility_dirs_host": (_I32, [_P, _P, _P, _P, _I64, _P, _I32, _P, _P, _P, _P]),
     "rt_trace_visibility_backward": (_I32, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I32,
                                             _P, _P, _P, _P, _P, _P]),
     "rt_mlp_cfg_default": (None, [_P]),
@@ -364,6 +365,42 @@ def rt_trace_visibility_dirs(bvh: Bvh, dirs, T_out=None, opts: rt_trace_opts | N
                                           C.byref(opts) if opts is not None else None, _stream(stream)),
            "rt_trace_visibility_dirs")
     return T_out
+
+
+def _host_ptr(t, dtype, name):
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError(f"{name} must be a host (CPU) tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr() if t.numel() > 0 else None
+
+
+def rt_visibility_dirs_host(mean, scale, quat, opacity, dirs, T_host=None, prm: rt_params | None = None,
+                            opts: rt_trace_opts | None = None, stream=None):
+    """The whole precompute from host tensors (pin them for asynchronous
+    copies): build + trace of every (Gaussian, direction) ray, T copied back
+    to T_host [n, K].  Valid once the stream is synchronised."""
+    n = mean.shape[0] if mean.dim() > 0 else 0
+    for t, w, nm in ((mean, 3, "mean"), (scale, 3, "scale"), (quat, 4, "quat"), (opacity, 1, "opacity")):
+        if t.numel() != n * w:
+            raise ValueError(f"{nm} must have {w} values per Gaussian")
+    K = dirs.shape[0]
+    if T_host is None:
+        T_host = torch.empty((n, K), dtype=torch.float32, pin_memory=torch.cuda.is_available())
+    elif T_host.numel() != n * K:
+        raise ValueError("T_host must have n*K elements")
+    prm = prm or params()
+    _check(lib().rt_visibility_dirs_host(_host_ptr(mean, torch.float32, "mean"),
+                                         _host_ptr(scale, torch.float32, "scale"),
+                                         _host_ptr(quat, torch.float32, "quat"),
+                                         _host_ptr(opacity, torch.float32, "opacity"), n,
+                                         _host_ptr(dirs, torch.float32, "dirs"), K, C.byref(prm),
+                                         C.byref(opts) if opts is not None else None,
+                                         _host_ptr(T_host, torch.float32, "T_host"), _stream(stream)),
+           "rt_visibility_dirs_host")
+    return T_host
 
 
 def pbr_inputs(albedo, roughness, env, cam, sh=None, kernel=RT_KERNEL_AUTO) -> rt_pbr_inputs:

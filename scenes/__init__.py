@@ -24,6 +24,8 @@ Workload recipes (Sec. 4.2 visibility precompute, Sec. 5.1 N_s directions):
   batch_scenes    -- 16 uniform scenes of uneven size (log-uniform counts).
   envmap          -- 64x32 equirectangular log-normal radiance map (sigma 1.5)
                      and its pixel-corner direction table.
+  composed_objects -- 4 object-scale scenes (125k each) placed as 16 instances
+                     by seeded rigid maps (Sec. 4.3 composition).
 """
 from __future__ import annotations
 
@@ -34,6 +36,8 @@ import numpy as np
 __all__ = [
     "fibonacci_sphere", "rotated_fibonacci", "uniform_scene", "object_scene",
     "batch_scene_sizes", "batch_scenes", "envmap", "loss_weights", "sample_ray_ids",
+    "batch_object_scenes", "composed_objects", "fibonacci_hemisphere", "shortest_axis_normals",
+    "pbr_material", "light_envmap",
 ]
 
 
@@ -279,6 +283,21 @@ def batch_object_scenes(sizes, seed_base: int = 300) -> list[dict]:
         sc["mean"] = _f32(sc["mean"].astype(np.float64) + off)
         out.append(sc)
     return out
+
+
+def composed_objects(seed: int = 60, n_obj: int = 4, n_inst: int = 16, per_obj: int = 125_000):
+    """Objects (``object_scene``, seeds seed..seed+n_obj-1) and n_inst seeded
+    rigid maps [R | t] (float32 3x4): R uniform over rotations, t U[-3,3]^3,
+    so instances overlap.  Instance j places object j mod n_obj.  Returns
+    (objects, pick, xforms)."""
+    from scipy.spatial.transform import Rotation
+    objs = [object_scene(per_obj, seed + i) for i in range(n_obj)]
+    rng = np.random.default_rng(3)
+    xf = []
+    for _ in range(n_inst):
+        R = Rotation.random(random_state=int(rng.integers(1 << 30))).as_matrix()
+        xf.append(np.concatenate([R, rng.uniform(-3, 3, (3, 1))], 1).astype(np.float32))
+    return objs, [i % n_obj for i in range(n_inst)], xf
 
 
 def envmap(seed: int = 399, h: int = 32, w: int = 64, sigma: float = 1.5) -> dict:

@@ -1,7 +1,7 @@
 """GPU checks of the boundary's host-facing contracts: the caller's
-allocator (torch's caching allocator through rt_set_allocator) and the
-device check of Gaussian inputs (synchronous error from the build, status
-word from the refit)."""
+allocator (torch's caching allocator through rt_set_allocator), the device
+check of Gaussian inputs (synchronous error from the build, status word from
+the refit) and the one-call precompute from host buffers."""
 import numpy as np
 import pytest
 import torch
@@ -84,3 +84,52 @@ def test_refit_reports_bad_inputs_through_the_status_word():
     rt.rt_bvh_refit(bvh, d["mean"], d["scale"], d["quat"], d["opacity"])
     torch.cuda.synchronize()
     assert rt.rt_status_last() == 0
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_precompute_from_host_buffers(pinned):
+    """rt_visibility_dirs_host (copies in, build, trace, copy out) gives the
+    device path's table bit for bit, from page-locked or pageable memory,
+    with the library's pool and with the caller's allocator."""
+    from paper_2311_16043_gb300 import rt
+    sc = scenes.object_scene(30_000, 4)
+    dirs_np = scenes.fibonacci_sphere(32)
+    d = _dev(sc)
+    bvh = rt.rt_build_bvh(d["mean"], d["scale"], d["quat"], d["opacity"])
+    ref = rt.rt_trace_visibility_dirs(bvh, torch.from_numpy(dirs_np).cuda()).cpu()
+    bvh.destroy()
+    host = {k: torch.from_numpy(np.ascontiguousarray(v)) for k, v in sc.items()}
+    hdirs = torch.from_numpy(dirs_np)
+    if pinned:
+        host = {k: v.pin_memory() for k, v in host.items()}
+        hdirs = hdirs.pin_memory()
+    for torch_alloc in (False, True):
+        rt.use_torch_allocator(torch_alloc)
+        try:
+            hT = torch.full((30_000, 32), -1.0, pin_memory=pinned)
+            out = rt.rt_visibility_dirs_host(host["mean"], host["scale"], host["quat"], host["opacity"], hdirs, hT)
+            torch.cuda.synchronize()
+        finally:
+            rt.use_torch_allocator(False)
+        assert out is hT
+        assert rt.rt_status_last() == 0
+        assert torch.equal(hT, ref)
+
+
+def test_precompute_from_host_buffers_edges():
+    from paper_2311_16043_gb300 import rt
+    sc = {k: torch.from_numpy(np.ascontiguousarray(v)) for k, v in scenes.uniform_scene(200, 5).items()}
+    dirs = torch.from_numpy(scenes.fibonacci_sphere(4))
+    empty = {k: v[:0] for k, v in sc.items()}
+    T = rt.rt_visibility_dirs_host(empty["mean"], empty["scale"], empty["quat"], empty["opacity"], dirs)
+    assert T.shape == (0, 4)
+    T = rt.rt_visibility_dirs_host(sc["mean"], sc["scale"], sc["quat"], sc["opacity"], dirs[:0])
+    assert T.shape == (200, 0)
+    with pytest.raises(TypeError):  # device tensors are not host buffers
+        rt.rt_visibility_dirs_host(sc["mean"].cuda(), sc["scale"], sc["quat"], sc["opacity"], dirs)
+    bad = sc["scale"].clone()
+    bad[7, 1] = 0.0
+    with pytest.raises(rt.RTError):  # the build's input check
+        rt.rt_visibility_dirs_host(sc["mean"], bad, sc["quat"], sc["opacity"], dirs)
+    torch.cuda.synchronize()
+    rt.rt_status_clear()
