@@ -81,19 +81,28 @@ def parse():
     ap.add_argument("--no-refit", action="store_true")
     ap.add_argument("--surrogate-steps", type=int, default=2000)
     ap.add_argument("--band", type=float, default=0.3)
-    return ap.parse_args()
+    ap.add_argument("--gaussians", type=int, default=0,
+                    help="override the workload's Gaussian count (a small case of the same kernels, for "
+                         "profiling); the JSON line reports the count used")
+    args = ap.parse_args()
+    if args.gaussians > 0:
+        gen, _, seed, K = WORKLOADS[args.workload]
+        WORKLOADS[args.workload] = (gen, args.gaussians, seed, K)
+    return args
 
 
 def make_scene(name):
     import scenes
     gen, n, seed, K = WORKLOADS[name]
     if gen == "composed":  # the reference arm samples rays of one object
-        return scenes.object_scene(125_000, seed), scenes.fibonacci_sphere(K)
-    if gen == "batch":
-        return scenes.batch_scenes(scenes.batch_scene_sizes(16, n, seed), seed_base=seed), scenes.fibonacci_sphere(K)
-    if gen == "batch_objects":
-        return (scenes.batch_object_scenes(scenes.batch_scene_sizes(16, n, seed), seed_base=seed),
-                scenes.fibonacci_sphere(K))
+        return scenes.object_scene(n // 16, seed), scenes.fibonacci_sphere(K)
+    if gen.startswith("batch"):
+        # sizes log-uniform in [50k, 2M] for the 8M-Gaussian workload; a smaller
+        # total (--gaussians) scales the range with it
+        f = n / 8_000_000
+        sizes = scenes.batch_scene_sizes(16, n, seed, lo=max(1000, int(50_000 * f)), hi=max(1000, int(2_000_000 * f)))
+        gen_scenes = scenes.batch_scenes if gen == "batch" else scenes.batch_object_scenes
+        return gen_scenes(sizes, seed_base=seed), scenes.fibonacci_sphere(K)
     sc = scenes.object_scene(n, seed) if gen == "object" else scenes.uniform_scene(n, seed)
     return sc, scenes.fibonacci_sphere(K)
 
@@ -541,7 +550,7 @@ def run_composed(args, rank, world, local, torch, dist, rt):
     128 directions through all instances."""
     import scenes
     dev = torch.device("cuda", local)
-    objs, pick, xf = scenes.composed_objects()
+    objs, pick, xf = scenes.composed_objects(per_obj=WORKLOADS[args.workload][1] // 16)
     bvhs = []
     for sc in objs:
         d = {k: torch.from_numpy(v).to(dev) for k, v in sc.items()}

@@ -180,7 +180,10 @@ __device__ __forceinline__ void batch_refill(const BatchJobDev *__restrict__ job
 // Jobs [0, n_item_jobs) are consumed as 32-ray items (work[0]); jobs
 // [n_item_jobs, n_jobs) as per-ray slots with lane refill (work[1]), after a
 // warp finds the item queue empty.
-__global__ void __launch_bounds__(128) k_trace_batch(const BatchJobDev *__restrict__ jobs, int n_item_jobs, int n_jobs,
+#ifndef RT_BATCH_MIN_BLOCKS
+#define RT_BATCH_MIN_BLOCKS 8
+#endif
+__global__ void __launch_bounds__(128, RT_BATCH_MIN_BLOCKS) k_trace_batch(const BatchJobDev *__restrict__ jobs, int n_item_jobs, int n_jobs,
                                                      int64_t total_items, int64_t total_slots, int *status,
                                                      unsigned long long *work) {
     const unsigned FULL = 0xffffffffu;

@@ -60,7 +60,10 @@ __device__ __forceinline__ bool top_slab(const float *bx, float3 oi, float3 inv)
     return slab(bx[0], bx[3], bx[1], bx[4], bx[2], bx[5], oi, inv);
 }
 
-__global__ void __launch_bounds__(128) k_scene_trace(const InstDev *__restrict__ inst, int n_inst,
+#ifndef RT_SCENE_MIN_BLOCKS
+#define RT_SCENE_MIN_BLOCKS 8
+#endif
+__global__ void __launch_bounds__(128, RT_SCENE_MIN_BLOCKS) k_scene_trace(const InstDev *__restrict__ inst, int n_inst,
                                                      const TopNode *__restrict__ top, uint32_t root_ref,
                                                      const float *__restrict__ root_box, const float *__restrict__ dirs,
                                                      int32_t K, float eps, float t_min, int64_t total_items,
