@@ -237,7 +237,7 @@ typedef enum {
 typedef struct {
     int32_t kernel;      /* rt_kernel                                          */
     int32_t order_block; /* PACKET: tiles of 32 Gaussians per direction sweep
-                            (0 = default)                                      */
+                            (0 = default, 1: a tile's directions in turn)      */
     int32_t block_threads; /* threads per block (0 = default)                  */
     int32_t hit_cap;     /* capacity per ray of hit_ids                        */
     int64_t *counters;   /* device int64[4] accumulated (not reset): box tests,

@@ -56,7 +56,7 @@ TraceJob full_job(const rt_bvh *bvh, int32_t K, int32_t order_block) {
     memset(&job, 0, sizeof(job));
     job.mode = MODE_FULL;
     job.n_tiles = (bvh->n + 31) / 32;
-    int64_t B = order_block > 0 ? order_block : 64;
+    int64_t B = order_block > 0 ? order_block : 1;
     if (B > job.n_tiles) B = job.n_tiles;
     if (B < 1) B = 1;
     job.order_block = (int32_t)B;
@@ -370,7 +370,7 @@ extern "C" rt_status rt_batch_create(const rt_batch_job *jobs, int32_t n_jobs, i
         rt_trace_opts o;
         memset(&o, 0, sizeof(o));
         o.kernel = default_kernel(J.bvh, J.rays.kind);
-        o.order_block = 64;
+        o.order_block = 1;
         if (autotune && count > 0) {
             r = rt_trace_autotune(J.bvh, &J.rays, J.T_out, &o, stream);
             if (r != RT_OK) {

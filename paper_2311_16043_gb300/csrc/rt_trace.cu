@@ -5,10 +5,12 @@
 // directions) an item is 32 Gaussians adjacent in Morton order x one
 // direction, so the warp's rays are nearly parallel and start close together.
 // Items are ordered in sweeps: `order_block` tiles for direction 0, the same
-// tiles for direction 1, ... so that the rows T[g, 0..K) of a tile are written
-// within a short window (whole sectors merge in L2) while neighbouring warps
-// still trace parallel rays.  Explicit ray lists and id subsets are taken in
-// chunks of 32 in the given order.
+// tiles for direction 1, ... .  The default, one tile per sweep, hands out a
+// tile's K directions in turn: the rows T[g, 0..K) of a tile are written
+// within a short window (whole sectors merge in L2) and the warps in flight
+// start in the same region of the tree (sweeps of 64 to 62,500 tiles measured
+// 0.6-2 % slower on the 2M-Gaussian object scene).  Explicit ray lists and id
+// subsets are taken in chunks of 32 in the given order.
 #include <string.h>
 
 #include "rt_trace_core.cuh"
@@ -156,7 +158,7 @@ rt_status rt_trace_launch(const rt_bvh *bvh, const rt_rayspec *rays, float *T_ou
     else job.mode = MODE_FULL;
     if (job.mode == MODE_FULL) {
         job.n_tiles = (bvh->n + 31) / 32;
-        int64_t B = o.order_block > 0 ? o.order_block : 64;
+        int64_t B = o.order_block > 0 ? o.order_block : 1;
         if (B > job.n_tiles) B = job.n_tiles;
         job.order_block = (int32_t)B;
         job.n_items = job.n_tiles * rs.K;
