@@ -726,10 +726,19 @@ def main():
             if i >= args.warmup:
                 e_ms.append(e0.elapsed_time(e1))
         e_clk = e_clocks.stop()
+        # this machine's host link, for reading the gap between e2e and value:
+        # one plain copy of the T table to the same page-locked buffer
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record()
+        hT.copy_(T, non_blocking=True)
+        c1.record()
+        torch.cuda.synchronize()
+        d2h_probe_ms = c0.elapsed_time(c1)
         em = reduce_max(statistics.mean(e_ms), world, dev)
         e2e = {"value": replica_rate(R, em, world), "unit": "rays/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": em,
-               "call": "rt_visibility_dirs_host (C ABI) from page-locked host buffers", "clocks": e_clk}
+               "call": "rt_visibility_dirs_host (C ABI) from page-locked host buffers", "clocks": e_clk,
+               "d2h_copy_probe": {"ms": d2h_probe_ms, "gbs": d2h / d2h_probe_ms / 1e6}}
 
     surrogate = None
     if not args.no_surrogate and rank == 0:
