@@ -134,8 +134,10 @@ rt_status rt_bvh_export(const rt_bvh *bvh, uint64_t *keys, int32_t *left, int32_
  * failure; the block must be 256-byte aligned), free releases a block in
  * stream order.  With an allocator set, every device allocation the library
  * makes — handles' buffers and per-call scratch — goes through it (e.g. a
- * framework's caching allocator); NULL restores the default (cudaMallocAsync
- * / cudaFreeAsync on the call's stream).  Process-wide: set it while no
+ * framework's caching allocator); NULL restores the default: the library's
+ * own stream-ordered pool on the call's device (cudaMallocFromPoolAsync /
+ * cudaFreeAsync on the call's stream), which keeps freed blocks mapped for
+ * reuse until rt_memory_trim.  Process-wide: set it while no
  * handle exists, since a handle returns its buffers through the allocator in
  * force when it is destroyed.  rt_surrogate_infer_noalloc allocates nothing
  * either way.  Errors: RT_ERR_INVALID_ARG (alloc or free missing). */
@@ -145,6 +147,11 @@ typedef struct {
     void *ctx;
 } rt_allocator;
 rt_status rt_set_allocator(const rt_allocator *a);
+/* Returns the library pool's unused blocks to the driver on every device,
+ * keeping at most keep_bytes reserved per device (0 = all).  Call after
+ * synchronising the streams that freed them.  Errors: RT_ERR_INVALID_ARG
+ * (keep_bytes < 0), RT_ERR_CUDA. */
+rt_status rt_memory_trim(int64_t keep_bytes);
 
 /* ------------------------------------------------------------------------ */
 /* Ray sets                                                                   */

@@ -4,6 +4,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "rt_internal.cuh"
 
 static __device__ int g_rt_status = 0;
@@ -68,7 +70,52 @@ rt_status rt_check_launch() {
 }
 
 namespace {
-rt_allocator g_alloc = {nullptr, nullptr, nullptr};  // alloc == null: stream-ordered CUDA pool
+rt_allocator g_alloc = {nullptr, nullptr, nullptr};  // alloc == null: the library's pool
+
+// The library's own stream-ordered pool per device.  Its release threshold is
+// unbounded, so blocks freed in stream order stay mapped for the next call
+// (the device's default pool would hand them back to the driver at every
+// synchronisation and remap them on the next allocation); rt_memory_trim
+// returns them.
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kMaxDevices] = {};
+
+cudaMemPool_t pool_for_current_device() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> g(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        uint64_t keep = ~uint64_t(0);
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        g_pool[dev] = pool;
+    }
+    return g_pool[dev];
+}
+}  // namespace
+
+extern "C" rt_status rt_memory_trim(int64_t keep_bytes) {
+    if (keep_bytes < 0) return RT_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> g(g_pool_mu);
+    for (int d = 0; d < kMaxDevices; ++d)
+        if (g_pool[d] && cudaMemPoolTrimTo(g_pool[d], (size_t)keep_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return RT_ERR_CUDA;
+        }
+    return RT_OK;
 }
 
 extern "C" rt_status rt_set_allocator(const rt_allocator *a) {
@@ -90,7 +137,9 @@ rt_status rt_alloc(void **p, size_t bytes, rt_stream_t s) {
         }
         return RT_OK;
     }
-    cudaError_t e = cudaMallocAsync(p, bytes, (cudaStream_t)s);
+    cudaMemPool_t pool = pool_for_current_device();
+    cudaError_t e = pool ? cudaMallocFromPoolAsync(p, bytes, pool, (cudaStream_t)s)
+                         : cudaMallocAsync(p, bytes, (cudaStream_t)s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;

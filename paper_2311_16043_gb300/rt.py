@@ -101,6 +101,7 @@ _SIGS = {
     "rt_trace_visibility": (_I32, [_P, _P, _P, _P, _P]),
     "rt_trace_visibility_dirs": (_I32, [_P, _P, _I32, _P, _P, _P]),
     "rt_visibility_dirs_host": (_I32, [_P, _P, _P, _P, _I64, _P, _I32, _P, _P, _P, _P]),
+    "rt_memory_trim": (_I32, [_I64]),
     "rt_trace_visibility_backward": (_I32, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I32,
                                             _P, _P, _P, _P, _P, _P]),
     "rt_mlp_cfg_default": (None, [_P]),
@@ -440,6 +441,11 @@ def rt_trace_ao(bvh: Bvh, rs: rt_rayspec, ao=None, opts: rt_trace_opts | None = 
 
 
 _ALLOCATOR = None  # keeps the ctypes callbacks alive while installed
+
+
+def rt_memory_trim(keep_bytes: int = 0) -> None:
+    """Return the library pool's unused device memory to the driver."""
+    _check(lib().rt_memory_trim(int(keep_bytes)), "rt_memory_trim")
 
 
 def use_torch_allocator(on: bool = True) -> None:

@@ -133,3 +133,22 @@ def test_precompute_from_host_buffers_edges():
         rt.rt_visibility_dirs_host(sc["mean"], bad, sc["quat"], sc["opacity"], dirs)
     torch.cuda.synchronize()
     rt.rt_status_clear()
+
+
+def test_pool_keeps_blocks_until_trimmed():
+    """The library's pool keeps freed blocks mapped across calls (no driver
+    remapping per call); rt_memory_trim hands them back."""
+    from paper_2311_16043_gb300 import rt
+    sc = {k: torch.from_numpy(np.ascontiguousarray(v)) for k, v in scenes.uniform_scene(200_000, 6).items()}
+    dirs = torch.from_numpy(scenes.fibonacci_sphere(32))
+    T = rt.rt_visibility_dirs_host(sc["mean"], sc["scale"], sc["quat"], sc["opacity"], dirs)
+    torch.cuda.synchronize()
+    held = torch.cuda.mem_get_info()[0]
+    rt.rt_memory_trim(0)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] > held  # the T scratch (25.6 MB) and tree came back
+    T2 = rt.rt_visibility_dirs_host(sc["mean"], sc["scale"], sc["quat"], sc["opacity"], dirs)
+    torch.cuda.synchronize()
+    assert rt.rt_status_last() == 0 and torch.equal(T, T2)
+    with pytest.raises(rt.RTError):
+        rt.rt_memory_trim(-1)
