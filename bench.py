@@ -421,7 +421,8 @@ def run_adjoint(rt, torch, dev):
     """Differentiation workload: L = sum_r w_r T_r over the rays of the first
     1,024 Gaussians of a 4,096-Gaussian uniform scene x 16 directions, and
     over all 4,096 x 32; forward + hand-written adjoint, with the hit log
-    replayed and with re-traversal; hit-log memory."""
+    replayed and with re-traversal, and with the hit log and deterministic
+    (fixed-point) accumulation; hit-log memory."""
     import scenes
     out = []
     for n_sub, K in ((1024, 16), (4096, 32)):
@@ -432,18 +433,21 @@ def run_adjoint(rt, torch, dev):
         w = torch.from_numpy(scenes.loss_weights(R, 41)).to(dev)
         prm = rt.params(t_min=0.0)
         bvh = rt.rt_build_bvh(d["mean"], d["scale"], d["quat"], d["opacity"], prm)
+        bvh_det = rt.rt_build_bvh(d["mean"], d["scale"], d["quat"], d["opacity"], rt.params(t_min=0.0,
+                                                                                             deterministic=True))
         rs = rt.rayspec(rt.RT_RAYS_DIRS, dirs=dirs)
         cap = 64
         ids = torch.empty((R, cap), dtype=torch.int32, device=dev)
         cnt = torch.empty(R, dtype=torch.int32, device=dev)
         res = {"gaussians": n_sub, "directions": K, "rays": R}
-        for mode in ("log", "recompute"):
+        for mode in ("log", "recompute", "log_deterministic"):
             def run():
-                o = rt.trace_opts(hit_ids=ids, hit_count=cnt) if mode == "log" else None
-                T = rt.rt_trace_visibility(bvh, rs, opts=o)
-                return T, rt.rt_trace_visibility_backward(bvh, rs, d["mean"], d["scale"], d["quat"], d["opacity"], T, w,
-                                                          ids if mode == "log" else None,
-                                                          cnt if mode == "log" else None)
+                tree = bvh_det if mode == "log_deterministic" else bvh
+                use_log = mode != "recompute"
+                o = rt.trace_opts(hit_ids=ids, hit_count=cnt) if use_log else None
+                T = rt.rt_trace_visibility(tree, rs, opts=o)
+                return T, rt.rt_trace_visibility_backward(tree, rs, d["mean"], d["scale"], d["quat"], d["opacity"], T,
+                                                          w, ids if use_log else None, cnt if use_log else None)
             for _ in range(3):
                 run()
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
@@ -460,6 +464,7 @@ def run_adjoint(rt, torch, dev):
         res["max_hits_per_ray"] = int(cnt.max())
         out.append(res)
         bvh.destroy()
+        bvh_det.destroy()
     return out
 
 

@@ -47,7 +47,8 @@ typedef enum {
     RT_ERR_HITLOG_OVERFLOW = 5, /* informational: some ray logged more hits than capacity */
     RT_ERR_TIMEOUT = 6,         /* a bounded device wait gave up           */
     RT_ERR_NOT_TRAINED = 7,     /* surrogate used before training          */
-    RT_ERR_UNSUPPORTED = 8      /* option combination not supported        */
+    RT_ERR_UNSUPPORTED = 8,     /* option combination not supported        */
+    RT_ERR_RANGE = 9            /* a value outside a fixed-point range (NaN included) */
 } rt_status;
 
 /* Tracing parameters.  Defaults (rt_params_default):
@@ -60,14 +61,21 @@ typedef enum {
  *                     fl(mu + fl(origin_eps * d)) and skip that Gaussian;
  *   box_mode = 0      leaf boxes of radius k_sigma; 1 = opacity-aware radius
  *                     min(k_sigma, sqrt(2 ln(o / alpha_min))), which gives the
- *                     same accepted set with tighter boxes.                  */
+ *                     same accepted set with tighter boxes;
+ *   deterministic = 0 the adjoint accumulates with float32 atomics (order
+ *                     depends on scheduling); 1 = in 64-bit fixed point
+ *                     (resolution 2^-32, |sum| < 2^31 per component, else
+ *                     RT_ERR_RANGE in the status word), so gradients are
+ *                     bit-reproducible whatever the order of rays.  The
+ *                     forward is reproducible for a given strategy either
+ *                     way.                                                   */
 typedef struct {
     float k_sigma;
     float alpha_min;
     float t_min;
     float origin_eps;
     int32_t box_mode;
-    int32_t reserved;
+    int32_t deterministic;
 } rt_params;
 
 void rt_params_default(rt_params *p);
@@ -395,7 +403,9 @@ rt_status rt_trace_ao(const rt_bvh *bvh, const rt_rayspec *rays, const rt_trace_
  * replayed; rays whose count exceeds hit_cap, or all rays if hit_ids is NULL,
  * are re-traversed.  The mean, scale, quat, opacity arrays must be the ones
  * the BVH was built from.  Accumulation uses float32 atomics (summation order
- * is not deterministic). */
+ * is not deterministic) unless the tree's params.deterministic is set: then
+ * 64-bit fixed-point sums (device scratch of 88 bytes per Gaussian) are added
+ * to the outputs once, bit-reproducibly. */
 rt_status rt_trace_visibility_backward(const rt_bvh *bvh, const rt_rayspec *rays,
                                        const float *mean, const float *scale, const float *quat,
                                        const float *opacity, const float *T, const float *dL_dT,

@@ -34,7 +34,7 @@ extern "C" void rt_params_default(rt_params *p) {
     p->t_min = 1e-4f;
     p->origin_eps = 1e-4f;
     p->box_mode = 0;
-    p->reserved = 0;
+    p->deterministic = 0;
 }
 
 extern "C" const char *rt_status_string(rt_status s) {
@@ -48,6 +48,7 @@ extern "C" const char *rt_status_string(rt_status s) {
         case RT_ERR_TIMEOUT: return "bounded device wait timed out";
         case RT_ERR_NOT_TRAINED: return "surrogate not trained";
         case RT_ERR_UNSUPPORTED: return "unsupported option";
+        case RT_ERR_RANGE: return "value outside the fixed-point range";
     }
     return "unknown status";
 }

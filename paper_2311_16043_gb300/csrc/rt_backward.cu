@@ -14,6 +14,11 @@
 // ray, otherwise found again by traversal (same code path as the forward, so
 // the same accepted set).  Rays the forward snapped to T = 0 have zero
 // gradient.
+// Accumulation: float32 atomics into the caller's arrays, or (params
+// deterministic = 1) integer atomics on 64-bit fixed point with 2^-32
+// resolution, one accumulator per parameter component, added to the caller's
+// arrays afterwards: integer addition is associative, so the result does not
+// depend on the order in which rays finish.
 #include "rt_trace_core.cuh"
 
 namespace {
@@ -21,7 +26,33 @@ namespace {
 struct GradOut {
     float *d_mean, *d_scale, *d_quat, *d_opacity, *d_ray_o;
     const float *mean, *scale, *quat, *opacity;
+    long long *fx;  // deterministic mode: [n][kFxPer] fixed-point accumulators
+    int *status;
 };
+
+// Fixed-point layout per Gaussian: mean 0-2, scale 3-5, quat 6-9, opacity 10.
+constexpr int kFxPer = 11;
+constexpr float kFxScale = 4294967296.0f;  // 2^32
+
+// v * 2^32 rounded to the nearest integer, added with an integer atomic; a
+// value or a sum outside the signed 64-bit range records RT_ERR_RANGE.
+__device__ __forceinline__ void fx_add(long long *p, float v, int *status) {
+    const float s = v * kFxScale;  // exact: a power of two
+    if (!(fabsf(s) < 9.2e18f)) {   // also NaN
+        rt_set_error(status, RT_ERR_RANGE);
+        return;
+    }
+    const long long q = __float2ll_rn(s);
+    const unsigned long long old = atomicAdd((unsigned long long *)p, (unsigned long long)q);
+    const long long o = (long long)old, sum = (long long)(old + (unsigned long long)q);
+    if (((o ^ sum) & (q ^ sum)) < 0) rt_set_error(status, RT_ERR_RANGE);
+}
+
+template <bool DET>
+__device__ __forceinline__ void grad_add(const GradOut &G, float *dst, int64_t i, int slot, float v) {
+    if (DET) fx_add(G.fx + i * kFxPer + slot, v, G.status);
+    else atomicAdd(dst, v);
+}
 
 // Peak point for the gradient: e = x(t*) - mu and alpha with IEEE division
 // and exponential.  dm^2/dmu = -2 Sigma^-1 e is first order in e, so t* must
@@ -50,6 +81,7 @@ __device__ __forceinline__ void peak_accurate(const BvhDev &b, int32_t p, float3
 }
 
 // Gradient contribution of one accepted hit (Gaussian with original index i).
+template <bool DET>
 __device__ __forceinline__ void hit_grad(const GradOut &G, int32_t i, float gT, float T, float alpha,
                                          float3 e, float3 &d_origin) {
     const float qw0 = G.quat[4 * i], qx0 = G.quat[4 * i + 1], qy0 = G.quat[4 * i + 2], qz0 = G.quat[4 * i + 3];
@@ -73,11 +105,11 @@ __device__ __forceinline__ void hit_grad(const GradOut &G, int32_t i, float gT, 
     const float gA = gT * (-T / (1.0f - alpha));  // dL/dalpha
     const float ex = alpha / G.opacity[i];        // exp(-m^2/2)
     const float gM = gA * (-0.5f * alpha);        // dL/dm^2
-    atomicAdd(G.d_opacity + i, gA * ex);
+    grad_add<DET>(G, G.d_opacity + i, i, 10, gA * ex);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) atomicAdd(G.d_mean + 3 * i + c, -2.0f * gM * sie[c]);
+    for (int c = 0; c < 3; ++c) grad_add<DET>(G, G.d_mean + 3 * i + c, i, c, -2.0f * gM * sie[c]);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) atomicAdd(G.d_scale + 3 * i + k, -2.0f * gM * u[k] * u[k] / s[k]);
+    for (int k = 0; k < 3; ++k) grad_add<DET>(G, G.d_scale + 3 * i + k, i, 3 + k, -2.0f * gM * u[k] * u[k] / s[k]);
     float Gm[9];
 #pragma unroll
     for (int c = 0; c < 3; ++c)
@@ -88,15 +120,16 @@ __device__ __forceinline__ void hit_grad(const GradOut &G, int32_t i, float gT, 
     const float gy = 2.f * (-2.f * y * Gm[0] + x * Gm[1] + w * Gm[2] + x * Gm[3] + z * Gm[5] - w * Gm[6] + z * Gm[7] - 2.f * y * Gm[8]);
     const float gz = 2.f * (-2.f * z * Gm[0] - w * Gm[1] + x * Gm[2] + w * Gm[3] - 2.f * z * Gm[4] + y * Gm[5] + x * Gm[6] + y * Gm[7]);
     const float dot = w * gw + x * gx + y * gy + z * gz;
-    atomicAdd(G.d_quat + 4 * i + 0, (gw - w * dot) / qn);
-    atomicAdd(G.d_quat + 4 * i + 1, (gx - x * dot) / qn);
-    atomicAdd(G.d_quat + 4 * i + 2, (gy - y * dot) / qn);
-    atomicAdd(G.d_quat + 4 * i + 3, (gz - z * dot) / qn);
+    grad_add<DET>(G, G.d_quat + 4 * i + 0, i, 6, (gw - w * dot) / qn);
+    grad_add<DET>(G, G.d_quat + 4 * i + 1, i, 7, (gx - x * dot) / qn);
+    grad_add<DET>(G, G.d_quat + 4 * i + 2, i, 8, (gy - y * dot) / qn);
+    grad_add<DET>(G, G.d_quat + 4 * i + 3, i, 9, (gz - z * dot) / qn);
     d_origin.x += 2.0f * gM * sie[0];
     d_origin.y += 2.0f * gM * sie[1];
     d_origin.z += 2.0f * gM * sie[2];
 }
 
+template <bool DET>
 __global__ void __launch_bounds__(128) k_backward(BvhDev b, RaySetDev rs, int64_t R, const float *T,
                                                   const float *dL_dT, const int32_t *hit_ids,
                                                   const int32_t *hit_count, int32_t cap, GradOut G,
@@ -138,14 +171,14 @@ __global__ void __launch_bounds__(128) k_backward(BvhDev b, RaySetDev rs, int64_
                     float alpha;
                     float3 e;
                     peak_accurate(b, p, o, d, alpha, e);
-                    hit_grad(G, i, gT, Tr, alpha, e, d_origin);
+                    hit_grad<DET>(G, i, gT, Tr, alpha, e, d_origin);
                 }
             } else if (b.n == 1) {
                 float alpha;
                 float3 e;
                 if (src != 0 && gauss_eval(b, 0, o, d, alpha, e)) {
                     peak_accurate(b, 0, o, d, alpha, e);
-                    hit_grad(G, __float_as_int(__ldg(b.gauss + 1).w), gT, Tr, alpha, e, d_origin);
+                    hit_grad<DET>(G, __float_as_int(__ldg(b.gauss + 1).w), gT, Tr, alpha, e, d_origin);
                 }
             } else if (b.n > 1) {
                 const float3 inv = safe_inv(d);
@@ -171,8 +204,8 @@ __global__ void __launch_bounds__(128) k_backward(BvhDev b, RaySetDev rs, int64_
                             float3 e;
                             if (p != src && gauss_eval(b, p, o, d, alpha, e)) {  // the forward's decision
                                 peak_accurate(b, p, o, d, alpha, e);
-                                hit_grad(G, __float_as_int(__ldg(b.gauss + 4 * p + 1).w), gT, Tr, alpha, e,
-                                         d_origin);
+                                hit_grad<DET>(G, __float_as_int(__ldg(b.gauss + 4 * p + 1).w), gT, Tr, alpha,
+                                              e, d_origin);
                             }
                         }
                     }
@@ -200,10 +233,26 @@ __global__ void __launch_bounds__(128) k_backward(BvhDev b, RaySetDev rs, int64_
             G.d_ray_o[3 * r + 2] = d_origin.z;
         }
         if (src_orig >= 0 && live) {
-            atomicAdd(G.d_mean + 3 * src_orig, d_origin.x);
-            atomicAdd(G.d_mean + 3 * src_orig + 1, d_origin.y);
-            atomicAdd(G.d_mean + 3 * src_orig + 2, d_origin.z);
+            grad_add<DET>(G, G.d_mean + 3 * src_orig, src_orig, 0, d_origin.x);
+            grad_add<DET>(G, G.d_mean + 3 * src_orig + 1, src_orig, 1, d_origin.y);
+            grad_add<DET>(G, G.d_mean + 3 * src_orig + 2, src_orig, 2, d_origin.z);
         }
+    }
+}
+
+// Deterministic mode: adds the fixed-point sums (times 2^-32) to the caller's
+// arrays.
+__global__ void k_fx_finalize(const long long *__restrict__ fx, int64_t n, float *d_mean, float *d_scale,
+                              float *d_quat, float *d_opacity) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n * kFxPer;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = j / kFxPer;
+        const int c = (int)(j - i * kFxPer);
+        const float v = (float)((double)fx[j] * (1.0 / 4294967296.0));
+        if (c < 3) d_mean[3 * i + c] += v;
+        else if (c < 6) d_scale[3 * i + c - 3] += v;
+        else if (c < 10) d_quat[4 * i + c - 6] += v;
+        else d_opacity[i] += v;
     }
 }
 
@@ -235,10 +284,30 @@ extern "C" rt_status rt_trace_visibility_backward(const rt_bvh *bvh, const rt_ra
     G.scale = scale;
     G.quat = quat;
     G.opacity = opacity;
+    G.fx = nullptr;
+    G.status = rt_status_ptr();
     int64_t grid = (R + 127) / 128;
     const int64_t cap_grid = (int64_t)rt_num_sms() * 16;
     if (grid > cap_grid) grid = cap_grid;
-    k_backward<<<(int)grid, 128, 0, (cudaStream_t)stream>>>(bvh_dev(bvh), rs, R, T, dL_dT, hit_ids,
-                                                           hit_count, hit_cap, G, rt_status_ptr());
-    return rt_check_launch();
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!bvh->params.deterministic) {
+        k_backward<false><<<(int)grid, 128, 0, st>>>(bvh_dev(bvh), rs, R, T, dL_dT, hit_ids, hit_count, hit_cap, G,
+                                                     G.status);
+        return rt_check_launch();
+    }
+    const size_t fx_bytes = (size_t)bvh->n * kFxPer * sizeof(long long);
+    RT_TRY(rt_alloc((void **)&G.fx, fx_bytes, stream));
+    rt_status s = cudaMemsetAsync(G.fx, 0, fx_bytes, st) == cudaSuccess ? RT_OK : RT_ERR_CUDA;
+    if (s == RT_OK) {
+        k_backward<true><<<(int)grid, 128, 0, st>>>(bvh_dev(bvh), rs, R, T, dL_dT, hit_ids, hit_count, hit_cap, G,
+                                                    G.status);
+        int64_t fgrid = (bvh->n * kFxPer + 255) / 256;
+        if (fgrid > (int64_t)rt_num_sms() * 8) fgrid = (int64_t)rt_num_sms() * 8;
+        k_fx_finalize<<<(int)fgrid, 256, 0, st>>>(G.fx, bvh->n, d_mean, d_scale, d_quat, d_opacity);
+        s = rt_check_launch();
+    } else {
+        cudaGetLastError();
+    }
+    rt_free(G.fx, stream);
+    return s;
 }

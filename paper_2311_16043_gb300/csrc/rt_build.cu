@@ -569,7 +569,7 @@ extern "C" rt_status rt_build_bvh(const float *mean, const float *scale, const f
     if (params) prm = *params;
     if (!(prm.k_sigma > 0.f) || !(prm.alpha_min > 0.f && prm.alpha_min < 1.f) ||
         !(prm.t_min >= 0.f && prm.t_min < 1.f) || !(prm.origin_eps >= 0.f) ||
-        (prm.box_mode != 0 && prm.box_mode != 1))
+        (prm.box_mode != 0 && prm.box_mode != 1) || (prm.deterministic != 0 && prm.deterministic != 1))
         return RT_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
 

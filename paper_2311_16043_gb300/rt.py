@@ -21,7 +21,7 @@ _LIB = None
 RT_OK = 0
 STATUS_NAMES = {0: "RT_OK", 1: "RT_ERR_INVALID_ARG", 2: "RT_ERR_OOM", 3: "RT_ERR_CUDA",
                 4: "RT_ERR_STACK_OVERFLOW", 5: "RT_ERR_HITLOG_OVERFLOW", 6: "RT_ERR_TIMEOUT",
-                7: "RT_ERR_NOT_TRAINED", 8: "RT_ERR_UNSUPPORTED"}
+                7: "RT_ERR_NOT_TRAINED", 8: "RT_ERR_UNSUPPORTED", 9: "RT_ERR_RANGE"}
 RT_RAYS_EXPLICIT, RT_RAYS_DIRS, RT_RAYS_ENV, RT_RAYS_HEMI = 0, 1, 2, 3
 (RT_KERNEL_AUTO, RT_KERNEL_RAY, RT_KERNEL_PACKET, RT_KERNEL_WIDE, RT_KERNEL_RAY_WIDE, RT_KERNEL_RAY_REFILL,
  RT_KERNEL_WARP_RAY) = 0, 1, 2, 3, 4, 5, 6
@@ -35,7 +35,7 @@ class RTError(RuntimeError):
 
 class rt_params(C.Structure):
     _fields_ = [("k_sigma", C.c_float), ("alpha_min", C.c_float), ("t_min", C.c_float),
-                ("origin_eps", C.c_float), ("box_mode", C.c_int32), ("reserved", C.c_int32)]
+                ("origin_eps", C.c_float), ("box_mode", C.c_int32), ("deterministic", C.c_int32)]
 
 
 class rt_rayspec(C.Structure):
@@ -174,10 +174,12 @@ def _stream(stream=None):
     return s.cuda_stream
 
 
-def params(k_sigma=3.0, alpha_min=1.0 / 255.0, t_min=1e-4, origin_eps=1e-4, box_mode=0) -> rt_params:
+def params(k_sigma=3.0, alpha_min=1.0 / 255.0, t_min=1e-4, origin_eps=1e-4, box_mode=0,
+           deterministic=False) -> rt_params:
     p = rt_params()
     lib().rt_params_default(C.byref(p))
     p.k_sigma, p.alpha_min, p.t_min, p.origin_eps, p.box_mode = k_sigma, alpha_min, t_min, origin_eps, box_mode
+    p.deterministic = int(bool(deterministic))
     return p
 
 
