@@ -276,6 +276,24 @@ __device__ __forceinline__ void wg_sync(int g) {
     asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(128) : "memory");
 }
 
+// Layer l's bias into this thread's accumulator row (128 columns), so the
+// MMA accumulates onto it and the epilogue adds nothing.
+__device__ __forceinline__ void tmem_store_bias(uint32_t lane_addr, const float *b) {
+#pragma unroll 1
+    for (int cc = 0; cc < 4; ++cc) {
+        float v[32];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const float4 x = reinterpret_cast<const float4 *>(b + 32 * cc)[q];
+            v[4 * q] = x.x;
+            v[4 * q + 1] = x.y;
+            v[4 * q + 2] = x.z;
+            v[4 * q + 3] = x.w;
+        }
+        tmem_st32(lane_addr + 32 * cc, v);
+    }
+}
+
 __global__ void __launch_bounds__(128 * INF_WG, 1) k_mlp_infer(MlpDev net, SampleSrc S, int64_t m, float *out,
                                                                float band, int64_t *fb_rid, int64_t *fb_pos,
                                                                unsigned long long *fb_count, int *status) {
@@ -328,8 +346,10 @@ __global__ void __launch_bounds__(128 * INF_WG, 1) k_mlp_infer(MlpDev net, Sampl
                 for (int k = 0; k < IN; ++k) f[k] = 0.0f;
             store_row_x0(act, tl, f);
         }
-        float z5 = b5;
+        tmem_store_bias(lane_addr, bias);
+        float2 z5p = make_float2(0.0f, 0.0f);  // even / odd units of the output layer
         for (int l = 0; l < 4; ++l) {
+            tmem_st_wait();
             fence_async_smem();
             tc_fence_before();
             wg_sync(g);
@@ -338,7 +358,7 @@ __global__ void __launch_bounds__(128 * INF_WG, 1) k_mlp_infer(MlpDev net, Sampl
                 const int K = l == 0 ? IN : H;
                 const uint32_t sbo = (uint32_t)(K / 8 * 128);
                 const uint32_t wb = w_addr + (l == 0 ? IMG_W1 : l == 1 ? IMG_W2 : l == 2 ? IMG_W3 : IMG_W4);
-                issue_mma(tmem, a_addr, 128, sbo, 256, wb, 128, sbo, 256, idesc, K, false);
+                issue_mma(tmem, a_addr, 128, sbo, 256, wb, 128, sbo, 256, idesc, K, true);  // onto the bias
                 tc_commit(bar);
             }
             if (!mbar_wait(bar, phase, WAIT_CYCLES)) {
@@ -348,23 +368,27 @@ __global__ void __launch_bounds__(128 * INF_WG, 1) k_mlp_infer(MlpDev net, Sampl
             phase ^= 1u;
             tc_fence_after();
             if (!ok) break;
-            const float *bl = bias + 128 * l;
 #pragma unroll 1
             for (int cc = 0; cc < 4; ++cc) {
                 float v[32];
                 tmem_ld32(lane_addr + 32 * cc, v);
-#pragma unroll
-                for (int k = 0; k < 32; ++k) v[k] += bl[32 * cc + k];
                 if (l < 3) {
                     store_chunk_relu(act, tl, 32 * cc, v);
                 } else {
+                    // z5 += w5_k bf16(relu(h_k)), two units per packed FMA
+                    const float2 *w5 = reinterpret_cast<const float2 *>(bias + 512 + 32 * cc);
 #pragma unroll
-                    for (int k = 0; k < 32; ++k) z5 = fmaf(bias[512 + 32 * cc + k], bf16_round(fmaxf(v[k], 0.0f)), z5);
+                    for (int q = 0; q < 16; ++q) {
+                        const uint32_t hq = pack_bf16_relu(v[2 * q], v[2 * q + 1]);
+                        z5p = __ffma2_rn(make_float2(bf16_lo(hq), bf16_hi(hq)), w5[q], z5p);
+                    }
                 }
             }
+            if (l < 3) tmem_store_bias(lane_addr, bias + 128 * (l + 1));
         }
         if (!ok) break;
         if (valid) {
+            const float z5 = b5 + (z5p.x + z5p.y);
             const float pr = 1.0f / (1.0f + __expf(-z5));
             out[i] = pr;
             const bool fb = band > 0.0f && fabsf(pr - 0.5f) < band;
