@@ -27,9 +27,12 @@ def _export(bvh):
 
 
 @pytest.mark.parametrize("n,seed,grid", [(1, 0, None), (2, 1, None), (3, 2, None), (4096, 1, None),
-                                         (10001, 3, None), (5000, 4, 8), (300_000, 2, None)])
+                                         (10001, 3, None), (5000, 4, 8), (300_000, 2, None),
+                                         (2_000_000, 2, None)])
 def test_topology_bit_exact(orc, n, seed, grid):
-    sc = scenes.object_scene(n, seed) if n == 300_000 else scenes.uniform_scene(n, seed)
+    """Sorted keys, children and parents equal the CPU twin's, up to the
+    bench's 2M-Gaussian object scene."""
+    sc = scenes.object_scene(n, seed) if n >= 300_000 else scenes.uniform_scene(n, seed)
     if grid:  # many equal Morton codes
         sc["mean"] = (np.round(sc["mean"] * grid) / grid).astype(np.float32)
     bvh, _ = _build(sc)
