@@ -155,7 +155,7 @@ typedef struct {
     void *ctx;
 } rt_allocator;
 rt_status rt_set_allocator(const rt_allocator *a);
-/* Returns the library pool's unused blocks to the driver on every device,
+/* Returns the library pool's unused blocks to the CUDA driver on every device,
  * keeping at most keep_bytes reserved per device (0 = all).  Call after
  * synchronising the streams that freed them.  Errors: RT_ERR_INVALID_ARG
  * (keep_bytes < 0), RT_ERR_CUDA. */

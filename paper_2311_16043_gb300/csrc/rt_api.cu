@@ -75,7 +75,7 @@ rt_allocator g_alloc = {nullptr, nullptr, nullptr};  // alloc == null: the libra
 
 // The library's own stream-ordered pool per device.  Its release threshold is
 // unbounded, so blocks freed in stream order stay mapped for the next call
-// (the device's default pool would hand them back to the driver at every
+// (the device's default pool would hand them back to the CUDA driver at every
 // synchronisation and remap them on the next allocation); rt_memory_trim
 // returns them.
 constexpr int kMaxDevices = 64;
