@@ -236,7 +236,7 @@ class ClockSampler:
 def trace_traffic():
     """DRAM bytes per launch of the trace kernel from the committed ncu summary,
     if it was taken on the current kernel sources (else None)."""
-    path = os.path.join(ROOT, "profiles", "trace_dram.txt")
+    path = os.path.join(ROOT, "profiles", "k_trace_dram_object2m_k128.txt")
     if not os.path.exists(path):
         return None
     kv = {}
