@@ -90,6 +90,15 @@ rt_status rt_status_clear(void);
  * (1 .. 4e9), records RT_ERR_TIMEOUT in the status word and returns.  No
  * fault, no hang; for tests of failure handling. */
 rt_status rt_selftest_wait_timeout(int64_t max_cycles, rt_stream_t stream);
+/* Upper bound, in SM clock cycles, of the bounded waits of the surrogate
+ * kernels (their mbarrier waits on their own tensor-core MMAs), process-wide;
+ * 0 restores the default of 4e9 (~2 s at 2 GHz).  A wait that gives up
+ * records RT_ERR_TIMEOUT; the whole warpgroup (inference) or CTA (training)
+ * then waits, with the default bound, for the MMAs it has in flight, frees
+ * its tensor memory and returns.  A tiny bound makes the waits give up on
+ * purpose, for tests of that exit path.  RT_ERR_INVALID_ARG outside
+ * [0, 4e9]. */
+rt_status rt_set_wait_limit(int64_t max_cycles);
 
 /* ------------------------------------------------------------------------ */
 /* LBVH (Sec. 4.1: binary radix tree of Karras 2012 over the Gaussians)      */
@@ -429,8 +438,15 @@ rt_status rt_trace_visibility_backward(const rt_bvh *bvh, const rt_rayspec *rays
  * 80 inputs; four hidden layers of 128 with ReLU; one sigmoid output.
  * Weights and activations are bf16 on the tensor cores with float32
  * accumulation; biases, the output layer and the master copy of all weights
- * are float32.  Loss: mean binary cross-entropy against soft targets T;
- * optimiser: Adam.
+ * are float32.  Loss: mean binary cross-entropy against soft targets T with
+ * a weight w (cfg.pos_weight) on the lit term,
+ *   L = -mean( w T log p + (1 - T) log(1 - p) ),
+ * optimiser: Adam.  The minimiser of the weighted loss for rays with mean
+ * visibility T is p = w T / (w T + 1 - T), so a ray region that is lit only
+ * now and then (small mean T) gets a p well inside the fallback band and is
+ * traced instead of being predicted as a small constant; the visibility
+ * estimate is recovered as T = p / (p + w (1 - p)) = sigmoid(z - ln w), z
+ * the logit.  w = 1 is the plain loss (T = p).
  *
  * Parameter block (float32, rt_surrogate_param_count() = 60033 values):
  *   W1[128][80], b1[128], W2[128][128], b2[128], W3[128][128], b3[128],
@@ -444,7 +460,7 @@ typedef struct {
     float beta2;   /* 0.999                                       */
     float eps;     /* 1e-8                                        */
     int32_t batch; /* samples per training step (262144)          */
-    int32_t reserved;
+    float pos_weight; /* w > 0, weight of the lit term of the loss (1) */
 } rt_mlp_cfg;
 
 void rt_mlp_cfg_default(rt_mlp_cfg *cfg);
@@ -466,11 +482,13 @@ rt_status rt_surrogate_set_state(rt_surrogate *s, const float *state, rt_stream_
 /* Scene bounds (host float[3] each) used to normalise origins. */
 rt_status rt_surrogate_set_bounds(rt_surrogate *s, const float *lo, const float *hi);
 
-/* p_out[m] = network output for explicit rays (device pos[m*3], dir[m*3]). */
+/* p_out[m] = network output p (the sigmoid) for explicit rays (device
+ * pos[m*3], dir[m*3]); the visibility estimate is p / (p + w (1 - p)). */
 rt_status rt_surrogate_forward(const rt_surrogate *s, const float *pos, const float *dir, int64_t m,
                                float *p_out, rt_stream_t stream);
-/* Mean BCE over m explicit samples (targets y[m]) and its gradient with
- * respect to the parameter block: grad_out[60033] and loss_out[1] (device). */
+/* Mean weighted BCE over m explicit samples (targets y[m], weight
+ * cfg.pos_weight on the y log p term) and its gradient with respect to the
+ * parameter block: grad_out[60033] and loss_out[1] (device). */
 rt_status rt_surrogate_loss_grad(const rt_surrogate *s, const float *pos, const float *dir,
                                  const float *y, int64_t m, float *grad_out, float *loss_out,
                                  rt_stream_t stream);
@@ -484,7 +502,8 @@ rt_status rt_surrogate_train(rt_surrogate *s, const rt_bvh *bvh, const rt_rayspe
                              const float *T_target, int32_t steps, uint64_t seed,
                              float *loss_curve, rt_stream_t stream);
 /* Visibility of an implicit ray set over `bvh` (DIRS or ENV, optionally a
- * ray_ids subset) from the surrogate: T_out[i] = p.  If band > 0, rays with
+ * ray_ids subset) from the surrogate: T_out[i] = p / (p + w (1 - p)), the
+ * network's estimate (= p for w = 1).  If band > 0, rays with
  * |p - 0.5| < band are traced on `bvh` instead (the fallback: one warp per
  * ray, RT_KERNEL_WARP_RAY) and T_out holds the traced value, bit-equal to
  * rt_trace_visibility with that kernel; n_fallback (device int64[1], may be
@@ -502,9 +521,10 @@ rt_status rt_surrogate_infer(const rt_surrogate *s, const rt_bvh *bvh, const rt_
  * counters live in a fixed 16 MiB + 256 B array inside the library, reserved
  * on every device that loads it until the process exits.  Same arguments and
  * results as rt_surrogate_infer; at most 1,048,576 rays per call (more:
- * RT_ERR_INVALID_ARG before anything is enqueued).  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress); make
- * that first call before any stream capture.  All calls share the array and
+ * RT_ERR_INVALID_ARG before anything is enqueued).  The first call in each
+ * CUDA context (once per device, and again after a device reset) looks up
+ * the array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  All calls share the array and
  * it keeps the previous call's contents (the call clears its counter itself):
  * calls that overlap on the GPU (other streams, other threads) race. */
 rt_status rt_surrogate_infer_noalloc(const rt_surrogate *s, const rt_bvh *bvh, const rt_rayspec *rays,

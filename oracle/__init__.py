@@ -88,7 +88,8 @@ def _load():
             "oracle_mlp_nparam": (i64, []),
             "oracle_mlp_set_bf16": (None, [i32]),
             "oracle_mlp_forward": (None, [P, i64, P, P, P]),
-            "oracle_mlp_loss_grad": (f64, [P, i64, P, P, P]),
+            "oracle_mlp_loss_grad": (f64, [P, i64, P, P, f64, P]),
+            "oracle_mlp_visibility": (None, [P, i64, P, f64, P]),
             "oracle_adam_step": (None, [i64, P, P, P, P, i64, f64, f64, f64, f64]),
         }
         for name, (res, args) in sig.items():
@@ -481,13 +482,25 @@ def mlp_forward(params, feat):
     return p, z
 
 
-def mlp_loss_grad(params, feat, y):
+def mlp_loss_grad(params, feat, y, pos_weight=1.0):
+    """Mean BCE against soft targets y with weight pos_weight on the lit
+    term, and its gradient (parameter-block layout)."""
     params = _c(params, np.float32)
     feat = _c(feat, np.float64)
     y = _c(y, np.float64)
     g = np.empty(params.shape[0], np.float64)
-    loss = _load().oracle_mlp_loss_grad(_p(params), feat.shape[0], _p(feat), _p(y), _p(g))
+    loss = _load().oracle_mlp_loss_grad(_p(params), feat.shape[0], _p(feat), _p(y), float(pos_weight), _p(g))
     return float(loss), g
+
+
+def mlp_visibility(params, feat, pos_weight=1.0):
+    """Visibility estimate 1 / (1 + w e^-z) of a network trained with weight
+    w = pos_weight on the lit term (= the sigmoid output for w = 1)."""
+    params = _c(params, np.float32)
+    feat = _c(feat, np.float64)
+    T = np.empty(feat.shape[0])
+    _load().oracle_mlp_visibility(_p(params), feat.shape[0], _p(feat), float(pos_weight), _p(T))
+    return T
 
 
 def adam_step(w, g, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):

@@ -1050,13 +1050,31 @@ void oracle_mlp_forward(const float *P, int64_t m, const double *feat, double *p
 }
 
 /*
- * Mean binary cross-entropy against soft targets y and its gradient for one
- * minibatch of m samples.  dL/dz5 = (p - y)/m; for l = 4..1 the upstream
+ * Visibility estimate of a network trained with weight w on the lit term of
+ * the loss (below): the weighted loss is minimised by p = w T / (w T + 1 - T),
+ * so T = p / (p + w (1 - p)) = 1 / (1 + w e^-z), z the logit.
+ */
+void oracle_mlp_visibility(const float *P, int64_t m, const double *feat, double w, double *T)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < m; ++i) {
+        double acts[5][MLP_H];
+        double z = mlp_fwd1(P, feat + i * MLP_IN, acts);
+        T[i] = 1.0 / (1.0 + w * exp(-z));
+    }
+}
+
+/*
+ * Mean binary cross-entropy against soft targets y, with weight w on the lit
+ * term, L = -(1/m) sum_i [w y_i log p_i + (1 - y_i) log(1 - p_i)], and its
+ * gradient for one minibatch of m samples.  dL/dz5 = (p (w y + 1 - y) - w y)/m
+ * (= (p - y)/m for w = 1); for l = 4..1 the upstream
  * gradient of the pre-activation, dz_l = bf16(dx_l * [x_l > 0]), feeds
  * dW_l = sum_i dz_l x_{l-1}^T, db_l = sum_i dz_l and dx_{l-1} = bf16(W_l)^T dz_l
  * (FP64 sums).  grad has the parameter-block layout; returns the loss.
  */
-double oracle_mlp_loss_grad(const float *P, int64_t m, const double *feat, const double *y, double *grad)
+double oracle_mlp_loss_grad(const float *P, int64_t m, const double *feat, const double *y, double w,
+                            double *grad)
 {
     static const int offW[4] = {OFF_W1, OFF_W2, OFF_W3, OFF_W4};
     static const int offB[4] = {OFF_B1, OFF_B2, OFF_B3, OFF_B4};
@@ -1082,8 +1100,8 @@ double oracle_mlp_loss_grad(const float *P, int64_t m, const double *feat, const
             /* log(1+e^-z) and log(1+e^z), stably */
             double sp_neg = (z > 0 ? 0.0 : -z) + log1p(exp(-fabs(z)));
             double sp_pos = (z > 0 ? z : 0.0) + log1p(exp(-fabs(z)));
-            loss += (yi * sp_neg + (1.0 - yi) * sp_pos) / (double)m;
-            double dz5 = (p - yi) / (double)m;
+            loss += (w * yi * sp_neg + (1.0 - yi) * sp_pos) / (double)m;
+            double dz5 = (p * (w * yi + 1.0 - yi) - w * yi) / (double)m;
             G[OFF_B5] += dz5;
             double dx[MLP_H];
             for (int k = 0; k < MLP_H; ++k) {

@@ -27,6 +27,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <atomic>
 #include <mutex>
 
 #include "rt_tc.cuh"
@@ -39,7 +40,7 @@ constexpr int IN = 80;
 constexpr int OFF_W1 = 0, OFF_B1 = 10240, OFF_W2 = 10368, OFF_B2 = 26752, OFF_W3 = 26880, OFF_B3 = 43264,
               OFF_W4 = 43392, OFF_B4 = 59776, OFF_W5 = 59904, OFF_B5 = 60032, NPARAM = 60033;
 constexpr int IMG_W1 = 0, IMG_W2 = 20480, IMG_W3 = 53248, IMG_W4 = 86016, IMG_BYTES = 118784;
-constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
+constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz: default bound of every wait
 constexpr unsigned FULL = 0xffffffffu;
 
 __host__ __device__ __forceinline__ uint32_t img_off(int r, int c, int kdim) {
@@ -258,6 +259,8 @@ struct MlpDev {
     const uint8_t *img;   // bf16 images
     float lo[3];          // origin normalisation x = 2 (p - lo)/(hi - lo) - 1 with
     float eh[3], el[3];   // hi - lo = eh + el exactly
+    float pos_w;          // weight w of the lit term of the loss
+    long long wait_cycles;  // bound of the first wait on each MMA commit
 };
 
 // ---------------------------------------------------------------------------
@@ -274,6 +277,21 @@ constexpr int INF_SMEM_TOTAL = INF_SMEM_BAR + 64;
 
 __device__ __forceinline__ void wg_sync(int g) {
     asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(128) : "memory");
+}
+
+// True iff v holds in all 128 threads of warpgroup g (a barrier of the group
+// with an AND reduction), so that the group takes every exit together.
+__device__ __forceinline__ bool wg_all(int g, bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, %2, 128, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(r)
+        : "r"(v ? 1u : 0u), "r"(1 + g)
+        : "memory");
+    return r != 0;
 }
 
 // Layer l's bias into this thread's accumulator row (128 columns), so the
@@ -294,9 +312,12 @@ __device__ __forceinline__ void tmem_store_bias(uint32_t lane_addr, const float 
     }
 }
 
+// out[i] is the network output p (decode == 0) or the visibility estimate
+// p / (p + w (1 - p)) = 1 / (1 + w e^-z) (decode != 0).
 __global__ void __launch_bounds__(128 * INF_WG, 1) k_mlp_infer(MlpDev net, SampleSrc S, int64_t m, float *out,
-                                                               float band, int64_t *fb_rid, int64_t *fb_pos,
-                                                               unsigned long long *fb_count, int *status) {
+                                                               int decode, float band, int64_t *fb_rid,
+                                                               int64_t *fb_pos, unsigned long long *fb_count,
+                                                               int *status) {
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *wimg = smem;
     float *bias = reinterpret_cast<float *>(smem + INF_SMEM_B);  // [4][128], then w5[128]
@@ -361,8 +382,13 @@ __global__ void __launch_bounds__(128 * INF_WG, 1) k_mlp_infer(MlpDev net, Sampl
                 issue_mma(tmem, a_addr, 128, sbo, 256, wb, 128, sbo, 256, idesc, K, true);  // onto the bias
                 tc_commit(bar);
             }
-            if (!mbar_wait(bar, phase, WAIT_CYCLES)) {
-                rt_set_error(status, RT_ERR_TIMEOUT);
+            // every thread waits; the group then agrees, so a wait that gives
+            // up in one thread takes the whole group out together
+            if (!wg_all(g, mbar_wait(bar, phase, net.wait_cycles))) {
+                // the committed MMAs still write this group's TMEM columns:
+                // let them finish (default bound) before leaving
+                mbar_wait(bar, phase, WAIT_CYCLES);
+                if (tl == 0) rt_set_error(status, RT_ERR_TIMEOUT);
                 ok = false;
             }
             phase ^= 1u;
@@ -389,8 +415,9 @@ __global__ void __launch_bounds__(128 * INF_WG, 1) k_mlp_infer(MlpDev net, Sampl
         if (!ok) break;
         if (valid) {
             const float z5 = b5 + (z5p.x + z5p.y);
-            const float pr = 1.0f / (1.0f + __expf(-z5));
-            out[i] = pr;
+            const float ez = __expf(-z5);
+            const float pr = 1.0f / (1.0f + ez);
+            out[i] = decode ? 1.0f / (1.0f + net.pos_w * ez) : pr;
             const bool fb = band > 0.0f && fabsf(pr - 0.5f) < band;
             const uint32_t mask = __ballot_sync(__activemask(), fb);
             if (fb) {
@@ -489,9 +516,13 @@ __global__ void __launch_bounds__(128, 1) k_mlp_train(MlpDev net, SampleSrc S, i
         tc_fence_before();
         __syncthreads();
     };
+    // every thread waits, then the CTA agrees (one vote), so a wait that
+    // gives up in one thread takes the whole CTA out together, after the
+    // committed MMAs have finished (default bound)
     auto wait_mma = [&]() {
-        if (!mbar_wait(bar, phase, WAIT_CYCLES)) {
-            rt_set_error(status, RT_ERR_TIMEOUT);
+        if (!__syncthreads_and(mbar_wait(bar, phase, net.wait_cycles) ? 1 : 0)) {
+            mbar_wait(bar, phase, WAIT_CYCLES);
+            if (t == 0) rt_set_error(status, RT_ERR_TIMEOUT);
             ok = false;
         }
         phase ^= 1u;
@@ -550,10 +581,12 @@ __global__ void __launch_bounds__(128, 1) k_mlp_train(MlpDev net, SampleSrc S, i
         }
         if (!ok) break;
         // ---- loss and output layer ----
+        // L = -(w y log p + (1 - y) log(1 - p)), dL/dz = p (1 + (w - 1) y) - w y
         const float pr = 1.0f / (1.0f + expf(-z5));
-        const float dz5 = valid ? (pr - y) * inv_batch : 0.0f;
+        const float wy = net.pos_w * y;
+        const float dz5 = valid ? (pr * (wy + 1.0f - y) - wy) * inv_batch : 0.0f;
         {
-            float lv = valid ? (y * (fmaxf(-z5, 0.0f) + log1pf(expf(-fabsf(z5)))) +
+            float lv = valid ? (wy * (fmaxf(-z5, 0.0f) + log1pf(expf(-fabsf(z5)))) +
                                 (1.0f - y) * (fmaxf(z5, 0.0f) + log1pf(expf(-fabsf(z5))))) * inv_batch
                              : 0.0f;
             float db5 = dz5;
@@ -757,10 +790,14 @@ struct rt_surrogate {
 
 namespace {
 
+std::atomic<long long> g_wait_cycles{WAIT_CYCLES};
+
 MlpDev mlp_dev(const rt_surrogate *s) {
     MlpDev n;
     n.params = s->params;
     n.img = s->img;
+    n.pos_w = s->cfg.pos_weight;
+    n.wait_cycles = g_wait_cycles.load();
     for (int c = 0; c < 3; ++c) {
         // exact split of hi - lo (host float arithmetic is IEEE round-to-nearest)
         const volatile float hi = s->hi[c], lo = s->lo[c];
@@ -806,7 +843,13 @@ extern "C" void rt_mlp_cfg_default(rt_mlp_cfg *c) {
     c->beta2 = 0.999f;
     c->eps = 1e-8f;
     c->batch = 262144;
-    c->reserved = 0;
+    c->pos_weight = 1.0f;
+}
+
+extern "C" rt_status rt_set_wait_limit(int64_t max_cycles) {
+    if (max_cycles < 0 || max_cycles > WAIT_CYCLES) return RT_ERR_INVALID_ARG;
+    g_wait_cycles.store(max_cycles == 0 ? WAIT_CYCLES : (long long)max_cycles);
+    return RT_OK;
 }
 
 extern "C" int64_t rt_surrogate_param_count(void) { return NPARAM; }
@@ -819,7 +862,7 @@ extern "C" rt_status rt_surrogate_create(const rt_mlp_cfg *cfg, uint64_t seed, r
     rt_mlp_cfg_default(&c);
     if (cfg) c = *cfg;
     if (!(c.lr > 0.f) || !(c.beta1 >= 0.f && c.beta1 < 1.f) || !(c.beta2 >= 0.f && c.beta2 < 1.f) ||
-        !(c.eps > 0.f) || c.batch <= 0)
+        !(c.eps > 0.f) || c.batch <= 0 || !(c.pos_weight > 0.f && c.pos_weight < 1e30f))
         return RT_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     rt_surrogate *s = new rt_surrogate();
@@ -937,8 +980,9 @@ extern "C" rt_status rt_surrogate_forward(const rt_surrogate *s, const float *po
     S.dir = dir;
     int64_t ngroups = ((m + 127) / 128 + INF_WG - 1) / INF_WG;
     int grid = (int)(ngroups < rt_num_sms() ? ngroups : rt_num_sms());
-    k_mlp_infer<<<grid, 128 * INF_WG, INF_SMEM_TOTAL, (cudaStream_t)stream>>>(mlp_dev(s), S, m, p_out, 0.f, nullptr,
-                                                                     nullptr, nullptr, rt_status_ptr());
+    k_mlp_infer<<<grid, 128 * INF_WG, INF_SMEM_TOTAL, (cudaStream_t)stream>>>(mlp_dev(s), S, m, p_out, 0, 0.f,
+                                                                              nullptr, nullptr, nullptr,
+                                                                              rt_status_ptr());
     return rt_check_launch();
 }
 
@@ -1036,8 +1080,8 @@ extern "C" rt_status rt_surrogate_infer(const rt_surrogate *s, const rt_bvh *bvh
     }
     int64_t ngroups = ((m + 127) / 128 + INF_WG - 1) / INF_WG;
     int grid = (int)(ngroups < rt_num_sms() ? ngroups : rt_num_sms());
-    k_mlp_infer<<<grid, 128 * INF_WG, INF_SMEM_TOTAL, st>>>(mlp_dev(s), S, m, T_out, band, fb_rid, fb_pos, fb_count,
-                                                   rt_status_ptr());
+    k_mlp_infer<<<grid, 128 * INF_WG, INF_SMEM_TOTAL, st>>>(mlp_dev(s), S, m, T_out, 1, band, fb_rid, fb_pos,
+                                                            fb_count, rt_status_ptr());
     rt_status r = rt_check_launch();
     if (r == RT_OK && use_fb) {
         r = rt_trace_launch_list(bvh, rays, fb_rid, fb_pos, fb_count, m, T_out, stream, work);
@@ -1090,23 +1134,72 @@ constexpr int64_t kNoAllocMaxRays = 1 << 20;
 static __device__ __align__(256) int64_t g_noalloc_scratch[2 * kNoAllocMaxRays + 32];
 
 std::mutex g_noalloc_mu;
-int64_t *g_noalloc_ptr[64] = {nullptr};
 
-// Device address of the scratch array on the current device, looked up once
-// per device (the host-side symbol is only a stand-in, never a device address).
-rt_status noalloc_scratch(int64_t **out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return RT_ERR_CUDA;
-    std::lock_guard<std::mutex> g(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-            cudaGetLastError();
-            return RT_ERR_CUDA;
+// The array's device address is a property of the module loaded into a CUDA
+// context.  A device reset destroys that context (and the module with it);
+// the next context gets a new unique id (cuCtxGetId), so addresses are cached
+// per context id and an address from a destroyed context is never reused.
+typedef int (*ctx_get_current_fn)(void **);
+typedef int (*ctx_get_id_fn)(void *, unsigned long long *);
+ctx_get_current_fn g_ctx_current = nullptr;
+ctx_get_id_fn g_ctx_id = nullptr;
+bool g_ctx_fns_done = false;
+constexpr int kNoAllocCache = 16;
+unsigned long long g_noalloc_ctx[kNoAllocCache] = {0};
+int64_t *g_noalloc_ptr[kNoAllocCache] = {nullptr};
+int g_noalloc_next = 0;
+
+// Unique id of the current CUDA context, 0 if none is current or the driver
+// does not provide the calls (then nothing is cached).  Caller holds the lock.
+unsigned long long current_ctx_id() {
+    if (!g_ctx_fns_done) {
+        g_ctx_fns_done = true;
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) ==
+                cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q2 == cudaDriverEntryPointSuccess) {
+            g_ctx_current = (ctx_get_current_fn)f1;
+            g_ctx_id = (ctx_get_id_fn)f2;
         }
-        g_noalloc_ptr[dev] = (int64_t *)p;
+        cudaGetLastError();
     }
-    *out = g_noalloc_ptr[dev];
+    if (!g_ctx_current || !g_ctx_id) return 0;
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_current(&ctx) != 0 || !ctx || g_ctx_id(ctx, &id) != 0) return 0;
+    return id;
+}
+
+// Device address of the scratch array in the current context (the host-side
+// symbol is only a stand-in, never a device address): looked up once per
+// context with cudaGetSymbolAddress; a failed lookup is returned as an error
+// and leaves nothing cached.
+rt_status noalloc_scratch(int64_t **out) {
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    unsigned long long id = current_ctx_id();
+    if (id != 0) {
+        for (int k = 0; k < kNoAllocCache; ++k) {
+            if (g_noalloc_ctx[k] == id && g_noalloc_ptr[k]) {
+                *out = g_noalloc_ptr[k];
+                return RT_OK;
+            }
+        }
+    }
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return RT_ERR_CUDA;
+    }
+    if (id == 0) id = current_ctx_id();  // the lookup made the primary context current
+    if (id != 0) {
+        g_noalloc_ctx[g_noalloc_next] = id;
+        g_noalloc_ptr[g_noalloc_next] = (int64_t *)p;
+        g_noalloc_next = (g_noalloc_next + 1) % kNoAllocCache;
+    }
+    *out = (int64_t *)p;
     return RT_OK;
 }
 
@@ -1146,7 +1239,7 @@ extern "C" rt_status rt_surrogate_infer_noalloc(const rt_surrogate *s, const rt_
     S.R = rs.n_rays;
     int64_t ngroups = ((m + 127) / 128 + INF_WG - 1) / INF_WG;
     int grid = (int)(ngroups < rt_num_sms() ? ngroups : rt_num_sms());
-    k_mlp_infer<<<grid, 128 * INF_WG, INF_SMEM_TOTAL, st>>>(mlp_dev(s), S, m, T_out, band, use_fb ? fb_rid : nullptr,
+    k_mlp_infer<<<grid, 128 * INF_WG, INF_SMEM_TOTAL, st>>>(mlp_dev(s), S, m, T_out, 1, band, use_fb ? fb_rid : nullptr,
                                                    use_fb ? fb_pos : nullptr, use_fb ? fb_count : nullptr,
                                                    rt_status_ptr());
     RT_TRY(rt_check_launch());

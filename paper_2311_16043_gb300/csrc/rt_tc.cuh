@@ -132,11 +132,28 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
 
+// Non-blocking test of the mbarrier phase with the given parity.
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
 // Wait for the mbarrier phase with the given parity to complete, giving up
-// after ~`max_cycles` SM clock cycles.  Returns false on timeout.
+// after ~`max_cycles` SM clock cycles.  Returns false on timeout.  The bound
+// is checked before each (potentially suspending) try_wait, so even a bound
+// of a few cycles is honoured.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long max_cycles) {
     const long long t0 = clock64();
     for (;;) {
+        if (mbar_test(bar, parity)) return true;
+        if (clock64() - t0 > max_cycles) return false;
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"

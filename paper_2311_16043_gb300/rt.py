@@ -74,7 +74,7 @@ class rt_batch_job(C.Structure):
 
 class rt_mlp_cfg(C.Structure):
     _fields_ = [("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
-                ("batch", C.c_int32), ("reserved", C.c_int32)]
+                ("batch", C.c_int32), ("pos_weight", C.c_float)]
 
 
 _P = C.c_void_p
@@ -88,6 +88,7 @@ _SIGS = {
     "rt_status_last": (_I32, []),
     "rt_status_clear": (_I32, []),
     "rt_selftest_wait_timeout": (_I32, [_I64, _P]),
+    "rt_set_wait_limit": (_I32, [_I64]),
     "rt_set_allocator": (_I32, [_P]),
     "rt_build_bvh": (_I32, [_P, _P, _P, _P, _I64, _P, _P, _P]),
     "rt_bvh_destroy": (_I32, [_P, _P]),
@@ -189,6 +190,11 @@ def rt_status_last() -> int:
 
 def rt_status_clear() -> None:
     _check(lib().rt_status_clear(), "rt_status_clear")
+
+
+def rt_set_wait_limit(max_cycles: int) -> None:
+    """Bound (SM cycles) of the surrogate kernels' waits; 0 restores ~2 s."""
+    _check(lib().rt_set_wait_limit(int(max_cycles)), "rt_set_wait_limit")
 
 
 class Bvh:
@@ -570,10 +576,10 @@ def rt_trace_visibility_backward(bvh: Bvh, rs: rt_rayspec, mean, scale, quat, op
 # ---------------------------------------------------------------------------
 # Learned visibility surrogate
 # ---------------------------------------------------------------------------
-def mlp_cfg(lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, batch=262144) -> rt_mlp_cfg:
+def mlp_cfg(lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, batch=262144, pos_weight=1.0) -> rt_mlp_cfg:
     c = rt_mlp_cfg()
     lib().rt_mlp_cfg_default(C.byref(c))
-    c.lr, c.beta1, c.beta2, c.eps, c.batch = lr, beta1, beta2, eps, batch
+    c.lr, c.beta1, c.beta2, c.eps, c.batch, c.pos_weight = lr, beta1, beta2, eps, batch, pos_weight
     return c
 
 

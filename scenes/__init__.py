@@ -327,6 +327,21 @@ def loss_weights(n_rays: int, seed: int) -> np.ndarray:
     return _f32(np.random.default_rng(seed).uniform(0.0, 1.0, size=n_rays))
 
 
+def stratified_ray_ids(n_rays: int, m: int, seed: int) -> np.ndarray:
+    """A seeded sorted sample of m distinct ray ids spread over the whole of
+    [0, n_rays): the range is cut into m strata [floor(j n/m), floor((j+1) n/m))
+    and one id is drawn uniformly from each (int64).  O(m), for samples too
+    large for sample_ray_ids."""
+    m = min(m, n_rays)
+    if m <= 0:
+        return np.zeros(0, np.int64)
+    j = np.arange(m + 1, dtype=np.int64)
+    edges = (j * n_rays) // m
+    lo, width = edges[:-1], edges[1:] - edges[:-1]
+    u = np.random.default_rng(seed).random(m)
+    return lo + np.minimum((u * width).astype(np.int64), width - 1)
+
+
 def sample_ray_ids(n_rays: int, m: int, seed: int) -> np.ndarray:
     """A seeded sorted sample of m distinct ray ids in [0, n_rays) (int64)."""
     rng = np.random.default_rng(seed)

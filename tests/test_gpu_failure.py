@@ -39,3 +39,45 @@ def test_invalid_ray_ids_are_reported():
     T = T.cpu().numpy()
     assert np.isnan(T[2]) and np.isnan(T[3]) and np.all(np.isfinite(T[[0, 1, 4]]))
     rt.rt_status_clear()
+
+
+def test_surrogate_waits_give_up_together_and_context_survives():
+    """The surrogate kernels' own bounded waits (on their MMA commits) made
+    to give up at once (a 1-cycle bound): inference and training report
+    RT_ERR_TIMEOUT, leave only after their MMAs finished, and the next calls
+    with the default bound give the same results as before."""
+    from paper_2311_16043_gb300 import rt
+    rng = np.random.default_rng(3)
+    m = 4000  # several tiles and warpgroups, the last tile ragged
+    pos = torch.from_numpy(rng.uniform(-1, 1, (m, 3)).astype(np.float32)).cuda()
+    d = rng.standard_normal((m, 3))
+    d = torch.from_numpy((d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)).cuda()
+    y = torch.from_numpy(rng.uniform(0, 1, m).astype(np.float32)).cuda()
+    s = rt.rt_surrogate_create(rt.mlp_cfg(batch=1024), seed=4)
+    p0 = rt.rt_surrogate_forward(s, pos, d)
+    loss0, g0 = rt.rt_surrogate_loss_grad(s, pos, d, y)
+    torch.cuda.synchronize()
+    rt.rt_status_clear()
+    try:
+        rt.rt_set_wait_limit(1)
+        rt.rt_surrogate_forward(s, pos, d)
+        torch.cuda.synchronize()
+        assert rt.rt_status_last() == 6  # RT_ERR_TIMEOUT
+        rt.rt_status_clear()
+        rt.rt_surrogate_loss_grad(s, pos, d, y)
+        torch.cuda.synchronize()
+        assert rt.rt_status_last() == 6
+    finally:
+        rt.rt_set_wait_limit(0)
+        rt.rt_status_clear()
+    p1 = rt.rt_surrogate_forward(s, pos, d)
+    loss1, g1 = rt.rt_surrogate_loss_grad(s, pos, d, y)
+    torch.cuda.synchronize()
+    assert rt.rt_status_last() == 0
+    assert torch.equal(p0, p1)
+    # the per-CTA sums of the bias gradients use shared-memory atomics, so
+    # the gradient is reproducible up to float32 summation order
+    assert torch.allclose(loss1, loss0, rtol=1e-6, atol=0)
+    assert torch.allclose(g1, g0, rtol=1e-4, atol=1e-6 * float(g0.abs().max()))
+    with pytest.raises(rt.RTError):
+        rt.rt_set_wait_limit(-1)

@@ -47,9 +47,9 @@ def rand_rays(m, seed):
     return pos, d.astype(np.float32)
 
 
-def make_surrogate(P, lo, hi):
+def make_surrogate(P, lo, hi, pos_weight=1.0):
     from paper_2311_16043_gb300 import rt
-    s = rt.rt_surrogate_create(rt.mlp_cfg(batch=1024), seed=1)
+    s = rt.rt_surrogate_create(rt.mlp_cfg(batch=1024, pos_weight=pos_weight), seed=1)
     rt.rt_surrogate_set_params(s, _dev(P))
     rt.rt_surrogate_set_bounds(s, lo, hi)
     return s
@@ -73,23 +73,103 @@ def test_forward_matches_oracle(orc, m):
     assert want.std() > 0.01 or m == 1  # a non-trivial network
 
 
-def test_loss_grad_matches_oracle(orc):
+@pytest.mark.parametrize("w", [1.0, 8.0])
+def test_loss_grad_matches_oracle(orc, w):
     from paper_2311_16043_gb300 import rt
     P = rand_params(5)
     lo, hi = np.array([-1.2, -1.2, -1.2], np.float32), np.array([1.4, 1.4, 1.4], np.float32)
-    s = make_surrogate(P, lo, hi)
+    s = make_surrogate(P, lo, hi, pos_weight=w)
     m = 1000  # 8 tiles, the last one ragged
     pos, d = rand_rays(m, 6)
-    y = np.random.default_rng(7).uniform(0, 1, m).astype(np.float32)
+    # mostly dark targets with a lit minority, as in the visibility tables
+    rng = np.random.default_rng(7)
+    y = np.where(rng.uniform(0, 1, m) < 0.2, rng.uniform(0, 1, m), 0.0).astype(np.float32)
     loss, g = rt.rt_surrogate_loss_grad(s, _dev(pos), _dev(d), _dev(y))
     torch.cuda.synchronize()
     assert rt.rt_status_last() == 0
     g = g.cpu().numpy().astype(np.float64)
-    want_loss, want = orc.mlp_loss_grad(P, orc.mlp_encode(pos, d, lo, hi), y.astype(np.float64))
+    want_loss, want = orc.mlp_loss_grad(P, orc.mlp_encode(pos, d, lo, hi), y.astype(np.float64), pos_weight=w)
     assert float(loss.item()) == pytest.approx(want_loss, rel=1e-4)
     for name, (a, b) in GROUPS.items():
         rel = np.linalg.norm(g[a:b] - want[a:b]) / max(np.linalg.norm(want[a:b]), 1e-30)
         assert rel < 1e-3, (name, rel)
+
+
+def _infer_case(orc, kind, ids_mode):
+    """Scene, ray set and the oracle's own float32 rays for one case."""
+    from paper_2311_16043_gb300 import rt
+    if ids_mode == "full":
+        sc = scenes.uniform_scene(1000, 12)
+        n, K = 1000, 8
+    else:
+        sc = scenes.uniform_scene(4096, 1)
+        n, K = 4096, 32
+    dv = {k: _dev(v) for k, v in sc.items()}
+    bvh = rt.rt_build_bvh(dv["mean"], dv["scale"], dv["quat"], dv["opacity"])
+    env = E = None
+    if kind == "dirs":
+        dirs = scenes.fibonacci_sphere(K)
+    else:
+        env = scenes.envmap(399)
+        E = rt.rt_envmap_create(env["radiance"], env["solid_angle"], env["corners"])
+    R = n * K
+    ids = np.arange(R, dtype=np.int64) if ids_mode == "full" else scenes.sample_ray_ids(R, 3001, 21)
+    ids_dev = None if ids_mode == "full" else _dev(ids)
+    if kind == "dirs":
+        rs = rt.rayspec(rt.RT_RAYS_DIRS, dirs=_dev(dirs), ray_ids=ids_dev)
+        ro, rd, rsrc = orc.dir_rays(sc["mean"], dirs, ids)
+    else:
+        rs = rt.rayspec(rt.RT_RAYS_ENV, env=E, n_samples=K, seed=777, ray_ids=ids_dev)
+        ro, rd, rsrc = orc.env_rays(sc["mean"], env, 777, K, ids)
+    return sc, bvh, rs, E, ro, rd, rsrc
+
+
+@pytest.mark.parametrize("kind,ids_mode", [("dirs", "full"), ("dirs", "subset"), ("env", "full"),
+                                           ("env", "subset")])
+@pytest.mark.parametrize("w", [1.0, 8.0])
+def test_infer_matches_oracle(orc, kind, ids_mode, w):
+    """rt_surrogate_infer on implicit ray sets (rays generated in the kernel,
+    a whole set or an id subset), element by element against the oracle's
+    MLP on the oracle's own rays: band 0 gives the visibility estimate
+    1 / (1 + w e^-z); with band 0.3 the rays with |p - 0.5| < 0.3 carry the
+    traced T (brute force within 1e-5) and the others keep the estimate."""
+    from paper_2311_16043_gb300 import rt
+    sc, bvh, rs, E, ro, rd, rsrc = _infer_case(orc, kind, ids_mode)
+    P = rand_params(13)
+    info = bvh.info()
+    lo, hi = np.array(info["lo"], np.float32), np.array(info["hi"], np.float32)
+    s = make_surrogate(P, lo, hi, pos_weight=w)
+    m = ro.shape[0]
+    got0 = rt.rt_surrogate_infer(s, bvh, rs, band=0.0)
+    nfb = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+    q = rt.rt_surrogate_infer(s, bvh, rs, band=0.3, n_fallback=nfb)
+    p_gpu = rt.rt_surrogate_forward(s, _dev(ro), _dev(rd))
+    torch.cuda.synchronize()
+    assert rt.rt_status_last() == 0
+    got0 = got0.cpu().numpy().astype(np.float64)
+    q = q.cpu().numpy().astype(np.float64)
+    p_gpu = p_gpu.cpu().numpy().astype(np.float64)
+    feat = orc.mlp_encode(ro, rd, lo, hi)
+    want = orc.mlp_visibility(P, feat, pos_weight=w)
+    p_want, _ = orc.mlp_forward(P, feat)
+    err = np.abs(got0 - want)
+    assert err.max() < 3e-3, err.max()
+    assert np.median(err) < 2e-4, np.median(err)
+    assert want.std() > 0.01
+    # the fallback set is decided on the network output p
+    fb = np.abs(p_gpu - 0.5) < 0.3
+    assert int(nfb.item()) == int(fb.sum()) and 0 < fb.sum() < m
+    near_edge = np.abs(np.abs(p_want - 0.5) - 0.3) < 3e-3
+    assert np.all((fb == (np.abs(p_want - 0.5) < 0.3)) | near_edge)
+    np.testing.assert_array_equal(q[~fb], got0[~fb])
+    ref = orc.trace(sc, ro[fb], rd[fb], rsrc[fb])
+    ok = ref["flags"] == 0
+    assert ok.mean() > 0.95
+    assert np.abs(q[fb][ok] - ref["T"][ok]).max() <= 1e-5
+    if E is not None:
+        E.destroy()
+    s.destroy()
+    bvh.destroy()
 
 
 def test_state_roundtrip():
@@ -155,41 +235,63 @@ def test_one_adam_step_matches_oracle(orc, small_trace):
 
 
 def test_training_and_fallback():
-    """Train on the tracer's visibility of an object-scale scene (300k
-    flattened Gaussians on analytic surfaces x 32 directions), then infer on
-    held-out (rotated) directions: the loss falls, the surrogate beats a
-    constant predictor, and with the fallback band the uncertain rays carry
-    the traced value exactly."""
+    """The bench workload: train on the tracer's visibility table of the
+    2M-Gaussian object scene x 128 directions (weight 4 on the lit term,
+    2,000 Adam steps of 2^18 samples), then infer on 2^20 held-out rays
+    (rotated Fibonacci set) sampled over the whole scene.  The loss falls;
+    the uncertain rays carry the traced value exactly; with the fallback the
+    MAE is at most 0.01 and at most half that of the best constant predictor
+    (0 here: most rays are dark), the network alone beats that constant, and
+    the surrogate with fallback is faster than the tracer on the same rays."""
     from paper_2311_16043_gb300 import rt
-    sc = scenes.object_scene(300_000, 2)
-    dirs = scenes.fibonacci_sphere(32)
+    n, K = 2_000_000, 128
+    sc = scenes.object_scene(n, 2)
+    dirs = scenes.fibonacci_sphere(K)
     dv = {k: _dev(v) for k, v in sc.items()}
     bvh = rt.rt_build_bvh(dv["mean"], dv["scale"], dv["quat"], dv["opacity"])
     rs = rt.rayspec(rt.RT_RAYS_DIRS, dirs=_dev(dirs))
     T = rt.rt_trace_visibility(bvh, rs)
-    s = rt.rt_surrogate_create(rt.mlp_cfg(batch=65536, lr=1e-3), seed=3)
-    curve = rt.rt_surrogate_train(s, bvh, rs, T, steps=1500, seed=5).cpu().numpy()
-    assert curve[-50:].mean() < 0.8 * curve[:5].mean(), (curve[:5], curve[-50:])
-    held = scenes.rotated_fibonacci(32, 51)
-    rs_h = rt.rayspec(rt.RT_RAYS_DIRS, dirs=_dev(held))
+    s = rt.rt_surrogate_create(rt.mlp_cfg(batch=262144, lr=1e-3, pos_weight=4.0), seed=5)
+    curve = rt.rt_surrogate_train(s, bvh, rs, T, steps=2000, seed=5).cpu().numpy()
+    del T
+    assert curve[-50:].mean() < 0.5 * curve[:5].mean(), (curve[:5], curve[-50:])
+    held = scenes.rotated_fibonacci(K, 51)
+    ids = _dev(scenes.sample_ray_ids(n * K, 1 << 20, 52))
+    rs_h = rt.rayspec(rt.RT_RAYS_DIRS, dirs=_dev(held), ray_ids=ids)
     # fallback rays are traced one warp per ray: compare with that traversal
     T_h = rt.rt_trace_visibility(bvh, rs_h, opts=rt.trace_opts(kernel=rt.RT_KERNEL_WARP_RAY))
     p = rt.rt_surrogate_infer(s, bvh, rs_h, band=0.0)
     nfb = torch.zeros(1, dtype=torch.int64, device="cuda")
     q = rt.rt_surrogate_infer(s, bvh, rs_h, band=0.3, n_fallback=nfb)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record()
+    rt.rt_surrogate_infer(s, bvh, rs_h, band=0.3, T_out=torch.empty_like(q))
+    ev[1].record()
+    rt.rt_trace_visibility(bvh, rs_h, torch.empty_like(q))
+    ev[2].record()
     torch.cuda.synchronize()
     assert rt.rt_status_last() == 0
+    t_surr, t_trace = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
     mae_s = (p - T_h).abs().mean().item()
     mae_f = (q - T_h).abs().mean().item()
     nf = int(nfb.item())
-    fb = (p - 0.5).abs() < 0.3
-    assert nf == int(fb.sum().item())
+    # the network output (the sigmoid, before decoding) decides the fallback
+    o, d, _ = rt.rt_materialize_rays(bvh, rs_h, ids)
+    pn = rt.rt_surrogate_forward(s, o, d)
+    torch.cuda.synchronize()
+    fb = (pn - 0.5).abs() < 0.3
+    assert nf == int(fb.sum().item()) and nf > 0
     assert torch.equal(q[fb], T_h[fb])  # fallback rays are traced exactly
     assert torch.equal(q[~fb], p[~fb])
-    assert mae_f <= mae_s
-    mae_const = (T_h - T.mean()).abs().mean().item()
-    print(f"held-out MAE: surrogate {mae_s:.4f}, with fallback {mae_f:.4f} ({nf} of {T_h.numel()} rays traced), "
-          f"constant {mae_const:.4f}; loss {curve[:5].mean():.4f} -> {curve[-50:].mean():.4f}")
-    # most rays of this scene are occluded, so the mean is a strong baseline
-    assert mae_s < 0.9 * mae_const
-    assert mae_f < 0.6 * mae_const
+    mae_zero = T_h.abs().mean().item()
+    med = T_h.median().item()
+    mae_const = min(mae_zero, (T_h - med).abs().mean().item())
+    print(f"held-out MAE: surrogate {mae_s:.5f}, with fallback {mae_f:.5f} ({nf} of {T_h.numel()} rays traced), "
+          f"predict-zero {mae_zero:.5f}, best constant {mae_const:.5f}; loss {curve[:5].mean():.4f} -> "
+          f"{curve[-50:].mean():.4f}; {t_surr:.2f} ms vs tracer {t_trace:.2f} ms")
+    assert mae_f <= 0.01
+    assert mae_f <= 0.5 * mae_const
+    assert mae_s < mae_const
+    assert t_surr < t_trace
+    s.destroy()
+    bvh.destroy()

@@ -84,6 +84,44 @@ def test_bce_gradient_is_p_minus_y(orc):
     assert loss == pytest.approx(want, rel=1e-12)
 
 
+@pytest.mark.parametrize("w", [1.0, 4.0, 30.0])
+def test_weighted_bce_minimiser_and_decoding(orc, w):
+    """A network that outputs one constant logit b5: the weighted loss over
+    targets y is smallest where p = w ybar / (w ybar + 1 - ybar) (a property
+    of the loss, found here by minimising it numerically over b5), its
+    gradient there is 0, and the visibility decoding returns ybar."""
+    rng = np.random.default_rng(8)
+    feat = rng.uniform(-1, 1, (64, 80))
+    y = np.where(rng.uniform(0, 1, 64) < 0.1, rng.uniform(0, 1, 64), 0.0)
+    ybar = y.mean()
+
+    def loss_at(b):
+        P = np.zeros(NP, np.float32)
+        P[OFF_B5] = b
+        return orc.mlp_loss_grad(P, feat, y, pos_weight=w)
+
+    # golden-section search of the loss over b5 (no use of the closed form)
+    a, b = -12.0, 6.0
+    g = (math.sqrt(5) - 1) / 2
+    for _ in range(80):
+        c, d = b - g * (b - a), a + g * (b - a)
+        if loss_at(c)[0] < loss_at(d)[0]:
+            b = d
+        else:
+            a = c
+    z = 0.5 * (a + b)
+    p = 1 / (1 + math.exp(-z))
+    assert p == pytest.approx(w * ybar / (w * ybar + 1 - ybar), rel=1e-5)
+    P = np.zeros(NP, np.float32)
+    P[OFF_B5] = z
+    _, grad = orc.mlp_loss_grad(P, feat, y, pos_weight=w)
+    assert abs(grad[OFF_B5]) < 1e-6
+    T = orc.mlp_visibility(P, feat[:4], pos_weight=w)
+    np.testing.assert_allclose(T, ybar, rtol=1e-5)
+    if w == 1.0:  # plain loss: the decoding is the sigmoid output itself
+        np.testing.assert_allclose(T, orc.mlp_forward(P, feat[:4])[0], rtol=1e-15)
+
+
 def _rand_params(seed, scale=1.0):
     rng = np.random.default_rng(seed)
     P = np.zeros(NP, np.float32)
@@ -99,7 +137,8 @@ def _rand_params(seed, scale=1.0):
     return P
 
 
-def test_backward_finite_differences(orc):
+@pytest.mark.parametrize("w", [1.0, 12.0])
+def test_backward_finite_differences(orc, w):
     orc.mlp_set_bf16(False)
     try:
         P = _rand_params(2)
@@ -107,7 +146,7 @@ def test_backward_finite_differences(orc):
         feat = rng.uniform(-1, 1, (16, 80))
         feat[:, 78:] = 0
         y = rng.uniform(0, 1, 16)
-        loss, g = orc.mlp_loss_grad(P, feat, y)
+        loss, g = orc.mlp_loss_grad(P, feat, y, pos_weight=w)
         idx = np.concatenate([rng.choice(np.arange(OFF_W1, OFF_B1), 40), rng.choice(np.arange(OFF_B1, OFF_W5), 60),
                               np.arange(OFF_W5, OFF_W5 + 8), [OFF_B5]])
         h = 1e-3  # float32 parameters: perturb by a representable step
@@ -116,7 +155,7 @@ def test_backward_finite_differences(orc):
             for sgn in (1, -1):
                 P2 = P.copy()
                 P2[i] = np.float32(P[i] + sgn * h)
-                vals.append(orc.mlp_loss_grad(P2, feat, y)[0])
+                vals.append(orc.mlp_loss_grad(P2, feat, y, pos_weight=w)[0])
             step = float(np.float32(P[i] + h)) - float(np.float32(P[i] - h))
             fd = (vals[0] - vals[1]) / step
             assert g[i] == pytest.approx(fd, rel=2e-3, abs=1e-7), i

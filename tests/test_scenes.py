@@ -90,3 +90,15 @@ def test_fibonacci_sets(k):
     h = scenes.fibonacci_hemisphere(k).astype(np.float64)
     assert np.all(h[:, 2] > 0)
     np.testing.assert_allclose(h[:, 2], 1.0 - (np.arange(k) + 0.5) / k, atol=1e-6)
+
+
+def test_stratified_ray_ids():
+    for n, m in ((1000, 1000), (1000, 7), (256_000_000, 1 << 20), (10, 3)):
+        ids = scenes.stratified_ray_ids(n, m, 5)
+        assert ids.dtype == np.int64 and ids.shape == (m,)
+        assert np.all(np.diff(ids) > 0) and ids[0] >= 0 and ids[-1] < n
+        j = np.arange(m)
+        assert np.all(ids >= (j * n) // m) and np.all(ids < ((j + 1) * n) // m)
+    assert scenes.stratified_ray_ids(5, 0, 1).size == 0
+    np.testing.assert_array_equal(scenes.stratified_ray_ids(1 << 20, 1000, 9),
+                                  scenes.stratified_ray_ids(1 << 20, 1000, 9))
