@@ -494,7 +494,8 @@ rt_status rt_surrogate_loss_grad(const rt_surrogate *s, const float *pos, const 
                                  rt_stream_t stream);
 /* `steps` Adam steps on samples of an implicit ray set over `bvh` (DIRS):
  * each step draws cfg.batch ray ids r uniformly (Philox4x64-10, counter
- * (i, step, 0, 0), key (seed, 1)), builds the ray as the tracer does and uses
+ * (i, step, 0, 0), key (seed, 1); r = floor(x R / 2^64) for the first output
+ * word x and R rays in the set), builds the ray as the tracer does and uses
  * T_target[r] (the traced visibility of the whole set) as the target.  Sets
  * the scene bounds from `bvh`.  loss_curve (device float32[steps], may be
  * NULL) receives each step's mean loss. */

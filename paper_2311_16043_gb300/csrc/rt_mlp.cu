@@ -14,8 +14,10 @@
 // whose prediction is within `band` of 0.5 are appended (warp-aggregated
 // atomics) to a fallback list that the tracer then resolves.
 //
-// Training (k_mlp_train): per tile, forward (activations kept in shared
-// memory), then backward with the same operands read K-major or MN-major:
+// Training (k_mlp_train, 512 threads: four warpgroups split the columns of
+// every epilogue of one 128-sample tile): per tile, forward (activations kept
+// in shared memory, weight images streamed by bulk async copies into two
+// buffers), then backward with the same operands read K-major or MN-major:
 //   dW_l += dz_l^T x_{l-1}   (M = units, N = inputs, K = samples; TMEM-resident
 //                             across the CTA's tiles for l = 2..4)
 //   dX_{l-1} = dz_l W_l      (M = samples, N = inputs, K = units)
@@ -210,10 +212,13 @@ __device__ __forceinline__ float transpose_reduce32(float (&v)[32], int lane) {
 __device__ __forceinline__ void issue_mma(uint32_t tmem_d, uint32_t a, uint32_t a_lbo, uint32_t a_sbo,
                                           uint32_t a_kstep, uint32_t b, uint32_t b_lbo, uint32_t b_sbo,
                                           uint32_t b_kstep, uint32_t idesc, int K, bool acc_first) {
-    for (int kk = 0; kk < K / 16; ++kk) {
-        tc_mma(tmem_d, tc_smem_desc(a + kk * a_kstep, a_lbo, a_sbo), tc_smem_desc(b + kk * b_kstep, b_lbo, b_sbo),
-               idesc, (kk > 0 || acc_first) ? 1u : 0u);
-    }
+    // a descriptor's start-address field is bits 0-13 (address / 16); shared
+    // addresses stay below 2^18 bytes, so stepping the address adds to the
+    // descriptor without a carry out of that field
+    const uint64_t da = tc_smem_desc(a, a_lbo, a_sbo), db = tc_smem_desc(b, b_lbo, b_sbo);
+    for (int kk = 0; kk < K / 16; ++kk)
+        tc_mma(tmem_d, da + (uint64_t)((kk * a_kstep) >> 4), db + (uint64_t)((kk * b_kstep) >> 4), idesc,
+               (kk > 0 || acc_first) ? 1u : 0u);
 }
 
 // Sample sources
@@ -241,18 +246,76 @@ __device__ __forceinline__ bool get_sample(const SampleSrc &S, int64_t i, int64_
     if (S.mode == 1) {
         rid = S.rs.ray_ids ? S.rs.ray_ids[i] : i;
     } else {
+        // uniform id in [0, R): the high 64 bits of x * R for a uniform
+        // 64-bit x (bias below R / 2^64)
         uint64_t c[4] = {(uint64_t)i, (uint64_t)S.step, 0ull, 0ull};
         philox4x64_10(c, S.seed, 1ull);
-        rid = (int64_t)(c[0] % (uint64_t)S.R);
+        rid = (int64_t)__umul64hi(c[0], (uint64_t)S.R);
     }
     if (rid < 0 || rid >= S.R) return false;  // reported by the caller's status check
-    const int64_t g = rid / S.rs.K;
-    const int32_t k = (int32_t)(rid - g * S.rs.K);
+    int64_t g;
+    int32_t k;
+    if (rid <= 0xffffffffll) {  // 32-bit division when the id fits
+        const uint32_t r32 = (uint32_t)rid, g32 = r32 / (uint32_t)S.rs.K;
+        g = g32;
+        k = (int32_t)(r32 - g32 * (uint32_t)S.rs.K);
+    } else {
+        g = rid / S.rs.K;
+        k = (int32_t)(rid - g * S.rs.K);
+    }
     const int32_t ps = S.b.rank[g];
     implicit_ray(S.rs, rid, k, g, __ldg(S.b.gauss + 4 * (int64_t)ps), p, d);
     y = S.T_target ? S.T_target[rid] : 0.0f;
     return true;
 }
+
+// The training kernel draws a sample in three steps spread over one tile
+// (see k_mlp_train): sample_index gives the ids without any load; the
+// Gaussian's sorted position, the target and then the mean arrive by
+// asynchronous copies; the ray is formed last.
+// The id of sample i without any load: ray id, Gaussian (caller order) and
+// direction index; ok = false beyond the minibatch or for an invalid id.
+struct SampleIdx {
+    int64_t rid, g;
+    int32_t k;
+    bool ok;
+};
+
+__device__ __forceinline__ SampleIdx sample_index(const SampleSrc &S, int64_t i, int64_t m) {
+    SampleIdx o;
+    o.rid = i;
+    o.g = 0;
+    o.k = 0;
+    o.ok = false;
+    if (i >= m) return o;
+    if (S.mode == 0) {
+        o.ok = true;
+        return o;
+    }
+    uint64_t c[4] = {(uint64_t)i, (uint64_t)S.step, 0ull, 0ull};
+    philox4x64_10(c, S.seed, 1ull);
+    const int64_t rid = (int64_t)__umul64hi(c[0], (uint64_t)S.R);
+    if (rid < 0 || rid >= S.R) return o;
+    if (rid <= 0xffffffffll) {
+        const uint32_t r32 = (uint32_t)rid, g32 = r32 / (uint32_t)S.rs.K;
+        o.g = g32;
+        o.k = (int32_t)(r32 - g32 * (uint32_t)S.rs.K);
+    } else {
+        o.g = rid / S.rs.K;
+        o.k = (int32_t)(rid - o.g * S.rs.K);
+    }
+    o.rid = rid;
+    o.ok = true;
+    return o;
+}
+
+// 4-byte asynchronous copy global -> shared (Ampere-style cp.async), and its
+// group commit / wait.
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 struct MlpDev {
     const float *params;  // f32 master
@@ -442,25 +505,121 @@ __global__ void __launch_bounds__(128 * INF_WG, 1) k_mlp_infer(MlpDev net, Sampl
 // ---------------------------------------------------------------------------
 // Training: forward + backward of a minibatch, per-CTA partial gradients
 // ---------------------------------------------------------------------------
-constexpr int TR_WBUF = 0;                       // 32768: one weight image
-constexpr int TR_X0 = TR_WBUF + 32768;           // 20480
+// 512 threads = 4 warpgroups on one 128-sample tile at a time: thread t owns
+// sample row r = t % 128 (TMEM lane r) and warpgroup q = t / 128 owns
+// columns [32q, 32q + 32) of every 128-wide epilogue, so each epilogue is a
+// quarter of a row per thread and 16 warps hide each other's latencies.
+// Weight images stream through two shared-memory buffers by bulk async
+// copies (cp.async.bulk, completion on an mbarrier) issued as soon as the
+// MMA that last read the buffer has finished, so each copy overlaps the next
+// MMA and epilogue.  Per tile the buffers hold, in use order,
+//   forward  L1: B0 = W1   L2: B1 = W2   L3: B0 = W3   L4: B1 = W4
+//   backward dX3: B1 = W4  dX2: B0 = W3  dX1: B1 = W2
+// and the copies are W3 -> B0 after L1, W4 -> B1 after L2, W2 -> B1 after
+// dX3 and (if another tile follows) W1 -> B0 after dX2; the next tile then
+// finds W1 in B0 and W2 in B1.  Warpgroup 3, which has neither encoding nor
+// dW1 work, draws the next tile's samples into a second sample buffer: the
+// ids while warpgroups 0-2 encode (the sorted position and the target then
+// arrive by asynchronous copies), the mean's copies after its first forward
+// epilogue and the rays while warpgroups 0-2 add the dW1 tile, so the two
+// rounds of dependent global loads never stall the tile.
+constexpr int TR_THREADS = 512;
+constexpr int TR_PSTRIDE = 60040;                // floats per partial (NPARAM + 1 rounded up to 8)
+constexpr int TR_WB0 = 0;                        // 32768: weight buffer 0
+constexpr int TR_WB1 = TR_WB0 + 32768;           // 32768: weight buffer 1
+constexpr int TR_X0 = TR_WB1 + 32768;            // 20480
 constexpr int TR_H1 = TR_X0 + 20480;             // 32768 each
 constexpr int TR_H2 = TR_H1 + 32768;
 constexpr int TR_H3 = TR_H2 + 32768;
 constexpr int TR_DZ = TR_H3 + 32768;
-constexpr int TR_F = TR_DZ + 32768;              // floats: b[4][128], w5[128], db[4][128], dw5[128], misc
-constexpr int TR_BAR = TR_F + (4 * 128 + 128 + 4 * 128 + 128 + 8) * 4;
+// floats: b[4][128], w5[128], db[4][128], dw5[128], z5 partials [4][128], misc[8]
+constexpr int TR_F = TR_DZ + 32768;
+// samples of the current and the next tile: [2][7][128] floats (p, d, y;
+// y < 0 marks a row beyond the minibatch)
+constexpr int TR_SMP = TR_F + (4 * 128 + 128 + 4 * 128 + 128 + 4 * 128 + 8) * 4;
+constexpr int TR_BAR = TR_SMP + 2 * 7 * 128 * 4;
 constexpr int TR_SMEM_TOTAL = TR_BAR + 64;
+static_assert(TR_SMEM_TOTAL <= 232448, "shared memory of the training kernel");
+static_assert(TR_PSTRIDE >= NPARAM + 1 && TR_PSTRIDE % 4 == 0, "partial stride");
 
-__device__ __forceinline__ void copy_img(uint8_t *dst, const uint8_t *src, int bytes, int t) {
-    for (int i = t; i < bytes / 16; i += 128)
-        reinterpret_cast<uint4 *>(dst)[i] = __ldg(reinterpret_cast<const uint4 *>(src) + i);
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
 }
 
-__global__ void __launch_bounds__(128, 1) k_mlp_train(MlpDev net, SampleSrc S, int64_t m, float inv_batch,
-                                                      float *partial, int *status) {
+// Bulk async copy global -> shared (16-byte aligned, size a multiple of 16);
+// completes `bytes` of transaction count on `bar`.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// 13 features of one scalar x (held as the pair xh + xl, see encode()):
+// x, then sin and cos of 2^k pi x for k = 0..5.
+__device__ __forceinline__ void encode_scalar(float xh, float xl, float *f) {
+    f[0] = xh;
+#pragma unroll
+    for (int k = 0; k < 6; k += 2) {
+        float sv, cv;
+        sincospi_k(xh, xl, k, sv, cv);
+        f[1 + 2 * k] = sv;
+        f[2 + 2 * k] = cv;
+        f[3 + 2 * k] = 2.0f * (sv * cv);
+        f[4 + 2 * k] = (cv - sv) * (cv + sv);
+    }
+}
+
+// Features [26q, 26q + 26) of row r (warpgroups 0..2: scalars 2q and 2q + 1
+// of (p_n, d)), written as bf16 pairs; warpgroup 2 also writes the two zero
+// pads (78, 79).  Same values as encode() + store_row_x0.
+__device__ __forceinline__ void encode_part(uint8_t *x0, int r, int q, bool valid, float3 p, float3 d,
+                                            const MlpDev &net) {
+    if (q > 2) return;
+    float xh[2] = {0.0f, 0.0f}, xl[2] = {0.0f, 0.0f};
+    if (valid) {
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int c = 2 * q + j;
+            if (c < 3) {
+                const float pc = c == 0 ? p.x : c == 1 ? p.y : p.z;
+                normalise_pair(pc, net.lo[c], net.eh[c], net.el[c], xh[j], xl[j]);
+            } else {
+                xh[j] = c == 3 ? d.x : c == 4 ? d.y : d.z;
+            }
+        }
+    }
+    float f[26];
+    if (valid) {
+        encode_scalar(xh[0], xl[0], f);
+        encode_scalar(xh[1], xl[1], f + 13);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 26; ++k) f[k] = 0.0f;
+    }
+#pragma unroll
+    for (int k = 0; k < 13; ++k)
+        *reinterpret_cast<uint32_t *>(x0 + img_off(r, 26 * q + 2 * k, IN)) = pack_bf16(f[2 * k], f[2 * k + 1]);
+    if (q == 2) *reinterpret_cast<uint32_t *>(x0 + img_off(r, 78, IN)) = 0u;
+}
+
+// a[0..3] += (x, y, z, w) in global memory without a return value (one
+// vector reduction; `a` 16-byte aligned).
+__device__ __forceinline__ void red_add_v4(float *a, float x, float y, float z, float w) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(a), "f"(x), "f"(y), "f"(z), "f"(w)
+                 : "memory");
+}
+
+// 32 values of row r, columns c0..c0+31, of a K-major bf16 image (kdim 128).
+__device__ __forceinline__ void load_chunk32(const uint8_t *img, int r, int c0, float (&v)[32]) {
+    load_chunk(img, r, c0, v);
+}
+
+__global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleSrc S, int64_t m, float inv_batch,
+                                                             float *partial, int *status) {
     extern __shared__ __align__(1024) uint8_t smem[];
-    uint8_t *wbuf = smem + TR_WBUF;
+    uint8_t *wb[2] = {smem + TR_WB0, smem + TR_WB1};
     uint8_t *x0 = smem + TR_X0;
     uint8_t *hb[3] = {smem + TR_H1, smem + TR_H2, smem + TR_H3};
     uint8_t *dz = smem + TR_DZ;
@@ -469,40 +628,49 @@ __global__ void __launch_bounds__(128, 1) k_mlp_train(MlpDev net, SampleSrc S, i
     float *w5 = fb + 512;         // [128]
     float *dbias = fb + 640;      // [4][128]
     float *dw5 = fb + 1152;       // [128]
-    float *misc = fb + 1280;      // [0] db5, [1] loss
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + TR_BAR);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + TR_BAR + 8);
+    float *z5p = fb + 1280;       // [4][128] per-warpgroup partial logits
+    float *misc = fb + 1792;      // [0] db5, [1] loss
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + TR_BAR);  // MMA commits
+    uint64_t *wbar = bar + 1;                                      // [2] weight copies
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + TR_BAR + 24);
+    float *smp = reinterpret_cast<float *>(smem + TR_SMP);  // [2][7][128]
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    float *part = partial + (int64_t)blockIdx.x * (NPARAM + 1);
+    const int r = t & 127, q = t >> 7, c0 = 32 * q;
+    float *part = partial + (int64_t)blockIdx.x * TR_PSTRIDE;
 
-    for (int i = t; i < 128; i += 128) {
-        bias[i] = net.params[OFF_B1 + i];
-        bias[128 + i] = net.params[OFF_B2 + i];
-        bias[256 + i] = net.params[OFF_B3 + i];
-        bias[384 + i] = net.params[OFF_B4 + i];
-        w5[i] = net.params[OFF_W5 + i];
-        dw5[i] = 0.0f;
+    if (t < 128) {
+        bias[t] = net.params[OFF_B1 + t];
+        bias[128 + t] = net.params[OFF_B2 + t];
+        bias[256 + t] = net.params[OFF_B3 + t];
+        bias[384 + t] = net.params[OFF_B4 + t];
+        w5[t] = net.params[OFF_W5 + t];
+        dw5[t] = 0.0f;
 #pragma unroll
-        for (int l = 0; l < 4; ++l) dbias[128 * l + i] = 0.0f;
+        for (int l = 0; l < 4; ++l) dbias[128 * l + t] = 0.0f;
     }
     if (t < 8) misc[t] = 0.0f;
-    for (int i = t; i < H * IN; i += 128) part[OFF_W1 + i] = 0.0f;
+    for (int i = t; i < H * IN; i += TR_THREADS) part[OFF_W1 + i] = 0.0f;
     const float b5 = net.params[OFF_B5];
-    if (t == 0) mbar_init(bar, 1);
+    if (t == 0) {
+        mbar_init(bar, 1);
+        mbar_init(wbar, 1);
+        mbar_init(wbar + 1, 1);
+    }
     if (warp == 0) tmem_alloc(tslot, 512);
+    fence_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
     const uint32_t tm_work = tmem, tm_dw[3] = {tmem + 128, tmem + 256, tmem + 384};  // dW2, dW3, dW4
-    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
-    const uint32_t s_wbuf = smem_u32(wbuf), s_x0 = smem_u32(x0), s_dz = smem_u32(dz);
+    const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
+    const uint32_t s_wb[2] = {smem_u32(wb[0]), smem_u32(wb[1])};
+    const uint32_t s_x0 = smem_u32(x0), s_dz = smem_u32(dz);
     const uint32_t s_h[3] = {smem_u32(hb[0]), smem_u32(hb[1]), smem_u32(hb[2])};
     const uint32_t id_fwd = tc_idesc_bf16(128, 128, false, false);
     const uint32_t id_dw = tc_idesc_bf16(128, 128, true, true);
     const uint32_t id_dw1 = tc_idesc_bf16(128, IN, true, true);
     const uint32_t id_dx = tc_idesc_bf16(128, 128, false, true);
-    const int img_off_l[4] = {IMG_W1, IMG_W2, IMG_W3, IMG_W4};
     uint32_t phase = 0;
     bool ok = true;
 
@@ -511,16 +679,107 @@ __global__ void __launch_bounds__(128, 1) k_mlp_train(MlpDev net, SampleSrc S, i
     const int64_t t0 = (int64_t)blockIdx.x * per;
     const int64_t t1 = t0 + per < ntiles ? t0 + per : ntiles;
 
+    // weight copies (thread 0 only): pending flags and phase bits per buffer
+    bool pend[2] = {false, false};
+    uint32_t wph[2] = {0u, 0u};
+    bool wok = true;
+    auto load_w = [&](int b, int img_off_bytes, int bytes) {
+        mbar_expect_tx(wbar + b, (uint32_t)bytes);
+        bulk_g2s(wb[b], net.img + img_off_bytes, (uint32_t)bytes, wbar + b);
+        pend[b] = true;
+    };
+    auto need_w = [&](int b) {
+        if (pend[b]) {
+            if (mbar_wait(wbar + b, wph[b], net.wait_cycles)) {
+                wph[b] ^= 1u;
+                pend[b] = false;
+            } else {
+                wok = false;
+            }
+        }
+    };
+    if (t == 0 && t1 > t0) {
+        load_w(0, IMG_W1, 20480);
+        load_w(1, IMG_W2, 32768);
+    }
+    // row r's sample of tile `tile` into sample buffer b (warpgroup 3), in
+    // three stages: ids (slots 0, 1: ray id; 3: direction index; 2: sorted
+    // position and 6: target by asynchronous copy), the mean (slots 4, 5, 2
+    // by asynchronous copy), the ray (slots 0-5)
+    auto draw_ids = [&](int64_t tile, int b) {
+        float *o = smp + b * 7 * 128 + r;
+        const SampleIdx a = sample_index(S, tile * 128 + r, m);
+        o[0] = __int_as_float((int)(a.rid & 0xffffffff));
+        o[128] = __int_as_float((int)(a.rid >> 32));
+        o[384] = __int_as_float(a.k);
+        if (a.ok) {
+            // the Gaussian's sorted position and the target land in shared
+            // memory asynchronously; draw_ray waits for them
+            if (S.mode != 0) cp_async4(o + 256, S.b.rank + a.g);
+            if (S.mode == 0 ? S.y != nullptr : S.T_target != nullptr)
+                cp_async4(o + 768, S.mode == 0 ? S.y + a.rid : S.T_target + a.rid);
+            else
+                o[768] = 0.0f;
+            cp_async_commit();
+        } else {
+            o[768] = -1.0f;
+        }
+    };
+    // second stage: the sorted position has landed; the Gaussian's mean
+    // follows by three asynchronous copies into slots 4, 5 and 2
+    auto draw_mean = [&](int b) {
+        cp_async_wait_all();
+        float *o = smp + b * 7 * 128 + r;
+        if (S.mode != 0 && o[768] >= 0.0f) {
+            const float *mu = reinterpret_cast<const float *>(S.b.gauss + 4 * (int64_t)__float_as_int(o[256]));
+            cp_async4(o + 512, mu);
+            cp_async4(o + 640, mu + 1);
+            cp_async4(o + 256, mu + 2);
+            cp_async_commit();
+        }
+    };
+    // third stage: the ray
+    auto draw_ray = [&](int b) {
+        cp_async_wait_all();
+        float *o = smp + b * 7 * 128 + r;
+        const int64_t rid = (int64_t)(uint32_t)__float_as_int(o[0]) | ((int64_t)__float_as_int(o[128]) << 32);
+        float3 p = make_float3(0.f, 0.f, 0.f), d = make_float3(0.f, 0.f, 1.f);
+        if (o[768] >= 0.0f) {
+            if (S.mode == 0) {
+                p = make_float3(S.pos[3 * rid], S.pos[3 * rid + 1], S.pos[3 * rid + 2]);
+                d = make_float3(S.dir[3 * rid], S.dir[3 * rid + 1], S.dir[3 * rid + 2]);
+            } else {
+                const int64_t g = S.rs.kind == RT_RAYS_HEMI ? rid / S.rs.K : 0;  // only hemisphere sets use it
+                implicit_ray(S.rs, rid, __float_as_int(o[384]), g, make_float4(o[512], o[640], o[256], 0.0f), p,
+                             d);
+            }
+        }
+        o[0] = p.x;
+        o[128] = p.y;
+        o[256] = p.z;
+        o[384] = d.x;
+        o[512] = d.y;
+        o[640] = d.z;
+    };
+    if (q == 3 && t1 > t0) {
+        draw_ids(t0, 0);
+        draw_mean(0);
+        draw_ray(0);
+    }
+    __syncthreads();
+
     auto sync_mma = [&]() {
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
     };
-    // every thread waits, then the CTA agrees (one vote), so a wait that
-    // gives up in one thread takes the whole CTA out together, after the
-    // committed MMAs have finished (default bound)
+    // every thread waits, then the CTA agrees (one vote; thread 0 also votes
+    // on its weight copies), so a wait that gives up anywhere takes the whole
+    // CTA out together, after the committed MMAs have finished
     auto wait_mma = [&]() {
-        if (!__syncthreads_and(mbar_wait(bar, phase, net.wait_cycles) ? 1 : 0)) {
+        bool mine = mbar_wait(bar, phase, net.wait_cycles);
+        if (t == 0) mine = mine && wok;
+        if (!__syncthreads_and(mine ? 1 : 0)) {
             mbar_wait(bar, phase, WAIT_CYCLES);
             if (t == 0) rt_set_error(status, RT_ERR_TIMEOUT);
             ok = false;
@@ -531,61 +790,67 @@ __global__ void __launch_bounds__(128, 1) k_mlp_train(MlpDev net, SampleSrc S, i
 
     for (int64_t tile = t0; tile < t1 && ok; ++tile) {
         const bool first = tile == t0;
-        const int64_t i = tile * 128 + t;
-        float3 p = make_float3(0.f, 0.f, 0.f), d = make_float3(0.f, 0.f, 1.f);
-        float y = 0.0f;
-        int64_t rid;
-        const bool valid = get_sample(S, i, m, p, d, y, rid);
-        {
-            float f[IN];
-            if (valid) encode(p, d, net.lo, net.eh, net.el, f);
-            else
-#pragma unroll
-                for (int k = 0; k < IN; ++k) f[k] = 0.0f;
-            store_row_x0(x0, t, f);
+        const int sb = (int)((tile - t0) & 1);
+        const float *smr = smp + sb * 7 * 128 + r;
+        const float y = smr[768];
+        const bool valid = y >= 0.0f;
+        if (q < 3) {
+            encode_part(x0, r, q, valid, make_float3(smr[0], smr[128], smr[256]),
+                        make_float3(smr[384], smr[512], smr[640]), net);
+        } else if (tile + 1 < t1) {
+            draw_ids(tile + 1, sb ^ 1);  // completed in this tile's dW1 phase
         }
-        // ---- forward ----
-        float z5 = b5;
+        // ---- forward: layer l reads x_l (x0, h1, h2, h3) and W_{l+1} ----
+        float h4[32];
+#pragma unroll
         for (int l = 0; l < 4; ++l) {
-            copy_img(wbuf, net.img + img_off_l[l], l == 0 ? 20480 : 32768, t);
             sync_mma();
             if (t == 0) {
                 tc_fence_after();
-                const int K = l == 0 ? IN : H;
-                const uint32_t sbo = (uint32_t)(K / 8 * 128);
-                const uint32_t a = l == 0 ? s_x0 : s_h[l - 1];
-                issue_mma(tm_work, a, 128, sbo, 256, s_wbuf, 128, sbo, 256, id_fwd, K, false);
+                const int b = l & 1;
+                need_w(b);
+                if (wok) {
+                    const int K = l == 0 ? IN : H;
+                    const uint32_t sbo = (uint32_t)(K / 8 * 128);
+                    const uint32_t a = l == 0 ? s_x0 : s_h[l - 1];
+                    issue_mma(tm_work, a, 128, sbo, 256, s_wb[b], 128, sbo, 256, id_fwd, K, false);
+                }
                 tc_commit(bar);
             }
             wait_mma();
             if (!ok) break;
-            const float *bl = bias + 128 * l;
+            if (t == 0) {
+                if (l == 0) load_w(0, IMG_W3, 32768);  // W1 read: B0 takes W3
+                if (l == 1) load_w(1, IMG_W4, 32768);  // W2 read: B1 takes W4
+            }
+            const float *bl = bias + 128 * l + c0;
+            float v[32];
+            tmem_ld32(tm_work + lane_off + c0, v);
             if (l < 3) {
-#pragma unroll 1
-                for (int cc = 0; cc < 4; ++cc) {
-                    float v[32];
-                    tmem_ld32(tm_work + lane_off + 32 * cc, v);
 #pragma unroll
-                    for (int k = 0; k < 32; ++k) v[k] = fmaxf(v[k] + bl[32 * cc + k], 0.0f);
-                    store_chunk(hb[l], t, 32 * cc, v);
-                }
+                for (int k = 0; k < 32; ++k) v[k] = fmaxf(v[k] + bl[k], 0.0f);
+                store_chunk(hb[l], r, c0, v);
+                if (l == 0 && q == 3 && tile + 1 < t1) draw_mean(sb ^ 1);
             } else {
-#pragma unroll 1
-                for (int cc = 0; cc < 4; ++cc) {
-                    float v[32];
-                    tmem_ld32(tm_work + lane_off + 32 * cc, v);
+                float zp = 0.0f;
 #pragma unroll
-                    for (int k = 0; k < 32; ++k) z5 = fmaf(w5[32 * cc + k], bf16_round(fmaxf(v[k] + bl[32 * cc + k], 0.0f)), z5);
+                for (int k = 0; k < 32; ++k) {
+                    h4[k] = bf16_round(fmaxf(v[k] + bl[k], 0.0f));
+                    zp = fmaf(w5[c0 + k], h4[k], zp);
                 }
+                z5p[128 * q + r] = zp;
             }
         }
         if (!ok) break;
-        // ---- loss and output layer ----
+        __syncthreads();
+        // ---- loss and output layer (every warpgroup computes the row's
+        // logit from the four partials in the same order) ----
         // L = -(w y log p + (1 - y) log(1 - p)), dL/dz = p (1 + (w - 1) y) - w y
+        const float z5 = b5 + ((z5p[r] + z5p[128 + r]) + (z5p[256 + r] + z5p[384 + r]));
         const float pr = 1.0f / (1.0f + expf(-z5));
         const float wy = net.pos_w * y;
         const float dz5 = valid ? (pr * (wy + 1.0f - y) - wy) * inv_batch : 0.0f;
-        {
+        if (q == 3) {  // the warpgroup with no encoding and no dW1 work
             float lv = valid ? (wy * (fmaxf(-z5, 0.0f) + log1pf(expf(-fabsf(z5)))) +
                                 (1.0f - y) * (fmaxf(z5, 0.0f) + log1pf(expf(-fabsf(z5))))) * inv_batch
                              : 0.0f;
@@ -600,49 +865,51 @@ __global__ void __launch_bounds__(128, 1) k_mlp_train(MlpDev net, SampleSrc S, i
             }
         }
         // dz4 = bf16(dz5 * w5 * [h4 > 0]); dw5 += dz5 * h4; db4 += dz4
-#pragma unroll 1
-        for (int cc = 0; cc < 4; ++cc) {
-            float v[32], g[32], h4[32];
-            tmem_ld32(tm_work + lane_off + 32 * cc, v);
+        {
+            float g[32];
 #pragma unroll
             for (int k = 0; k < 32; ++k) {
-                h4[k] = bf16_round(fmaxf(v[k] + bias[384 + 32 * cc + k], 0.0f));
-                g[k] = h4[k] > 0.0f ? bf16_round(dz5 * w5[32 * cc + k]) : 0.0f;
+                g[k] = h4[k] > 0.0f ? bf16_round(dz5 * w5[c0 + k]) : 0.0f;
                 h4[k] *= dz5;
             }
-            store_chunk(dz, t, 32 * cc, g);
-            atomicAdd(dw5 + 32 * cc + lane, transpose_reduce32(h4, lane));
-            atomicAdd(dbias + 384 + 32 * cc + lane, transpose_reduce32(g, lane));
+            store_chunk(dz, r, c0, g);
+            atomicAdd(dw5 + c0 + lane, transpose_reduce32(h4, lane));
+            atomicAdd(dbias + 384 + c0 + lane, transpose_reduce32(g, lane));
         }
-        // ---- backward through layers 4, 3, 2 ----
+        // ---- backward through layers 4, 3, 2: dz_{l+1} (dz or h_{l+1}'s
+        // buffer) and W_{l+1} (B1, B0, B1) ----
+#pragma unroll
         for (int l = 3; l >= 1; --l) {
-            // W_{l+1} is in wbuf (l == 3: still loaded from the forward)
-            if (l < 3) copy_img(wbuf, net.img + img_off_l[l], 32768, t);
             sync_mma();
             if (t == 0) {
                 tc_fence_after();
-                const uint32_t s_dzl = l == 3 ? s_dz : s_h[l];  // dz_{l+1} lives in h_{l+1}'s buffer below layer 4
-                // dW_{l+1} += dz^T x_l : A = dz (MN-major), B = h_l (MN-major), K = samples
-                issue_mma(tm_dw[l - 1], s_dzl, 2048, 128, 4096, s_h[l - 1], 2048, 128, 4096, id_dw, 128,
-                          !first);
-                // dX_l = dz W_{l+1} : A = dz (K-major), B = W (MN-major), K = units
-                issue_mma(tm_work, s_dzl, 128, 2048, 256, s_wbuf, 2048, 128, 4096, id_dx, 128, false);
+                const int b = l == 2 ? 0 : 1;
+                need_w(b);
+                if (wok) {
+                    const uint32_t s_dzl = l == 3 ? s_dz : s_h[l];
+                    // dW_{l+1} += dz^T x_l : A = dz (MN-major), B = h_l (MN-major), K = samples
+                    issue_mma(tm_dw[l - 1], s_dzl, 2048, 128, 4096, s_h[l - 1], 2048, 128, 4096, id_dw, 128,
+                              !first);
+                    // dX_l = dz W_{l+1} : A = dz (K-major), B = W (MN-major), K = units
+                    issue_mma(tm_work, s_dzl, 128, 2048, 256, s_wb[b], 2048, 128, 4096, id_dx, 128, false);
+                }
                 tc_commit(bar);
             }
             wait_mma();
             if (!ok) break;
+            if (t == 0) {
+                if (l == 3) load_w(1, IMG_W2, 32768);                     // W4 read: B1 takes W2
+                if (l == 2 && tile + 1 < t1) load_w(0, IMG_W1, 20480);    // W3 read: B0 takes W1
+            }
             // dz_l = bf16(dX_l * [h_l > 0]) written over h_l; db_l += dz_l
             uint8_t *hl = hb[l - 1];
-#pragma unroll 1
-            for (int cc = 0; cc < 4; ++cc) {
-                float v[32], h[32];
-                tmem_ld32(tm_work + lane_off + 32 * cc, v);
-                load_chunk(hl, t, 32 * cc, h);
+            float v[32], h[32];
+            tmem_ld32(tm_work + lane_off + c0, v);
+            load_chunk32(hl, r, c0, h);
 #pragma unroll
-                for (int k = 0; k < 32; ++k) v[k] = h[k] > 0.0f ? bf16_round(v[k]) : 0.0f;
-                store_chunk(hl, t, 32 * cc, v);
-                atomicAdd(dbias + 128 * (l - 1) + 32 * cc + lane, transpose_reduce32(v, lane));
-            }
+            for (int k = 0; k < 32; ++k) v[k] = h[k] > 0.0f ? bf16_round(v[k]) : 0.0f;
+            store_chunk(hl, r, c0, v);
+            atomicAdd(dbias + 128 * (l - 1) + c0 + lane, transpose_reduce32(v, lane));
         }
         if (!ok) break;
         // ---- dW1 = dz1^T x0 (per tile, added to this CTA's partial) ----
@@ -654,22 +921,32 @@ __global__ void __launch_bounds__(128, 1) k_mlp_train(MlpDev net, SampleSrc S, i
         }
         wait_mma();
         if (!ok) break;
-        {
+        // fire-and-forget vector adds: each address of this CTA's partial
+        // is only ever added to by this thread, in tile order, so the sums
+        // are deterministic; warpgroup 3 has no dW1 columns
+        if (q < 2) {
+            float *row = part + OFF_W1 + (int64_t)r * IN + c0;
             float v[32];
-            float *row = part + OFF_W1 + (int64_t)t * IN;
-#pragma unroll 1
-            for (int cc = 0; cc < 2; ++cc) {
-                tmem_ld32(tm_work + lane_off + 32 * cc, v);
+            tmem_ld32(tm_work + lane_off + c0, v);
 #pragma unroll
-                for (int k = 0; k < 32; ++k) row[32 * cc + k] += v[k];
-            }
-            float w[16];
-            tmem_ld16(tm_work + lane_off + 64, w);
+            for (int k = 0; k < 8; ++k) red_add_v4(row + 4 * k, v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+        } else if (q == 2) {
+            float *row = part + OFF_W1 + (int64_t)r * IN + c0;
+            float v[16];
+            tmem_ld16(tm_work + lane_off + c0, v);
 #pragma unroll
-            for (int k = 0; k < 16; ++k) row[64 + k] += w[k];
+            for (int k = 0; k < 4; ++k) red_add_v4(row + 4 * k, v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+        } else if (tile + 1 < t1) {
+            draw_ray(sb ^ 1);  // the next tile's rays, read after its first barrier
         }
         tc_fence_before();
         __syncthreads();
+    }
+    // weight copies still in flight (only after a give-up): let them land
+    if (t == 0) {
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+            if (pend[b]) mbar_wait(wbar + b, wph[b], WAIT_CYCLES);
     }
     // ---- flush this CTA's partial gradient ----
     tc_fence_before();
@@ -679,21 +956,22 @@ __global__ void __launch_bounds__(128, 1) k_mlp_train(MlpDev net, SampleSrc S, i
     const int offW[3] = {OFF_W2, OFF_W3, OFF_W4};
 #pragma unroll 1
     for (int l = 0; l < 3; ++l) {
-        float *row = part + offW[l] + (int64_t)t * H;
-#pragma unroll 1
-        for (int cc = 0; cc < 4; ++cc) {
-            float v[32];
-            tmem_ld32(tm_dw[l] + lane_off + 32 * cc, v);
+        float4 *row = reinterpret_cast<float4 *>(part + offW[l] + (int64_t)r * H + c0);
+        float v[32];
+        tmem_ld32(tm_dw[l] + lane_off + c0, v);
 #pragma unroll
-            for (int k = 0; k < 32; ++k) row[32 * cc + k] = any ? v[k] : 0.0f;
-        }
+        for (int k = 0; k < 8; ++k)
+            row[k] = any ? make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3])
+                         : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
-    part[OFF_B1 + t] = dbias[t];
-    part[OFF_B2 + t] = dbias[128 + t];
-    part[OFF_B3 + t] = dbias[256 + t];
-    part[OFF_B4 + t] = dbias[384 + t];
-    part[OFF_W5 + t] = dw5[t];
+    if (t < 128) {
+        part[OFF_B1 + t] = dbias[t];
+        part[OFF_B2 + t] = dbias[128 + t];
+        part[OFF_B3 + t] = dbias[256 + t];
+        part[OFF_B4 + t] = dbias[384 + t];
+        part[OFF_W5 + t] = dw5[t];
+    }
     if (t == 0) {
         part[OFF_B5] = misc[0];
         part[NPARAM] = misc[1];
@@ -711,7 +989,9 @@ __global__ void k_mlp_reduce_adam(const float *partial, int nparts, float *grad_
                                   float b2, float eps, float c1, float c2, int adam) {
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q <= NPARAM; q += gridDim.x * blockDim.x) {
         float g = 0.0f;
-        for (int c = 0; c < nparts; ++c) g += partial[(int64_t)c * (NPARAM + 1) + q];
+        // loads run ahead of the (sequential, fixed-order) sum
+#pragma unroll 8
+        for (int c = 0; c < nparts; ++c) g += partial[(int64_t)c * TR_PSTRIDE + q];
         if (q == NPARAM) {
             if (loss_out) *loss_out = g;
             continue;
@@ -783,7 +1063,7 @@ struct rt_surrogate {
     void *block;
     float *params, *adam_m, *adam_v;
     uint8_t *img;
-    float *partial;  // [nparts][NPARAM+1]
+    float *partial;  // [nparts][TR_PSTRIDE]
     int nparts;
     float *scratch;  // [NPARAM+1] misc device scratch
 };
@@ -829,7 +1109,8 @@ rt_status train_launch(const rt_surrogate *s, const SampleSrc &S, int64_t m, flo
     int64_t ntiles = (m + 127) / 128;
     int grid = (int)(ntiles < s->nparts ? ntiles : s->nparts);
     if (grid < 1) grid = 1;
-    k_mlp_train<<<grid, 128, TR_SMEM_TOTAL, st>>>(mlp_dev(s), S, m, inv_batch, s->partial, rt_status_ptr());
+    k_mlp_train<<<grid, TR_THREADS, TR_SMEM_TOTAL, st>>>(mlp_dev(s), S, m, inv_batch, s->partial,
+                                                         rt_status_ptr());
     RT_TRY(rt_check_launch());
     return RT_OK;
 }
@@ -874,6 +1155,7 @@ extern "C" rt_status rt_surrogate_create(const rt_mlp_cfg *cfg, uint64_t seed, r
     }
     s->nparts = rt_num_sms();
     const size_t pbytes = ((size_t)(NPARAM + 1) * 4 + 255) & ~(size_t)255;
+    static_assert((((size_t)(NPARAM + 1) * 4 + 255) & ~(size_t)255) >= (size_t)TR_PSTRIDE * 4, "partial rows");
     const size_t total = 3 * pbytes + IMG_BYTES + (size_t)s->nparts * pbytes + pbytes;
     rt_status r = rt_alloc(&s->block, total, stream);
     if (r != RT_OK) {
@@ -887,7 +1169,7 @@ extern "C" rt_status rt_surrogate_create(const rt_mlp_cfg *cfg, uint64_t seed, r
     s->img = (uint8_t *)(b + 3 * pbytes);
     s->partial = (float *)(b + 3 * pbytes + IMG_BYTES);
     s->scratch = (float *)(b + 3 * pbytes + IMG_BYTES + (size_t)s->nparts * pbytes);
-    // partial rows are NPARAM+1 floats apart
+    // partial rows are TR_PSTRIDE floats apart (pbytes >= 4 * TR_PSTRIDE)
     k_mlp_init<<<64, 256, 0, st>>>(s->params, seed);
     k_fill<<<64, 256, 0, st>>>(s->adam_m, NPARAM, 0.f);
     k_fill<<<64, 256, 0, st>>>(s->adam_v, NPARAM, 0.f);

@@ -201,7 +201,8 @@ def small_trace(orc):
 
 def test_one_adam_step_matches_oracle(orc, small_trace):
     """One training step: the minibatch is re-drawn on the CPU from the
-    oracle's own Philox4x64-10 (counter (i, step, 0, 0), key (seed, 1)), the
+    oracle's own Philox4x64-10 (counter (i, step, 0, 0), key (seed, 1); ray
+    id = floor(x R / 2^64) of the first output word x), the
     targets are the oracle's T, and the expected update is the oracle's Adam
     step on the oracle's gradient."""
     from paper_2311_16043_gb300 import rt
@@ -219,7 +220,7 @@ def test_one_adam_step_matches_oracle(orc, small_trace):
     P1 = rt.rt_surrogate_get_params(s).cpu().numpy().astype(np.float64)
     torch.cuda.synchronize()
     R = 4096 * 32
-    rid = np.array([int(orc.philox([i, 0, 0, 0], [seed, 1])[0]) % R for i in range(B)], np.int64)
+    rid = np.array([(int(orc.philox([i, 0, 0, 0], [seed, 1])[0]) * R) >> 64 for i in range(B)], np.int64)
     info = bvh.info()
     lo, hi = np.array(info["lo"], np.float32), np.array(info["hi"], np.float32)
     feat = orc.mlp_encode(o[rid], d[rid], lo, hi)
