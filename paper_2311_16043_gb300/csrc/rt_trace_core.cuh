@@ -456,18 +456,22 @@ __device__ __forceinline__ float trace_wide(const BvhDev &b, float3 o, float3 d,
         const uint32_t m1 = (r1 & RT_LEAF_BIT) ? 0u : __ballot_sync(FULL, h1) & alive;
         const uint32_t m2 = (r2 & RT_LEAF_BIT) ? 0u : __ballot_sync(FULL, h2) & alive;
         const uint32_t m3 = (r3 & RT_LEAF_BIT) ? 0u : __ballot_sync(FULL, h3) & alive;
-        uint32_t nn = 0, nm = 0;
-        int npush = 0;
-        int2 push[3];
-        if (m0) { nn = r0; nm = m0; }
-        if (m1) { if (nm) push[npush++] = make_int2((int)r1, (int)m1); else { nn = r1; nm = m1; } }
-        if (m2) { if (nm) push[npush++] = make_int2((int)r2, (int)m2); else { nn = r2; nm = m2; } }
-        if (m3) { if (nm) push[npush++] = make_int2((int)r3, (int)m3); else { nn = r3; nm = m3; } }
+        // the first needed child is visited next; the others are pushed in
+        // slot order (popped last-first).  Lane c (< 4) holds child c, so
+        // the pushes are one compaction, with no indexed local array.
+        const uint32_t ml = lane == 0 ? m0 : lane == 1 ? m1 : lane == 2 ? m2 : m3;
+        const uint32_t rl = lane == 0 ? r0 : lane == 1 ? r1 : lane == 2 ? r2 : r3;
+        const uint32_t need = __ballot_sync(FULL, lane < 4 && ml != 0u);
+        const int first = __ffs(need) - 1;
+        const uint32_t nn = first == 0 ? r0 : first == 1 ? r1 : first == 2 ? r2 : r3;
+        const uint32_t nm = first == 0 ? m0 : first == 1 ? m1 : first == 2 ? m2 : first == 3 ? m3 : 0u;
+        const uint32_t pushm = need & (need - 1u);  // all but the first
+        const int npush = __popc(pushm);
         if (sp + npush > RT_WIDE_STACK) {
             rt_set_error(status, RT_ERR_STACK_OVERFLOW);
             break;
         }
-        if (lane < npush) stk[sp + lane] = lane == 0 ? push[0] : lane == 1 ? push[1] : push[2];
+        if ((pushm >> lane) & 1u) stk[sp + __popc(pushm & ((1u << lane) - 1u))] = make_int2((int)rl, (int)ml);
         sp += npush;
         __syncwarp();
         if (nm) {
