@@ -79,6 +79,7 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-pbr", action="store_true")
     ap.add_argument("--no-refit", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 16-scene batch section of the default line")
     ap.add_argument("--surrogate-steps", type=int, default=2000)
     ap.add_argument("--band", type=float, default=0.3)
     ap.add_argument("--pos-weight", type=float, default=4.0,
@@ -492,13 +493,11 @@ def run_adjoint(rt, torch, dev):
     return out
 
 
-def run_batch(args, rank, world, local, torch, dist, rt):
-    """Batched multi-scene workload: every scene's BVH is built, then one
-    graph-captured persistent launch traces all scenes' direction and
-    env-map rays; a step is one replay of that graph."""
+def batch_setup(name, torch, rt, dev, autotune=True):
+    """Every scene's BVH, the DIRS and ENV jobs over them and the batch (one
+    graph-captured persistent launch over all jobs)."""
     import scenes
-    dev = torch.device("cuda", local)
-    scs, dirs_np = make_scene(args.workload)
+    scs, dirs_np = make_scene(name)
     env = scenes.envmap(399)
     E = rt.rt_envmap_create(env["radiance"], env["solid_angle"], env["corners"])
     dirs = torch.from_numpy(dirs_np).to(dev)
@@ -519,8 +518,89 @@ def run_batch(args, rank, world, local, torch, dist, rt):
             jobs.append((bvh, rs, torch.empty(rt.rt_rayspec_count(bvh, rs), dtype=torch.float32, device=dev)))
             specs.append((kind, mk))
     t0 = time.perf_counter()
-    batch = rt.rt_batch_create(jobs, autotune=True)
+    batch = rt.rt_batch_create(jobs, autotune=autotune)
     create_s = time.perf_counter() - t0
+    return {"E": E, "dirs": dirs, "jobs": jobs, "bvhs": bvhs, "specs": specs, "batch": batch,
+            "build_ms": build_ms, "create_s": create_s}
+
+
+def batch_ray_stats(B, torch, rt, dev, sample=1 << 16):
+    """Outside the timed region: per ray kind, the early-exit fraction over
+    every output, and per-ray work (child-box tests, Gaussian tests, accepted
+    hits) counted on `sample` seeded rays of each job with the per-ray 4-wide
+    traversal, which does each ray's minimal work; the work estimate of the
+    whole batch in the bench's byte model (28 B per box test, 40 B per
+    Gaussian test, 16 B per ray) from those per-job averages."""
+    import scenes
+    stats, alg_bytes = {}, 0.0
+    for kind in ("dirs", "env"):
+        rays = zeros = box = gauss = hits = sampled = 0
+        for (bvh, _, T), (k2, mk) in zip(B["jobs"], B["specs"]):
+            if k2 != kind:
+                continue
+            rays += T.numel()
+            zeros += int((T == 0).sum())
+            ids = torch.from_numpy(scenes.sample_ray_ids(T.numel(), min(sample, T.numel()), 5)).to(dev)
+            cnt = torch.zeros(4, dtype=torch.int64, device=dev)
+            rt.rt_trace_visibility(bvh, mk(ids), opts=rt.trace_opts(kernel=rt.RT_KERNEL_RAY_WIDE, counters=cnt))
+            c = [int(x) for x in cnt.cpu()]
+            m = ids.numel()
+            alg_bytes += T.numel() * (28.0 * c[0] / m + 40.0 * c[1] / m + 16.0)
+            box, gauss, hits, sampled = box + c[0], gauss + c[1], hits + c[2], sampled + m
+        stats[kind] = {"rays": rays, "early_exit_fraction": zeros / max(rays, 1),
+                       "box_tests_per_ray": box / max(sampled, 1), "gaussian_tests_per_ray": gauss / max(sampled, 1),
+                       "accepted_hits_per_ray": hits / max(sampled, 1)}
+    return stats, alg_bytes
+
+
+def batch_destroy(B):
+    B["batch"].destroy()
+    for bvh, _ in B["bvhs"]:
+        bvh.destroy()
+    B["E"].destroy()
+
+
+def run_batch_section(args, torch, rt, dev):
+    """The batch workload inside the default bench line: one warm-up replay
+    and one timed replay of the object-scale 16-scene batch, with the
+    roofline of its one persistent launch."""
+    name = "batch16_objects_k128_env512"
+    B = batch_setup(name, torch, rt, dev)
+    info = B["batch"].info()
+    B["batch"].run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    e0.record()
+    B["batch"].run()
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    stats, alg = batch_ray_stats(B, torch, rt, dev)
+    pk, pk_kind = peaks()
+    R = info["n_rays"]
+    out = {"workload": name, "rays": R, "ms": ms, "rays_per_s": R / (ms / 1000.0), "warmup": 1, "steps": 1,
+           "scene_sizes": [b.n for b, _ in B["bvhs"]], "build_ms_all_scenes": B["build_ms"],
+           "batch_create_s": B["create_s"], "strategy_per_job": info["kernel"], "ray_stats": stats,
+           "roofline": {"bound": "hbm", "achieved": alg / (ms / 1000.0) / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                        "frac": alg / (ms / 1000.0) / 1e9 / pk["hbm_gbs"], "peak_kind": pk_kind,
+                        "algorithmic_bytes_per_launch": alg, "kernel": "k_trace_batch (one persistent launch)",
+                        "bytes_model": "28 B per child-box test + 40 B per Gaussian test + 16 B per ray; per-ray "
+                                       "counts from 2^16 sampled rays per job (per-ray 4-wide traversal)"},
+           "clocks": clk}
+    batch_destroy(B)
+    return out
+
+
+def run_batch(args, rank, world, local, torch, dist, rt):
+    """Batched multi-scene workload: every scene's BVH is built, then one
+    graph-captured persistent launch traces all scenes' direction and
+    env-map rays; a step is one replay of that graph."""
+    dev = torch.device("cuda", local)
+    B = batch_setup(args.workload, torch, rt, dev)
+    batch = B["batch"]
     info = batch.info()
     R = info["n_rays"]
     for _ in range(args.warmup):
@@ -540,37 +620,26 @@ def run_batch(args, rank, world, local, torch, dist, rt):
         ms.append(e0.elapsed_time(e1))
     clk = clocks.stop()
     m = reduce_max(statistics.mean(ms), world, dev)
-    # ray statistics (outside the timed region): the early-exit fraction over
-    # every output, accepted hits per ray from a counted trace of 2^18 sampled
-    # rays per job
-    stats = {}
-    for kind in ("dirs", "env"):
-        rays = zeros = hits = sampled = 0
-        for (bvh, _, T), (k2, mk) in zip(jobs, specs):
-            if k2 != kind:
-                continue
-            rays += T.numel()
-            zeros += int((T == 0).sum())
-            ids = torch.from_numpy(scenes.sample_ray_ids(T.numel(), 1 << 18, 5)).to(dev)
-            cnt = torch.zeros(4, dtype=torch.int64, device=dev)
-            rt.rt_trace_visibility(bvh, mk(ids), opts=rt.trace_opts(counters=cnt))
-            hits += int(cnt[2])
-            sampled += ids.numel()
-        stats[kind] = {"rays": rays, "early_exit_fraction": zeros / max(rays, 1),
-                       "accepted_hits_per_ray": hits / max(sampled, 1)}
+    stats, alg = batch_ray_stats(B, torch, rt, dev)
+    pk, pk_kind = peaks()
     if rank == 0:
+        achieved = alg / (statistics.mean(ms) / 1000.0) / 1e9
         line = {"metric": METRIC, "value": replica_rate(R, m, world), "unit": "rays/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": m, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": workload_config(args.workload, {
-                    "rays_per_step": R, "work_items": info["n_items"], "build_ms_all_scenes": build_ms,
-                    "batch_create_s": create_s, "strategy_per_job": info["kernel"],
+                    "rays_per_step": R, "work_items": info["n_items"], "build_ms_all_scenes": B["build_ms"],
+                    "batch_create_s": B["create_s"], "strategy_per_job": info["kernel"],
                     "order_block_per_job": info["order_block"],
-                    "scene_sizes": [b.n for b, _ in bvhs], "ray_stats": stats}),
+                    "scene_sizes": [b.n for b, _ in B["bvhs"]], "ray_stats": stats}),
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                             "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_kind": pk_kind,
+                             "algorithmic_bytes_per_launch": alg, "kernel": "k_trace_batch (one persistent launch)",
+                             "bytes_model": "28 B per child-box test + 40 B per Gaussian test + 16 B per ray; "
+                                            "per-ray counts from 2^16 sampled rays per job"},
                 "cpu_baseline": None, "e2e": None, "gpu_launches": args.steps, "clocks": clk}
         print(json.dumps(line), flush=True)
-    batch.destroy()
-    E.destroy()
+    batch_destroy(B)
 
 
 def run_composed(args, rank, world, local, torch, dist, rt):
@@ -763,11 +832,32 @@ def main():
         c1.record()
         torch.cuda.synchronize()
         d2h_probe_ms = c0.elapsed_time(c1)
+        # the same steps as the call, one at a time through the binding, each
+        # timed on the stream (after one more L2 flush): if e2e exceeds their
+        # sum, the difference is in the call itself (its allocations)
+        flush.fill_(-1.0)
+        pe = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        pe[0].record()
+        dd = {k: v.to(dev, non_blocking=True) for k, v in host.items()}
+        ddirs = hdirs.to(dev, non_blocking=True)
+        pe[1].record()
+        pbvh = rt.rt_build_bvh(dd["mean"], dd["scale"], dd["quat"], dd["opacity"], prm)
+        pe[2].record()
+        rt.rt_trace_visibility_dirs(pbvh, ddirs, T, opts)
+        pe[3].record()
+        hT.copy_(T, non_blocking=True)
+        pe[4].record()
+        torch.cuda.synchronize()
+        pbvh.destroy()
+        phases = {"h2d_ms": pe[0].elapsed_time(pe[1]), "build_ms": pe[1].elapsed_time(pe[2]),
+                  "trace_ms": pe[2].elapsed_time(pe[3]), "d2h_ms": pe[3].elapsed_time(pe[4])}
+        phases["sum_ms"] = sum(phases.values())
         em = reduce_max(statistics.mean(e_ms), world, dev)
         e2e = {"value": replica_rate(R, em, world), "unit": "rays/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "ms_per_step": em,
+               "d2h_bytes_per_step": d2h, "ms_per_step": em, "ms_each": e_ms,
                "call": "rt_visibility_dirs_host (C ABI) from page-locked host buffers", "clocks": e_clk,
-               "d2h_copy_probe": {"ms": d2h_probe_ms, "gbs": d2h / d2h_probe_ms / 1e6}}
+               "d2h_copy_probe": {"ms": d2h_probe_ms, "gbs": d2h / d2h_probe_ms / 1e6},
+               "phases_through_binding": phases}
 
     surrogate = None
     if not args.no_surrogate and rank == 0:
@@ -781,6 +871,11 @@ def main():
     refit = None
     if not args.no_refit and rank == 0:
         refit = run_refit(rt, torch, d, sc, dirs, opts, dev)
+    batch_sec = None
+    if not args.no_batch and rank == 0:
+        del T
+        torch.cuda.empty_cache()
+        batch_sec = run_batch_section(args, torch, rt, dev)
 
     pk, pk_kind = peaks()
     tr_ms = statistics.mean(trace_ms)
@@ -811,7 +906,8 @@ def main():
                     "kernel": KERNEL_NAMES[args.kernel]}),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": (BUILD_KERNELS_PER_STEP + 1) * args.steps,
-                "clocks": clk, "surrogate": surrogate, "adjoint": adjoint, "pbr": pbr, "refit": refit}
+                "clocks": clk, "surrogate": surrogate, "adjoint": adjoint, "pbr": pbr, "refit": refit,
+                "batch": batch_sec}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
