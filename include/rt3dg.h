@@ -346,6 +346,16 @@ rt_status rt_scene_info(const rt_scene *scene, int64_t *n_total, int32_t *n_inst
  * trees.  Errors: RT_ERR_INVALID_ARG. */
 rt_status rt_scene_trace_dirs(const rt_scene *scene, const float *dirs, int32_t K, float *T_out,
                               rt_stream_t stream);
+/* The same for any implicit ray set over the scene's rows (row = g_base_j +
+ * g as above, n_total rows): DIRS (as rt_scene_trace_dirs), HEMI (Sec. 3.3:
+ * the local hemisphere directions rays->dirs[K] about the world-frame normal
+ * of each row, rays->normals[n_total*3], device; Sec. 4.3 relighting of a
+ * composed scene re-traces these) or ENV (env-map samples, rays->env and
+ * rays->seed; the sample of row r, index s is keyed by the ray id r*S + s).
+ * The direction is in the world frame; the origin and the rest as above.
+ * T_out[row*K + k].  Errors: RT_ERR_INVALID_ARG, RT_ERR_UNSUPPORTED
+ * (explicit rays or ray_ids). */
+rt_status rt_scene_trace(const rt_scene *scene, const rt_rayspec *rays, float *T_out, rt_stream_t stream);
 rt_status rt_scene_destroy(rt_scene *scene, rt_stream_t stream);
 
 /* ------------------------------------------------------------------------ */

@@ -380,6 +380,29 @@ def _rows(R, v, c):
     return (R[0, c] * v[:, 0] + R[1, c] * v[:, 1]) + R[2, c] * v[:, 2]
 
 
+def instance_world_means(objects, xforms):
+    """World means of a composed scene's Gaussians in scene order (instance
+    by instance, each object's Gaussians in their original order): instance
+    j places objects[j] by xforms[j] = [R | t] (3x4, world = R local + t),
+    m_c = fl(((R_c0 x + R_c1 y) + R_c2 z) + t_c) in float32."""
+    out = []
+    for sc, xf in zip(objects, xforms):
+        X = np.asarray(xf, np.float32).reshape(3, 4)
+        R, t = X[:, :3], X[:, 3]
+        mu = _c(sc["mean"], np.float32)
+        out.append(np.stack([((R[c, 0] * mu[:, 0] + R[c, 1] * mu[:, 1]) + R[c, 2] * mu[:, 2]) + t[c]
+                             for c in range(3)], 1).astype(np.float32))
+    return np.concatenate(out)
+
+
+def instance_rows(objects, rows):
+    """(instance, local index) of scene rows (scene order as above)."""
+    base = np.cumsum([0] + [sc["mean"].shape[0] for sc in objects])
+    rows = np.asarray(rows, np.int64)
+    inst = np.searchsorted(base, rows, side="right") - 1
+    return inst.astype(np.int32), (rows - base[inst]).astype(np.int32)
+
+
 def instance_world_rays(objects, xforms, dirs, eps=1e-4):
     """World rays of a composed scene (Sec. 4.3).  Instance j places object
     objects[j] by xforms[j] = [R | t] (3x4, world = R local + t); the ray from

@@ -233,10 +233,15 @@ extern "C" rt_status rt_envmap_destroy(rt_envmap *env, rt_stream_t stream) {
 // Ray sets
 // ---------------------------------------------------------------------------
 rt_status rt_rayset_dev(const rt_bvh *bvh, const rt_rayspec *rays, RaySetDev *out, int64_t *count) {
-    if (!bvh || !rays || !out) return RT_ERR_INVALID_ARG;
+    if (!bvh) return RT_ERR_INVALID_ARG;
+    return rt_rayset_dev_n(bvh->n, bvh->params.origin_eps, rays, out, count);
+}
+
+rt_status rt_rayset_dev_n(int64_t n, float origin_eps, const rt_rayspec *rays, RaySetDev *out, int64_t *count) {
+    if (!rays || !out || n < 0) return RT_ERR_INVALID_ARG;
     memset(out, 0, sizeof(*out));
     out->kind = rays->kind;
-    out->eps = bvh->params.origin_eps;
+    out->eps = origin_eps;
     out->seed = rays->seed;
     int64_t cnt = -1;
     switch (rays->kind) {
@@ -254,14 +259,14 @@ rt_status rt_rayset_dev(const rt_bvh *bvh, const rt_rayspec *rays, RaySetDev *ou
             if (rays->n_dirs <= 0 || !rays->dirs) return RT_ERR_INVALID_ARG;
             out->K = rays->n_dirs;
             out->dirs = rays->dirs;
-            cnt = bvh->n * rays->n_dirs;
+            cnt = n * rays->n_dirs;
             break;
         case RT_RAYS_HEMI:
-            if (rays->n_dirs <= 0 || !rays->dirs || (bvh->n > 0 && !rays->normals)) return RT_ERR_INVALID_ARG;
+            if (rays->n_dirs <= 0 || !rays->dirs || (n > 0 && !rays->normals)) return RT_ERR_INVALID_ARG;
             out->K = rays->n_dirs;
             out->dirs = rays->dirs;
             out->normals = rays->normals;
-            cnt = bvh->n * rays->n_dirs;
+            cnt = n * rays->n_dirs;
             break;
         case RT_RAYS_ENV:
             if (rays->n_dirs <= 0 || !rays->env) return RT_ERR_INVALID_ARG;
@@ -270,7 +275,7 @@ rt_status rt_rayset_dev(const rt_bvh *bvh, const rt_rayspec *rays, RaySetDev *ou
             out->env_corners = rays->env->corners;
             out->env_h = rays->env->h;
             out->env_w = rays->env->w;
-            cnt = bvh->n * rays->n_dirs;
+            cnt = n * rays->n_dirs;
             break;
         default:
             return RT_ERR_INVALID_ARG;

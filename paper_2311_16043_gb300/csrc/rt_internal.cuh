@@ -224,6 +224,9 @@ __device__ __forceinline__ void implicit_ray(const RaySetDev &rs, int64_t r, int
 
 // Host: convert a public ray set into the device view (validates it).
 rt_status rt_rayset_dev(const rt_bvh *bvh, const rt_rayspec *rays, RaySetDev *out, int64_t *count);
+// The same for a set over n Gaussians (a composed scene's rows) with origin
+// offset origin_eps.
+rt_status rt_rayset_dev_n(int64_t n, float origin_eps, const rt_rayspec *rays, RaySetDev *out, int64_t *count);
 
 // Host: enqueue one trace of a ray set (rt_trace.cu).  `work` is an optional
 // caller-provided device counter (8 bytes); NULL allocates one per call.

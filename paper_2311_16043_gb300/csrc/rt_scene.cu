@@ -63,12 +63,15 @@ __device__ __forceinline__ bool top_slab(const float *bx, float3 oi, float3 inv)
 #ifndef RT_SCENE_MIN_BLOCKS
 #define RT_SCENE_MIN_BLOCKS 8
 #endif
+// rs: an implicit ray set over the scene's rows (row = g_base of the
+// instance + the Gaussian's original index): DIRS, HEMI (world-frame normals
+// per row) or ENV (ray id row * K + k keys the sample).
 __global__ void __launch_bounds__(128, RT_SCENE_MIN_BLOCKS) k_scene_trace(const InstDev *__restrict__ inst, int n_inst,
                                                      const TopNode *__restrict__ top, uint32_t root_ref,
-                                                     const float *__restrict__ root_box, const float *__restrict__ dirs,
-                                                     int32_t K, float eps, float t_min, int64_t total_items,
-                                                     float *__restrict__ T_out, int *status,
+                                                     const float *__restrict__ root_box, RaySetDev rs, float t_min,
+                                                     int64_t total_items, float *__restrict__ T_out, int *status,
                                                      unsigned long long *work) {
+    const int32_t K = rs.K;
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     WorkCounts wc = {0, 0, 0};
@@ -94,10 +97,10 @@ __global__ void __launch_bounds__(128, RT_SCENE_MIN_BLOCKS) k_scene_trace(const 
         if (p >= J.b.n) continue;
         const float4 mu4 = __ldg(J.b.gauss + 4 * p);
         const int64_t g = __float_as_int(__ldg(J.b.gauss + 4 * p + 1).w);
-        const float3 d = make_float3(__ldg(dirs + 3 * k), __ldg(dirs + 3 * k + 1), __ldg(dirs + 3 * k + 2));
         const float3 mw = to_world(J.R, J.t, make_float3(mu4.x, mu4.y, mu4.z));
-        const float3 o = make_float3(__fadd_rn(mw.x, __fmul_rn(eps, d.x)), __fadd_rn(mw.y, __fmul_rn(eps, d.y)),
-                                     __fadd_rn(mw.z, __fmul_rn(eps, d.z)));
+        const int64_t row = J.g_base + g;
+        float3 o, d;  // fl(mw + fl(eps d)), d from the set (world frame)
+        implicit_ray(rs, row * K + k, k, row, make_float4(mw.x, mw.y, mw.z, 0.0f), o, d);
         const float3 inv = safe_inv(d);
         const float3 oi = make_float3(o.x * inv.x, o.y * inv.y, o.z * inv.z);
         float T = 1.0f;
@@ -122,7 +125,7 @@ __global__ void __launch_bounds__(128, RT_SCENE_MIN_BLOCKS) k_scene_trace(const 
                 else rt_set_error(status, RT_ERR_STACK_OVERFLOW);
             }
         }
-        T_out[(J.g_base + g) * K + k] = T < t_min ? 0.0f : T;
+        T_out[row * K + k] = T < t_min ? 0.0f : T;
     }
 }
 
@@ -335,11 +338,15 @@ extern "C" rt_status rt_scene_info(const rt_scene *sc, int64_t *n_total, int32_t
     return RT_OK;
 }
 
-extern "C" rt_status rt_scene_trace_dirs(const rt_scene *sc, const float *dirs, int32_t K, float *T_out,
-                                         rt_stream_t stream) {
-    if (!sc || K <= 0 || !dirs) return RT_ERR_INVALID_ARG;
+extern "C" rt_status rt_scene_trace(const rt_scene *sc, const rt_rayspec *rays, float *T_out, rt_stream_t stream) {
+    if (!sc || !rays) return RT_ERR_INVALID_ARG;
+    if (rays->kind == RT_RAYS_EXPLICIT || rays->ray_ids) return RT_ERR_UNSUPPORTED;
+    RaySetDev rs;
+    int64_t count = 0;
+    RT_TRY(rt_rayset_dev_n(sc->n_total, sc->params.origin_eps, rays, &rs, &count));
     if (sc->n_total == 0) return RT_OK;
     if (!T_out) return RT_ERR_INVALID_ARG;
+    const int32_t K = rs.K;
     cudaStream_t st = (cudaStream_t)stream;
     // work items: instance by instance, all tiles of direction 0, then 1, ...
     const int64_t items = sc->n_tiles * K;
@@ -358,12 +365,22 @@ extern "C" rt_status rt_scene_trace_dirs(const rt_scene *sc, const float *dirs, 
         }
         k_scene_trace<<<per_sm * rt_num_sms(), 128, 0, st>>>(
             (const InstDev *)sc->dev, sc->n_inst, (const TopNode *)((char *)sc->dev + o_top), sc->root_ref,
-            (const float *)((char *)sc->dev + o_rb), dirs, K, sc->params.origin_eps, sc->params.t_min, items,
-            T_out, rt_status_ptr(), work);
+            (const float *)((char *)sc->dev + o_rb), rs, sc->params.t_min, items, T_out, rt_status_ptr(), work);
         res = rt_check_launch();
     }
     rt_free(work, stream);
     return res;
+}
+
+extern "C" rt_status rt_scene_trace_dirs(const rt_scene *sc, const float *dirs, int32_t K, float *T_out,
+                                         rt_stream_t stream) {
+    if (!sc || K <= 0 || !dirs) return RT_ERR_INVALID_ARG;
+    rt_rayspec rs;
+    memset(&rs, 0, sizeof(rs));
+    rs.kind = RT_RAYS_DIRS;
+    rs.n_dirs = K;
+    rs.dirs = dirs;
+    return rt_scene_trace(sc, &rs, T_out, stream);
 }
 
 extern "C" rt_status rt_scene_destroy(rt_scene *sc, rt_stream_t stream) {

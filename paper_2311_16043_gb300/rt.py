@@ -125,6 +125,7 @@ _SIGS = {
     "rt_scene_update": (_I32, [_P, _P, _I32, _P]),
     "rt_scene_info": (_I32, [_P, _P, _P]),
     "rt_scene_trace_dirs": (_I32, [_P, _P, _I32, _P, _P]),
+    "rt_scene_trace": (_I32, [_P, _P, _P, _P]),
     "rt_scene_destroy": (_I32, [_P, _P]),
     "rt_trace_ao": (_I32, [_P, _P, _P, _P, _P]),
     "rt_batch_create": (_I32, [_P, _I32, _I32, _P, _P]),
@@ -538,6 +539,18 @@ def rt_scene_trace_dirs(scene: Scene, dirs, T_out=None, stream=None):
         T_out = torch.empty((scene.n_total, K), dtype=torch.float32, device="cuda")
     _check(lib().rt_scene_trace_dirs(scene.handle, _ptr(dirs, torch.float32, "dirs"), K,
                                      _ptr(T_out, torch.float32, "T_out"), _stream(stream)), "rt_scene_trace_dirs")
+    return T_out
+
+
+def rt_scene_trace(scene: Scene, rs: rt_rayspec, T_out=None, stream=None):
+    """Visibility of an implicit ray set (DIRS, HEMI with world-frame normals
+    per scene row, or ENV) over every Gaussian of every instance:
+    T[n_total, K], instances in order."""
+    K = int(rs.n_dirs)
+    if T_out is None:
+        T_out = torch.empty((scene.n_total, K), dtype=torch.float32, device="cuda")
+    _check(lib().rt_scene_trace(scene.handle, C.byref(rs), _ptr(T_out, torch.float32, "T_out"), _stream(stream)),
+           "rt_scene_trace")
     return T_out
 
 

@@ -86,3 +86,23 @@ def test_rigid_motion_of_the_composition(orc):
     ok = (a["flags"] == 0) & (b["flags"] == 0)
     assert ok.mean() > 0.99
     assert np.abs(a["T"] - b["T"])[ok].max() <= TOL
+
+
+def test_world_means_and_rows(orc):
+    """The world means are the origins the direction rays start from (less
+    the offset along d), row by row in scene order; rows map back to their
+    instance and local index."""
+    objs = [scenes.uniform_scene(50, 3), scenes.uniform_scene(20, 4)]
+    xf = [np.concatenate([np.eye(3), [[0.5], [0.0], [-1.0]]], 1).astype(np.float32),
+          np.concatenate([np.array([[0, -1, 0], [1, 0, 0], [0, 0, 1]]), [[0.0], [2.0], [0.0]]], 1).astype(np.float32)]
+    m = orc.instance_world_means(objs, xf)
+    assert m.dtype == np.float32 and m.shape == (70, 3)
+    np.testing.assert_array_equal(m[:50], (objs[0]["mean"] + np.float32([0.5, 0.0, -1.0])).astype(np.float32))
+    mu = objs[1]["mean"]
+    np.testing.assert_allclose(m[50:], np.stack([-mu[:, 1], mu[:, 0] + 2.0, mu[:, 2]], 1), rtol=0, atol=1e-6)
+    dirs = scenes.fibonacci_sphere(4)
+    o, d, si, sl = orc.instance_world_rays(objs, xf, dirs, eps=0.0)
+    np.testing.assert_array_equal(o[::4], m)
+    inst, loc = orc.instance_rows(objs, np.arange(70))
+    np.testing.assert_array_equal(inst, si[::4])
+    np.testing.assert_array_equal(loc, sl[::4])
