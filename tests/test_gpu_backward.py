@@ -3,7 +3,8 @@ gradient (itself pinned to central finite differences), on the
 differentiation workload: the 4,096-Gaussian uniform scene restricted to a
 1,024-Gaussian, 16-direction subset (16,384 rays), L = sum_r w_r T_r with
 w_r ~ U(0,1), T_min = 0.  Bar: 1e-3 relative (vector norm per parameter
-group, and per component above a floor)."""
+group), and per component 1e-3 relative plus 2e-5 of the group's largest
+component (see _check)."""
 import numpy as np
 import pytest
 import torch
@@ -36,13 +37,20 @@ def case(orc):
 
 
 def _check(got, want, name):
+    """1e-3 relative as a vector norm per parameter group, and per component
+    |got - want| <= 1e-3 |want| + 2e-5 max|want| for every component.  The
+    absolute term is the float32 evaluation of the chain rule: each
+    component is a sum over hits of terms computed with ~1e-6 relative
+    error, some of them as large as the group's largest component, and a
+    mean component also collects the origin gradients of its own rays, which
+    largely cancel its hit terms; the float64-exact (fixed-point) summation
+    shows the same error, so it is not the atomics' order."""
     got = np.asarray(got, np.float64)
     rel = np.linalg.norm(got - want) / np.linalg.norm(want)
     assert rel < 1e-3, (name, rel)
-    floor = 1e-3 * np.abs(want).max()
-    big = np.abs(want) > floor
-    comp = np.abs(got[big] - want[big]) / np.abs(want[big])
-    assert np.quantile(comp, 0.999) < 1e-3 and comp.max() < 1e-2, (name, comp.max())
+    tol = 1e-3 * np.abs(want) + 2e-5 * np.abs(want).max()
+    err = np.abs(got - want)
+    assert np.all(err <= tol), (name, float((err / tol).max()))
 
 
 @pytest.mark.parametrize("use_log", [True, False])
