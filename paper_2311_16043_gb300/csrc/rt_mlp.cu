@@ -335,8 +335,9 @@ struct MlpDev {
 constexpr int INF_WG = 3;
 constexpr int INF_SMEM_ACT = IMG_BYTES;                          // INF_WG x 32768
 constexpr int INF_SMEM_B = INF_SMEM_ACT + INF_WG * 32768;        // b1..b4, w5: 5*128 floats
-constexpr int INF_SMEM_BAR = INF_SMEM_B + 5 * 128 * 4;           // INF_WG mbarriers + tmem slot
+constexpr int INF_SMEM_BAR = INF_SMEM_B + 5 * 128 * 4;           // 2 x INF_WG mbarriers + tmem slot
 constexpr int INF_SMEM_TOTAL = INF_SMEM_BAR + 64;
+static_assert(2 * INF_WG * 8 + 4 <= 64, "barrier area of the inference kernel");
 
 __device__ __forceinline__ void wg_sync(int g) {
     asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(128) : "memory");
@@ -385,7 +386,7 @@ __global__ void __launch_bounds__(128 * INF_WG, 1) k_mlp_infer(MlpDev net, Sampl
     uint8_t *wimg = smem;
     float *bias = reinterpret_cast<float *>(smem + INF_SMEM_B);  // [4][128], then w5[128]
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + INF_SMEM_BAR);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + INF_SMEM_BAR + 8 * INF_WG);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + INF_SMEM_BAR + 16 * INF_WG);
     const int t = threadIdx.x, g = t >> 7, tl = t & 127, wq = tl >> 5, lane = t & 31;
     uint8_t *act = smem + INF_SMEM_ACT + g * 32768;
     uint64_t *bar = bars + g;
@@ -401,7 +402,7 @@ __global__ void __launch_bounds__(128 * INF_WG, 1) k_mlp_infer(MlpDev net, Sampl
     }
     const float b5 = net.params[OFF_B5];
     if (t == 0)
-        for (int k = 0; k < INF_WG; ++k) mbar_init(bars + k, 1);
+        for (int k = 0; k < 2 * INF_WG; ++k) mbar_init(bars + k, 1);  // MMA commits, then drains
     if (t < 32) tmem_alloc(tslot, 512);
     fence_async_smem();
     tc_fence_before();
@@ -445,18 +446,12 @@ __global__ void __launch_bounds__(128 * INF_WG, 1) k_mlp_infer(MlpDev net, Sampl
                 issue_mma(tmem, a_addr, 128, sbo, 256, wb, 128, sbo, 256, idesc, K, true);  // onto the bias
                 tc_commit(bar);
             }
-            // every thread waits; the group then agrees, so a wait that gives
-            // up in one thread takes the whole group out together
-            if (!wg_all(g, mbar_wait(bar, phase, net.wait_cycles))) {
-                // the committed MMAs still write this group's TMEM columns:
-                // let them finish (default bound) before leaving
-                mbar_wait(bar, phase, WAIT_CYCLES);
-                if (tl == 0) rt_set_error(status, RT_ERR_TIMEOUT);
-                ok = false;
-            }
+            // a wait that gives up marks this thread; the thread still runs
+            // the tile's remaining steps (garbage values, no early exit), so
+            // the group stays in step until it votes at the end of the tile
+            if (!mbar_wait(bar, phase, net.wait_cycles)) ok = false;
             phase ^= 1u;
             tc_fence_after();
-            if (!ok) break;
 #pragma unroll 1
             for (int cc = 0; cc < 4; ++cc) {
                 float v[32];
@@ -475,7 +470,6 @@ __global__ void __launch_bounds__(128 * INF_WG, 1) k_mlp_infer(MlpDev net, Sampl
             }
             if (l < 3) tmem_store_bias(lane_addr, bias + 128 * (l + 1));
         }
-        if (!ok) break;
         if (valid) {
             const float z5 = b5 + (z5p.x + z5p.y);
             const float ez = __expf(-z5);
@@ -494,7 +488,16 @@ __global__ void __launch_bounds__(128 * INF_WG, 1) k_mlp_infer(MlpDev net, Sampl
             }
         }
         tc_fence_before();
-        wg_sync(g);
+        // the end-of-tile barrier doubles as the vote: the group leaves
+        // together after a give-up anywhere in it, once its MMAs are done
+        if (!wg_all(g, ok)) {
+            ok = false;
+            if (tl == 0) {
+                tc_commit(bars + INF_WG + g);  // completes when all MMAs issued so far have
+                rt_set_error(status, RT_ERR_TIMEOUT);
+            }
+            mbar_wait(bars + INF_WG + g, 0, WAIT_CYCLES);
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -631,8 +634,8 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleS
     float *z5p = fb + 1280;       // [4][128] per-warpgroup partial logits
     float *misc = fb + 1792;      // [0] db5, [1] loss
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + TR_BAR);  // MMA commits
-    uint64_t *wbar = bar + 1;                                      // [2] weight copies
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + TR_BAR + 24);
+    uint64_t *wbar = bar + 1;                                      // [2] weight copies; bar[3]: drain
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + TR_BAR + 32);
     float *smp = reinterpret_cast<float *>(smem + TR_SMP);  // [2][7][128]
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int r = t & 127, q = t >> 7, c0 = 32 * q;
@@ -655,6 +658,7 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleS
         mbar_init(bar, 1);
         mbar_init(wbar, 1);
         mbar_init(wbar + 1, 1);
+        mbar_init(bar + 3, 1);
     }
     if (warp == 0) tmem_alloc(tslot, 512);
     fence_async_smem();
@@ -684,6 +688,7 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleS
     uint32_t wph[2] = {0u, 0u};
     bool wok = true;
     auto load_w = [&](int b, int img_off_bytes, int bytes) {
+        if (pend[b]) return;  // only after a give-up: one copy per buffer and phase
         mbar_expect_tx(wbar + b, (uint32_t)bytes);
         bulk_g2s(wb[b], net.img + img_off_bytes, (uint32_t)bytes, wbar + b);
         pend[b] = true;
@@ -773,17 +778,13 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleS
         tc_fence_before();
         __syncthreads();
     };
-    // every thread waits, then the CTA agrees (one vote; thread 0 also votes
-    // on its weight copies), so a wait that gives up anywhere takes the whole
-    // CTA out together, after the committed MMAs have finished
+    // a wait that gives up (thread 0: also a weight copy) marks this thread;
+    // the thread still runs the tile's remaining steps (garbage values, no
+    // early exit), so the CTA stays in step until it votes at the end of the
+    // tile, then leaves together once its MMAs are done
     auto wait_mma = [&]() {
-        bool mine = mbar_wait(bar, phase, net.wait_cycles);
-        if (t == 0) mine = mine && wok;
-        if (!__syncthreads_and(mine ? 1 : 0)) {
-            mbar_wait(bar, phase, WAIT_CYCLES);
-            if (t == 0) rt_set_error(status, RT_ERR_TIMEOUT);
-            ok = false;
-        }
+        if (!mbar_wait(bar, phase, net.wait_cycles)) ok = false;
+        if (t == 0 && !wok) ok = false;
         phase ^= 1u;
         tc_fence_after();
     };
@@ -818,7 +819,6 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleS
                 tc_commit(bar);
             }
             wait_mma();
-            if (!ok) break;
             if (t == 0) {
                 if (l == 0) load_w(0, IMG_W3, 32768);  // W1 read: B0 takes W3
                 if (l == 1) load_w(1, IMG_W4, 32768);  // W2 read: B1 takes W4
@@ -841,7 +841,6 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleS
                 z5p[128 * q + r] = zp;
             }
         }
-        if (!ok) break;
         __syncthreads();
         // ---- loss and output layer (every warpgroup computes the row's
         // logit from the four partials in the same order) ----
@@ -896,7 +895,6 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleS
                 tc_commit(bar);
             }
             wait_mma();
-            if (!ok) break;
             if (t == 0) {
                 if (l == 3) load_w(1, IMG_W2, 32768);                     // W4 read: B1 takes W2
                 if (l == 2 && tile + 1 < t1) load_w(0, IMG_W1, 20480);    // W3 read: B0 takes W1
@@ -911,7 +909,6 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleS
             store_chunk(hl, r, c0, v);
             atomicAdd(dbias + 128 * (l - 1) + c0 + lane, transpose_reduce32(v, lane));
         }
-        if (!ok) break;
         // ---- dW1 = dz1^T x0 (per tile, added to this CTA's partial) ----
         sync_mma();
         if (t == 0) {
@@ -920,7 +917,6 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleS
             tc_commit(bar);
         }
         wait_mma();
-        if (!ok) break;
         // fire-and-forget vector adds: each address of this CTA's partial
         // is only ever added to by this thread, in tile order, so the sums
         // are deterministic; warpgroup 3 has no dW1 columns
@@ -940,7 +936,15 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleS
             draw_ray(sb ^ 1);  // the next tile's rays, read after its first barrier
         }
         tc_fence_before();
-        __syncthreads();
+        // the end-of-tile barrier doubles as the vote
+        if (!__syncthreads_and(ok ? 1 : 0)) {
+            ok = false;
+            if (t == 0) {
+                tc_commit(bar + 3);  // completes when all MMAs issued so far have
+                rt_set_error(status, RT_ERR_TIMEOUT);
+            }
+            mbar_wait(bar + 3, 0, WAIT_CYCLES);
+        }
     }
     // weight copies still in flight (only after a give-up): let them land
     if (t == 0) {
@@ -966,15 +970,15 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleS
     }
     __syncthreads();
     if (t < 128) {
-        part[OFF_B1 + t] = dbias[t];
-        part[OFF_B2 + t] = dbias[128 + t];
-        part[OFF_B3 + t] = dbias[256 + t];
-        part[OFF_B4 + t] = dbias[384 + t];
-        part[OFF_W5 + t] = dw5[t];
+        part[OFF_B1 + t] = any ? dbias[t] : 0.0f;
+        part[OFF_B2 + t] = any ? dbias[128 + t] : 0.0f;
+        part[OFF_B3 + t] = any ? dbias[256 + t] : 0.0f;
+        part[OFF_B4 + t] = any ? dbias[384 + t] : 0.0f;
+        part[OFF_W5 + t] = any ? dw5[t] : 0.0f;
     }
     if (t == 0) {
-        part[OFF_B5] = misc[0];
-        part[NPARAM] = misc[1];
+        part[OFF_B5] = any ? misc[0] : 0.0f;
+        part[NPARAM] = any ? misc[1] : 0.0f;
     }
     tc_fence_before();
     __syncthreads();
