@@ -215,7 +215,7 @@ def test_id_subset_matches_full_trace(small):
     from paper_2311_16043_gb300 import rt
     sc, dirs, _ = small
     bvh = build(sc)
-    full = trace_dirs(bvh, dirs, kernel=1).reshape(-1)  # id subsets use the per-ray traversal
+    full = trace_dirs(bvh, dirs, kernel=6).reshape(-1)  # id lists up to 2^22 rays: one warp per ray
     sel = scenes.sample_ray_ids(4096 * 32, 5000, 3)
     rs = rt.rayspec(rt.RT_RAYS_DIRS, dirs=_dev(dirs), ray_ids=_dev(sel))
     T = rt.rt_trace_visibility(bvh, rs)
