@@ -351,6 +351,41 @@ def run_surrogate(args, rt, torch, d, dirs, T, prm, dev):
         out["batches"].append(out_b)
     s.destroy()
     bvh.destroy()
+    out["other_scenes"] = [surrogate_other_scene(rt, torch, dev, *c, pos_weight=args.pos_weight, band=args.band)
+                           for c in (("uniform_4k_k32", "uniform", 4096, 1, 32),
+                                     ("uniform_300k_k64", "uniform", 300_000, 3, 64))]
+    return out
+
+
+def surrogate_other_scene(rt, torch, dev, name, gen, n, seed, K, pos_weight, band, steps=2000):
+    """The surrogate on a second scene: trained (the same recipe) on its
+    Fibonacci table, evaluated on every ray of the rotated set, next to the
+    trivial predictors.  uniform_4k_k32 is the sparse config-1 scene (no
+    T = 0 rays); uniform_300k_k64 the same distributions at 300k Gaussians
+    (optically dense)."""
+    import scenes
+    sc = scenes.uniform_scene(n, seed) if gen == "uniform" else scenes.object_scene(n, seed)
+    d = {k: torch.from_numpy(v).to(dev) for k, v in sc.items()}
+    bvh = rt.rt_build_bvh(d["mean"], d["scale"], d["quat"], d["opacity"])
+    rs = rt.rayspec(rt.RT_RAYS_DIRS, dirs=torch.from_numpy(scenes.fibonacci_sphere(K)).to(dev))
+    T = rt.rt_trace_visibility(bvh, rs)
+    rs_h = rt.rayspec(rt.RT_RAYS_DIRS, dirs=torch.from_numpy(scenes.rotated_fibonacci(K, 51)).to(dev))
+    Th = rt.rt_trace_visibility(bvh, rs_h, opts=rt.trace_opts(kernel=rt.RT_KERNEL_WARP_RAY))
+    s = rt.rt_surrogate_create(rt.mlp_cfg(batch=262144, lr=1e-3, pos_weight=pos_weight), seed=5)
+    rt.rt_surrogate_train(s, bvh, rs, T.view(-1), steps=steps, seed=5)
+    p = rt.rt_surrogate_infer(s, bvh, rs_h, band=0.0)
+    nfb = torch.zeros(1, dtype=torch.int64, device=dev)
+    q = rt.rt_surrogate_infer(s, bvh, rs_h, band=band, n_fallback=nfb)
+    torch.cuda.synchronize()
+    med = float(Th.median())
+    out = {"scene": name, "gaussians": n, "directions": K, "rays": n * K, "mean_T": float(Th.mean()),
+           "zero_fraction": float((Th == 0).float().mean()), "mae_predict_zero": float(Th.abs().mean()),
+           "mae_best_constant": min(float(Th.abs().mean()), float((Th - med).abs().mean())),
+           "mae_predict_mean": float((Th - Th.mean()).abs().mean()),
+           "mae_surrogate_only": float((p - Th).abs().mean()), "mae_with_fallback": float((q - Th).abs().mean()),
+           "fallback_fraction": float(nfb.item()) / (n * K)}
+    s.destroy()
+    bvh.destroy()
     return out
 
 
