@@ -3,8 +3,8 @@
 //
 // Network: frequency encoding of (origin, direction) -> 80 inputs ->
 // 4 x 128 ReLU -> 1 sigmoid.  bf16 weights and activations, f32 accumulation
-// in TMEM.  One CTA of 128 threads per SM; thread r owns sample row r of a
-// 128-sample tile (= TMEM lane r of the accumulator).
+// in TMEM.  One CTA per SM; sample row r of a 128-sample tile is TMEM lane r
+// of the accumulator.
 //
 // Inference (k_mlp_infer): the four weight images stay in shared memory; per
 // tile the encoding is written to shared memory, each layer is one chain of
@@ -21,10 +21,11 @@
 //   dW_l += dz_l^T x_{l-1}   (M = units, N = inputs, K = samples; TMEM-resident
 //                             across the CTA's tiles for l = 2..4)
 //   dX_{l-1} = dz_l W_l      (M = samples, N = inputs, K = units)
-// Bias gradients are column sums of dz (warp transpose-reductions).  Each CTA
-// writes one partial gradient; k_mlp_reduce_adam sums the partials in a fixed
-// order (deterministic), applies Adam to the f32 master weights and re-packs
-// the bf16 weight images.
+// The bias gradients (sums of dz over samples) come out of the tensor cores
+// through a column of ones in the input tile.  Each CTA writes one partial
+// gradient; k_mlp_reduce_adam sums the partials in a fixed order
+// (deterministic), applies Adam to the f32 master weights and re-packs the
+// bf16 weight images.
 #include <cuda_bf16.h>
 #include <math.h>
 #include <string.h>
@@ -38,7 +39,8 @@
 namespace {
 
 constexpr int H = 128;
-constexpr int IN = 80;
+constexpr int IN = 80;       // 78 features and two pad columns
+constexpr int IN_FEAT = 78;  // the bf16 images hold zero weights in the pad columns
 constexpr int OFF_W1 = 0, OFF_B1 = 10240, OFF_W2 = 10368, OFF_B2 = 26752, OFF_W3 = 26880, OFF_B3 = 43264,
               OFF_W4 = 43392, OFF_B4 = 59776, OFF_W5 = 59904, OFF_B5 = 60032, NPARAM = 60033;
 constexpr int IMG_W1 = 0, IMG_W2 = 20480, IMG_W3 = 53248, IMG_W4 = 86016, IMG_BYTES = 118784;
@@ -176,15 +178,29 @@ __device__ __forceinline__ void store_chunk_relu(uint8_t *img, int r, int c0, co
     }
 }
 
-__device__ __forceinline__ void load_chunk(const uint8_t *img, int r, int c0, float (&v)[32]) {
+// Row r, columns c0..c0+31, of a K-major bf16 image (kdim 128) as 16 bf16
+// pairs (column c0 + 2k in the low half of u[k]), and back.
+__device__ __forceinline__ void load_chunk_raw(const uint8_t *img, int r, int c0, uint32_t (&u)[16]) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        uint4 u = *reinterpret_cast<const uint4 *>(img + img_off(r, c0 + 8 * q, H));
-        v[8 * q + 0] = bf16_lo(u.x); v[8 * q + 1] = bf16_hi(u.x);
-        v[8 * q + 2] = bf16_lo(u.y); v[8 * q + 3] = bf16_hi(u.y);
-        v[8 * q + 4] = bf16_lo(u.z); v[8 * q + 5] = bf16_hi(u.z);
-        v[8 * q + 6] = bf16_lo(u.w); v[8 * q + 7] = bf16_hi(u.w);
+        const uint4 x = *reinterpret_cast<const uint4 *>(img + img_off(r, c0 + 8 * q, H));
+        u[4 * q] = x.x;
+        u[4 * q + 1] = x.y;
+        u[4 * q + 2] = x.z;
+        u[4 * q + 3] = x.w;
     }
+}
+__device__ __forceinline__ void store_chunk_raw(uint8_t *img, int r, int c0, const uint32_t (&u)[16]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        *reinterpret_cast<uint4 *>(img + img_off(r, c0 + 8 * q, H)) =
+            make_uint4(u[4 * q], u[4 * q + 1], u[4 * q + 2], u[4 * q + 3]);
+}
+// Per half of a bf16 pair: all ones where the value is > 0, else zero (NaN: zero).
+__device__ __forceinline__ uint32_t bf16x2_pos_mask(uint32_t u) {
+    __nv_bfloat162 h;
+    memcpy(&h, &u, sizeof(u));
+    return __hgt2_mask(h, __float2bfloat162_rn(0.0f));
 }
 
 // Warp transpose-reduction: afterwards lane l holds sum over the warp's
@@ -575,8 +591,12 @@ __device__ __forceinline__ void encode_scalar(float xh, float xl, float *f) {
 }
 
 // Features [26q, 26q + 26) of row r (warpgroups 0..2: scalars 2q and 2q + 1
-// of (p_n, d)), written as bf16 pairs; warpgroup 2 also writes the two zero
-// pads (78, 79).  Same values as encode() + store_row_x0.
+// of (p_n, d)), written as bf16 pairs: the values of encode() +
+// store_row_x0.  Warpgroup 2 also writes the pad columns as (1, 0): the
+// weight images are zero there, so the forward is unchanged, and the dW1
+// product's column 78 becomes the sum over samples of dz1, the gradient of
+// the layer-1 bias; the B operand of the other layers' bias-gradient
+// products is this tile's columns 64..79.
 __device__ __forceinline__ void encode_part(uint8_t *x0, int r, int q, bool valid, float3 p, float3 d,
                                             const MlpDev &net) {
     if (q > 2) return;
@@ -587,7 +607,12 @@ __device__ __forceinline__ void encode_part(uint8_t *x0, int r, int q, bool vali
             const int c = 2 * q + j;
             if (c < 3) {
                 const float pc = c == 0 ? p.x : c == 1 ? p.y : p.z;
-                normalise_pair(pc, net.lo[c], net.eh[c], net.el[c], xh[j], xl[j]);
+                // selects, not net.lo[c]: a run-time index into the kernel
+                // parameter makes the compiler copy it to local memory
+                const float lo = c == 0 ? net.lo[0] : c == 1 ? net.lo[1] : net.lo[2];
+                const float eh = c == 0 ? net.eh[0] : c == 1 ? net.eh[1] : net.eh[2];
+                const float el = c == 0 ? net.el[0] : c == 1 ? net.el[1] : net.el[2];
+                normalise_pair(pc, lo, eh, el, xh[j], xl[j]);
             } else {
                 xh[j] = c == 3 ? d.x : c == 4 ? d.y : d.z;
             }
@@ -604,7 +629,7 @@ __device__ __forceinline__ void encode_part(uint8_t *x0, int r, int q, bool vali
 #pragma unroll
     for (int k = 0; k < 13; ++k)
         *reinterpret_cast<uint32_t *>(x0 + img_off(r, 26 * q + 2 * k, IN)) = pack_bf16(f[2 * k], f[2 * k + 1]);
-    if (q == 2) *reinterpret_cast<uint32_t *>(x0 + img_off(r, 78, IN)) = 0u;
+    if (q == 2) *reinterpret_cast<uint32_t *>(x0 + img_off(r, IN_FEAT, IN)) = 0x3f80u;  // bf16 (1, 0)
 }
 
 // a[0..3] += (x, y, z, w) in global memory without a return value (one
@@ -614,17 +639,13 @@ __device__ __forceinline__ void red_add_v4(float *a, float x, float y, float z, 
                  : "memory");
 }
 
-// 32 values of row r, columns c0..c0+31, of a K-major bf16 image (kdim 128).
-__device__ __forceinline__ void load_chunk32(const uint8_t *img, int r, int c0, float (&v)[32]) {
-    load_chunk(img, r, c0, v);
-}
-
 __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleSrc S, int64_t m, float inv_batch,
                                                              float *partial, int *status) {
     extern __shared__ __align__(1024) uint8_t smem[];
-    uint8_t *wb[2] = {smem + TR_WB0, smem + TR_WB1};
+    // buffers by index: arithmetic, not arrays (no local-memory copies)
+    auto wb = [&](int b) { return smem + TR_WB0 + 32768 * b; };
     uint8_t *x0 = smem + TR_X0;
-    uint8_t *hb[3] = {smem + TR_H1, smem + TR_H2, smem + TR_H3};
+    auto hb = [&](int i) { return smem + TR_H1 + 32768 * i; };
     uint8_t *dz = smem + TR_DZ;
     float *fb = reinterpret_cast<float *>(smem + TR_F);
     float *bias = fb;             // [4][128]
@@ -666,15 +687,19 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleS
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-    const uint32_t tm_work = tmem, tm_dw[3] = {tmem + 128, tmem + 256, tmem + 384};  // dW2, dW3, dW4
+    const uint32_t tm_work = tmem;
+    auto tm_dw = [&](int i) { return tmem + 128u * (uint32_t)(i + 1); };  // dW2, dW3, dW4
     const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
-    const uint32_t s_wb[2] = {smem_u32(wb[0]), smem_u32(wb[1])};
+    const uint32_t s_wb0 = smem_u32(wb(0));
+    auto s_wb = [&](int b) { return s_wb0 + 32768u * (uint32_t)b; };
     const uint32_t s_x0 = smem_u32(x0), s_dz = smem_u32(dz);
-    const uint32_t s_h[3] = {smem_u32(hb[0]), smem_u32(hb[1]), smem_u32(hb[2])};
+    const uint32_t s_h0 = smem_u32(hb(0));
+    auto s_h = [&](int i) { return s_h0 + 32768u * (uint32_t)i; };
     const uint32_t id_fwd = tc_idesc_bf16(128, 128, false, false);
     const uint32_t id_dw = tc_idesc_bf16(128, 128, true, true);
     const uint32_t id_dw1 = tc_idesc_bf16(128, IN, true, true);
     const uint32_t id_dx = tc_idesc_bf16(128, 128, false, true);
+    const uint32_t id_db = tc_idesc_bf16(128, 16, true, true);
     uint32_t phase = 0;
     bool ok = true;
 
@@ -683,21 +708,21 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleS
     const int64_t t0 = (int64_t)blockIdx.x * per;
     const int64_t t1 = t0 + per < ntiles ? t0 + per : ntiles;
 
-    // weight copies (thread 0 only): pending flags and phase bits per buffer
-    bool pend[2] = {false, false};
-    uint32_t wph[2] = {0u, 0u};
+    // weight copies (thread 0 only): bit b of `pend` / `wph` is buffer b's
+    // pending flag / phase
+    uint32_t pend = 0u, wph = 0u;
     bool wok = true;
     auto load_w = [&](int b, int img_off_bytes, int bytes) {
-        if (pend[b]) return;  // only after a give-up: one copy per buffer and phase
+        if ((pend >> b) & 1u) return;  // only after a give-up: one copy per buffer and phase
         mbar_expect_tx(wbar + b, (uint32_t)bytes);
-        bulk_g2s(wb[b], net.img + img_off_bytes, (uint32_t)bytes, wbar + b);
-        pend[b] = true;
+        bulk_g2s(wb(b), net.img + img_off_bytes, (uint32_t)bytes, wbar + b);
+        pend |= 1u << b;
     };
     auto need_w = [&](int b) {
-        if (pend[b]) {
-            if (mbar_wait(wbar + b, wph[b], net.wait_cycles)) {
-                wph[b] ^= 1u;
-                pend[b] = false;
+        if ((pend >> b) & 1u) {
+            if (mbar_wait(wbar + b, (wph >> b) & 1u, net.wait_cycles)) {
+                wph ^= 1u << b;
+                pend &= ~(1u << b);
             } else {
                 wok = false;
             }
@@ -813,8 +838,8 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleS
                 if (wok) {
                     const int K = l == 0 ? IN : H;
                     const uint32_t sbo = (uint32_t)(K / 8 * 128);
-                    const uint32_t a = l == 0 ? s_x0 : s_h[l - 1];
-                    issue_mma(tm_work, a, 128, sbo, 256, s_wb[b], 128, sbo, 256, id_fwd, K, false);
+                    const uint32_t a = l == 0 ? s_x0 : s_h(l - 1);
+                    issue_mma(tm_work, a, 128, sbo, 256, s_wb(b), 128, sbo, 256, id_fwd, K, false);
                 }
                 tc_commit(bar);
             }
@@ -823,19 +848,22 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleS
                 if (l == 0) load_w(0, IMG_W3, 32768);  // W1 read: B0 takes W3
                 if (l == 1) load_w(1, IMG_W4, 32768);  // W2 read: B1 takes W4
             }
-            const float *bl = bias + 128 * l + c0;
+            // h = bf16(relu(x W^T + b)), the ReLU folded into the conversion;
+            // the bias is added after the MMA in float32 (accumulating the
+            // products onto a bias stored in TMEM measured a larger gradient
+            // error, through ReLU decisions at pre-activations near 0)
             float v[32];
             tmem_ld32(tm_work + lane_off + c0, v);
-            if (l < 3) {
 #pragma unroll
-                for (int k = 0; k < 32; ++k) v[k] = fmaxf(v[k] + bl[k], 0.0f);
-                store_chunk(hb[l], r, c0, v);
+            for (int k = 0; k < 32; ++k) v[k] += bias[128 * l + c0 + k];
+            if (l < 3) {
+                store_chunk_relu(hb(l), r, c0, v);
                 if (l == 0 && q == 3 && tile + 1 < t1) draw_mean(sb ^ 1);
             } else {
                 float zp = 0.0f;
 #pragma unroll
                 for (int k = 0; k < 32; ++k) {
-                    h4[k] = bf16_round(fmaxf(v[k] + bl[k], 0.0f));
+                    h4[k] = bf16_round(fmaxf(v[k], 0.0f));
                     zp = fmaf(w5[c0 + k], h4[k], zp);
                 }
                 z5p[128 * q + r] = zp;
@@ -863,17 +891,16 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleS
                 atomicAdd(misc + 0, db5);
             }
         }
-        // dz4 = bf16(dz5 * w5 * [h4 > 0]); dw5 += dz5 * h4; db4 += dz4
+        // dz4 = bf16(dz5 * w5 * [h4 > 0]) (rounded by the store); dw5 += dz5 * h4
         {
             float g[32];
 #pragma unroll
             for (int k = 0; k < 32; ++k) {
-                g[k] = h4[k] > 0.0f ? bf16_round(dz5 * w5[c0 + k]) : 0.0f;
+                g[k] = h4[k] > 0.0f ? dz5 * w5[c0 + k] : 0.0f;
                 h4[k] *= dz5;
             }
             store_chunk(dz, r, c0, g);
             atomicAdd(dw5 + c0 + lane, transpose_reduce32(h4, lane));
-            atomicAdd(dbias + 384 + c0 + lane, transpose_reduce32(g, lane));
         }
         // ---- backward through layers 4, 3, 2: dz_{l+1} (dz or h_{l+1}'s
         // buffer) and W_{l+1} (B1, B0, B1) ----
@@ -885,12 +912,12 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleS
                 const int b = l == 2 ? 0 : 1;
                 need_w(b);
                 if (wok) {
-                    const uint32_t s_dzl = l == 3 ? s_dz : s_h[l];
+                    const uint32_t s_dzl = l == 3 ? s_dz : s_h(l);
                     // dW_{l+1} += dz^T x_l : A = dz (MN-major), B = h_l (MN-major), K = samples
-                    issue_mma(tm_dw[l - 1], s_dzl, 2048, 128, 4096, s_h[l - 1], 2048, 128, 4096, id_dw, 128,
+                    issue_mma(tm_dw(l - 1), s_dzl, 2048, 128, 4096, s_h(l - 1), 2048, 128, 4096, id_dw, 128,
                               !first);
                     // dX_l = dz W_{l+1} : A = dz (K-major), B = W (MN-major), K = units
-                    issue_mma(tm_work, s_dzl, 128, 2048, 256, s_wb[b], 2048, 128, 4096, id_dx, 128, false);
+                    issue_mma(tm_work, s_dzl, 128, 2048, 256, s_wb(b), 2048, 128, 4096, id_dx, 128, false);
                 }
                 tc_commit(bar);
             }
@@ -899,21 +926,28 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleS
                 if (l == 3) load_w(1, IMG_W2, 32768);                     // W4 read: B1 takes W2
                 if (l == 2 && tile + 1 < t1) load_w(0, IMG_W1, 20480);    // W3 read: B0 takes W1
             }
-            // dz_l = bf16(dX_l * [h_l > 0]) written over h_l; db_l += dz_l
-            uint8_t *hl = hb[l - 1];
-            float v[32], h[32];
+            // dz_l = bf16(dX_l) * [h_l > 0] on bf16 pairs, written over h_l
+            uint8_t *hl = hb(l - 1);
+            float v[32];
+            uint32_t hp[16];
             tmem_ld32(tm_work + lane_off + c0, v);
-            load_chunk32(hl, r, c0, h);
+            load_chunk_raw(hl, r, c0, hp);
 #pragma unroll
-            for (int k = 0; k < 32; ++k) v[k] = h[k] > 0.0f ? bf16_round(v[k]) : 0.0f;
-            store_chunk(hl, r, c0, v);
-            atomicAdd(dbias + 128 * (l - 1) + c0 + lane, transpose_reduce32(v, lane));
+            for (int k = 0; k < 16; ++k) hp[k] = pack_bf16(v[2 * k], v[2 * k + 1]) & bf16x2_pos_mask(hp[k]);
+            store_chunk_raw(hl, r, c0, hp);
         }
-        // ---- dW1 = dz1^T x0 (per tile, added to this CTA's partial) ----
+        // ---- dW1 = dz1^T x0 (per tile, added to this CTA's partial) and the
+        // bias gradients: x0's column 78 is all ones, so column 78 of dW1 is
+        // db1 = sum over samples of dz1, and dz_l^T times x0's columns 64..79
+        // gives db_l in its column 14 (db4, db3, db2 in work columns 94,
+        // 110, 126) ----
         sync_mma();
         if (t == 0) {
             tc_fence_after();
-            issue_mma(tm_work, s_h[0], 2048, 128, 4096, s_x0, 1280, 128, 2560, id_dw1, 128, false);
+            issue_mma(tm_work, s_h(0), 2048, 128, 4096, s_x0, 1280, 128, 2560, id_dw1, 128, false);
+            issue_mma(tm_work + 80, s_dz, 2048, 128, 4096, s_x0 + 1024, 1280, 128, 2560, id_db, 128, false);
+            issue_mma(tm_work + 96, s_h(2), 2048, 128, 4096, s_x0 + 1024, 1280, 128, 2560, id_db, 128, false);
+            issue_mma(tm_work + 112, s_h(1), 2048, 128, 4096, s_x0 + 1024, 1280, 128, 2560, id_db, 128, false);
             tc_commit(bar);
         }
         wait_mma();
@@ -927,13 +961,22 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleS
 #pragma unroll
             for (int k = 0; k < 8; ++k) red_add_v4(row + 4 * k, v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
         } else if (q == 2) {
+            // columns 64..95: dW1 64..79 (78: db1), then db4's product (94)
             float *row = part + OFF_W1 + (int64_t)r * IN + c0;
-            float v[16];
-            tmem_ld16(tm_work + lane_off + c0, v);
+            float v[32];
+            tmem_ld32(tm_work + lane_off + c0, v);
+            dbias[r] += v[14];
+            dbias[384 + r] += v[30];
+            v[14] = 0.0f;  // the pad weight's gradient
 #pragma unroll
             for (int k = 0; k < 4; ++k) red_add_v4(row + 4 * k, v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
-        } else if (tile + 1 < t1) {
-            draw_ray(sb ^ 1);  // the next tile's rays, read after its first barrier
+        } else {
+            // columns 96..127: db3's and db2's products (110, 126)
+            float v[32];
+            tmem_ld32(tm_work + lane_off + c0, v);
+            dbias[256 + r] += v[14];
+            dbias[128 + r] += v[30];
+            if (tile + 1 < t1) draw_ray(sb ^ 1);  // the next tile's rays, read after its first barrier
         }
         tc_fence_before();
         // the end-of-tile barrier doubles as the vote
@@ -950,7 +993,7 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleS
     if (t == 0) {
 #pragma unroll
         for (int b = 0; b < 2; ++b)
-            if (pend[b]) mbar_wait(wbar + b, wph[b], WAIT_CYCLES);
+            if ((pend >> b) & 1u) mbar_wait(wbar + b, (wph >> b) & 1u, WAIT_CYCLES);
     }
     // ---- flush this CTA's partial gradient ----
     tc_fence_before();
@@ -958,11 +1001,11 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleS
     tc_fence_after();
     const bool any = t1 > t0 && ok;
     const int offW[3] = {OFF_W2, OFF_W3, OFF_W4};
-#pragma unroll 1
+#pragma unroll
     for (int l = 0; l < 3; ++l) {
         float4 *row = reinterpret_cast<float4 *>(part + offW[l] + (int64_t)r * H + c0);
         float v[32];
-        tmem_ld32(tm_dw[l] + lane_off + c0, v);
+        tmem_ld32(tm_dw(l) + lane_off + c0, v);
 #pragma unroll
         for (int k = 0; k < 8; ++k)
             row[k] = any ? make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3])
@@ -987,41 +1030,55 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleS
 }
 
 // Sum the CTA partials in a fixed order; either write the gradient or take
-// an Adam step on the f32 master weights and re-pack the bf16 images.
-__global__ void k_mlp_reduce_adam(const float *partial, int nparts, float *grad_out, float *loss_out,
-                                  float *params, float *mo, float *vo, uint8_t *img, float lr, float b1,
-                                  float b2, float eps, float c1, float c2, int adam) {
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q <= NPARAM; q += gridDim.x * blockDim.x) {
-        float g = 0.0f;
-        // loads run ahead of the (sequential, fixed-order) sum
+// an Adam step on the f32 master weights and re-pack the bf16 images.  A
+// block of RA_GROUPS warps takes 32 consecutive parameters: warp w sums
+// partials w, w + RA_GROUPS, ... (its loads all in flight), then warp 0 adds
+// the RA_GROUPS sums in order.
+constexpr int RA_GROUPS = 8;
+__global__ void __launch_bounds__(32 * RA_GROUPS) k_mlp_reduce_adam(
+    const float *partial, int nparts, float *grad_out, float *loss_out, float *params, float *mo, float *vo,
+    uint8_t *img, float lr, float b1, float b2, float eps, float c1, float c2, int adam) {
+    __shared__ float sums[RA_GROUPS][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int q = blockIdx.x * 32 + lane;
+    float g = 0.0f;
+    if (q <= NPARAM) {
 #pragma unroll 8
-        for (int c = 0; c < nparts; ++c) g += partial[(int64_t)c * TR_PSTRIDE + q];
-        if (q == NPARAM) {
-            if (loss_out) *loss_out = g;
-            continue;
-        }
-        if (!adam) {
-            grad_out[q] = g;
-            continue;
-        }
-        const float m = b1 * mo[q] + (1.0f - b1) * g;
-        const float v = b2 * vo[q] + (1.0f - b2) * g * g;
-        mo[q] = m;
-        vo[q] = v;
-        const float w = params[q] - lr * (m / c1) / (sqrtf(v / c2) + eps);
-        params[q] = w;
-        // re-pack the bf16 image of weight matrices
-        int base = -1, kin = 0, ioff = 0;
-        if (q < OFF_B1) { base = OFF_W1; kin = IN; ioff = IMG_W1; }
-        else if (q >= OFF_W2 && q < OFF_B2) { base = OFF_W2; kin = H; ioff = IMG_W2; }
-        else if (q >= OFF_W3 && q < OFF_B3) { base = OFF_W3; kin = H; ioff = IMG_W3; }
-        else if (q >= OFF_W4 && q < OFF_B4) { base = OFF_W4; kin = H; ioff = IMG_W4; }
-        if (base >= 0) {
-            const int e = q - base, r = e / kin, c = e % kin;
-            *reinterpret_cast<__nv_bfloat16 *>(img + ioff + img_off(r, c, kin)) = __float2bfloat16_rn(w);
-        }
+        for (int c = w; c < nparts; c += RA_GROUPS) g += partial[(int64_t)c * TR_PSTRIDE + q];
+    }
+    sums[w][lane] = g;
+    __syncthreads();
+    if (w != 0 || q > NPARAM) return;
+    g = sums[0][lane];
+#pragma unroll
+    for (int k = 1; k < RA_GROUPS; ++k) g += sums[k][lane];
+    if (q == NPARAM) {
+        if (loss_out) *loss_out = g;
+        return;
+    }
+    if (!adam) {
+        grad_out[q] = g;
+        return;
+    }
+    const float m = b1 * mo[q] + (1.0f - b1) * g;
+    const float v = b2 * vo[q] + (1.0f - b2) * g * g;
+    mo[q] = m;
+    vo[q] = v;
+    const float wq = params[q] - lr * (m / c1) / (sqrtf(v / c2) + eps);
+    params[q] = wq;
+    // re-pack the bf16 image of weight matrices
+    int base = -1, kin = 0, ioff = 0;
+    if (q < OFF_B1) { base = OFF_W1; kin = IN; ioff = IMG_W1; }
+    else if (q >= OFF_W2 && q < OFF_B2) { base = OFF_W2; kin = H; ioff = IMG_W2; }
+    else if (q >= OFF_W3 && q < OFF_B3) { base = OFF_W3; kin = H; ioff = IMG_W3; }
+    else if (q >= OFF_W4 && q < OFF_B4) { base = OFF_W4; kin = H; ioff = IMG_W4; }
+    if (base >= 0) {
+        const int e = q - base, r = e / kin, c = e % kin;
+        *reinterpret_cast<__nv_bfloat16 *>(img + ioff + img_off(r, c, kin)) =
+            __float2bfloat16_rn(base == OFF_W1 && c >= IN_FEAT ? 0.0f : wq);
     }
 }
+constexpr int RA_BLOCKS = (NPARAM + 1 + 31) / 32;
 
 __global__ void k_mlp_pack(const float *params, uint8_t *img) {
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < OFF_B4; q += gridDim.x * blockDim.x) {
@@ -1032,7 +1089,8 @@ __global__ void k_mlp_pack(const float *params, uint8_t *img) {
         else if (q >= OFF_W4 && q < OFF_B4) { base = OFF_W4; kin = H; ioff = IMG_W4; }
         if (base >= 0) {
             const int e = q - base, r = e / kin, c = e % kin;
-            *reinterpret_cast<__nv_bfloat16 *>(img + ioff + img_off(r, c, kin)) = __float2bfloat16_rn(params[q]);
+            *reinterpret_cast<__nv_bfloat16 *>(img + ioff + img_off(r, c, kin)) =
+                __float2bfloat16_rn(base == OFF_W1 && c >= IN_FEAT ? 0.0f : params[q]);
         }
     }
 }
@@ -1286,7 +1344,7 @@ extern "C" rt_status rt_surrogate_loss_grad(const rt_surrogate *s, const float *
     RT_TRY(train_launch(s, S, m, 1.0f / (float)m, st));
     int64_t ntiles = (m + 127) / 128;
     int nparts = (int)(ntiles < s->nparts ? ntiles : s->nparts);
-    k_mlp_reduce_adam<<<(NPARAM + 256) / 256, 256, 0, st>>>(s->partial, nparts, grad_out, loss_out, nullptr,
+    k_mlp_reduce_adam<<<RA_BLOCKS, 32 * RA_GROUPS, 0, st>>>(s->partial, nparts, grad_out, loss_out, nullptr,
                                                            nullptr, nullptr, nullptr, 0.f, 0.f, 0.f, 0.f, 1.f,
                                                            1.f, 0);
     return rt_check_launch();
@@ -1320,7 +1378,7 @@ extern "C" rt_status rt_surrogate_train(rt_surrogate *s, const rt_bvh *bvh, cons
         s->step += 1;
         const double c1 = 1.0 - pow((double)s->cfg.beta1, (double)s->step);
         const double c2 = 1.0 - pow((double)s->cfg.beta2, (double)s->step);
-        k_mlp_reduce_adam<<<(NPARAM + 256) / 256, 256, 0, st>>>(
+        k_mlp_reduce_adam<<<RA_BLOCKS, 32 * RA_GROUPS, 0, st>>>(
             s->partial, nparts, nullptr, loss_curve ? loss_curve + k : nullptr, s->params, s->adam_m, s->adam_v,
             s->img, s->cfg.lr, s->cfg.beta1, s->cfg.beta2, s->cfg.eps, (float)c1, (float)c2, 1);
         RT_TRY(rt_check_launch());
