@@ -247,6 +247,12 @@ struct SampleSrc {
     uint64_t seed;
     int64_t step;
     int64_t R;  // rays in the implicit set
+    // training (mode 2): per-CTA buffer of one tile's drawn samples
+    // ([gridDim][7][128] floats); pf_use: this launch's first tile is there
+    // (drawn by the previous step's launch); pf_make: draw the next step's
+    // first tile into it
+    float *pf;
+    int pf_use, pf_make;
 };
 
 __device__ __forceinline__ bool get_sample(const SampleSrc &S, int64_t i, int64_t m, float3 &p, float3 &d,
@@ -297,7 +303,7 @@ struct SampleIdx {
     bool ok;
 };
 
-__device__ __forceinline__ SampleIdx sample_index(const SampleSrc &S, int64_t i, int64_t m) {
+__device__ __forceinline__ SampleIdx sample_index(const SampleSrc &S, int64_t i, int64_t m, int64_t step) {
     SampleIdx o;
     o.rid = i;
     o.g = 0;
@@ -308,7 +314,7 @@ __device__ __forceinline__ SampleIdx sample_index(const SampleSrc &S, int64_t i,
         o.ok = true;
         return o;
     }
-    uint64_t c[4] = {(uint64_t)i, (uint64_t)S.step, 0ull, 0ull};
+    uint64_t c[4] = {(uint64_t)i, (uint64_t)step, 0ull, 0ull};
     philox4x64_10(c, S.seed, 1ull);
     const int64_t rid = (int64_t)__umul64hi(c[0], (uint64_t)S.R);
     if (rid < 0 || rid >= S.R) return o;
@@ -539,9 +545,10 @@ __global__ void __launch_bounds__(128 * INF_WG, 1) k_mlp_infer(MlpDev net, Sampl
 // finds W1 in B0 and W2 in B1.  Warpgroup 3, which has neither encoding nor
 // dW1 work, draws the next tile's samples into a second sample buffer: the
 // ids while warpgroups 0-2 encode (the sorted position and the target then
-// arrive by asynchronous copies), the mean's copies after its first forward
-// epilogue and the rays while warpgroups 0-2 add the dW1 tile, so the two
-// rounds of dependent global loads never stall the tile.
+// arrive by asynchronous copies), the mean's copies after its last forward
+// epilogue and the rays while warpgroups 0-2 add the dW1 tile, four MMA
+// phases apart, so the two rounds of dependent global loads do not stall
+// the tile.
 constexpr int TR_THREADS = 512;
 constexpr int TR_PSTRIDE = 60040;                // floats per partial (NPARAM + 1 rounded up to 8)
 constexpr int TR_WB0 = 0;                        // 32768: weight buffer 0
@@ -551,11 +558,12 @@ constexpr int TR_H1 = TR_X0 + 20480;             // 32768 each
 constexpr int TR_H2 = TR_H1 + 32768;
 constexpr int TR_H3 = TR_H2 + 32768;
 constexpr int TR_DZ = TR_H3 + 32768;
-// floats: b[4][128], w5[128], db[4][128], dw5[128], z5 partials [4][128], misc[8]
+// floats: b[4][128], w5[128], db[4][128], dw5[128], z5 partials [4][128]
+// (then dw5 partials per warp), misc[16]
 constexpr int TR_F = TR_DZ + 32768;
 // samples of the current and the next tile: [2][7][128] floats (p, d, y;
 // y < 0 marks a row beyond the minibatch)
-constexpr int TR_SMP = TR_F + (4 * 128 + 128 + 4 * 128 + 128 + 4 * 128 + 8) * 4;
+constexpr int TR_SMP = TR_F + (4 * 128 + 128 + 4 * 128 + 128 + 4 * 128 + 16) * 4;
 constexpr int TR_BAR = TR_SMP + 2 * 7 * 128 * 4;
 constexpr int TR_SMEM_TOTAL = TR_BAR + 64;
 static_assert(TR_SMEM_TOTAL <= 232448, "shared memory of the training kernel");
@@ -573,6 +581,15 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                      smem_u32(dst)),
                  "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
+}
+
+// Programmatic dependent launch: wait until the grid launched before this
+// one in the stream has completed and its memory is visible (immediate when
+// this grid was launched without the attribute), and allow the grid
+// launched after this one to start early.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dependents_launch() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 // 13 features of one scalar x (held as the pair xh + xl, see encode()):
@@ -633,10 +650,14 @@ __device__ __forceinline__ void encode_part(uint8_t *x0, int r, int q, bool vali
 }
 
 // a[0..3] += (x, y, z, w) in global memory without a return value (one
-// vector reduction; `a` 16-byte aligned).
-__device__ __forceinline__ void red_add_v4(float *a, float x, float y, float z, float w) {
-    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(a), "f"(x), "f"(y), "f"(z), "f"(w)
-                 : "memory");
+// vector reduction; `a` 16-byte aligned), or a[0..3] = (x, y, z, w) when
+// `store` (the first tile of a partial: no zero fill before it).
+__device__ __forceinline__ void add_v4(float *a, float x, float y, float z, float w, bool store) {
+    if (store)
+        *reinterpret_cast<float4 *>(a) = make_float4(x, y, z, w);
+    else
+        asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(a), "f"(x), "f"(y), "f"(z), "f"(w)
+                     : "memory");
 }
 
 __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleSrc S, int64_t m, float inv_batch,
@@ -652,8 +673,8 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleS
     float *w5 = fb + 512;         // [128]
     float *dbias = fb + 640;      // [4][128]
     float *dw5 = fb + 1152;       // [128]
-    float *z5p = fb + 1280;       // [4][128] per-warpgroup partial logits
-    float *misc = fb + 1792;      // [0] db5, [1] loss
+    float *z5p = fb + 1280;       // [4][128] per-warpgroup partial logits, then per-warp dw5 sums
+    float *misc = fb + 1792;      // [0] db5, [1] loss; [8 + w], [12 + w]: warp w's loss, db5 sums
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + TR_BAR);  // MMA commits
     uint64_t *wbar = bar + 1;                                      // [2] weight copies; bar[3]: drain
     uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + TR_BAR + 32);
@@ -662,19 +683,22 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleS
     const int r = t & 127, q = t >> 7, c0 = 32 * q;
     float *part = partial + (int64_t)blockIdx.x * TR_PSTRIDE;
 
+    const int64_t ntiles = (m + 127) / 128;
+    const int64_t per = (ntiles + gridDim.x - 1) / gridDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * per;
+    const int64_t t1 = t0 + per < ntiles ? t0 + per : ntiles;
+    if (t0 >= t1) return;  // no tiles: no partial (the reduction reads the first ceil(ntiles / per))
+    // Until the grid-dependency wait below the kernel reads nothing that the
+    // launch before it in the stream (the partial reduction and Adam step of
+    // the previous training step, which may still be running under a
+    // programmatic dependent launch) writes, and writes nothing it reads:
+    // shared memory and TMEM set-up, the first tile's samples and encoding.
     if (t < 128) {
-        bias[t] = net.params[OFF_B1 + t];
-        bias[128 + t] = net.params[OFF_B2 + t];
-        bias[256 + t] = net.params[OFF_B3 + t];
-        bias[384 + t] = net.params[OFF_B4 + t];
-        w5[t] = net.params[OFF_W5 + t];
         dw5[t] = 0.0f;
 #pragma unroll
         for (int l = 0; l < 4; ++l) dbias[128 * l + t] = 0.0f;
     }
-    if (t < 8) misc[t] = 0.0f;
-    for (int i = t; i < H * IN; i += TR_THREADS) part[OFF_W1 + i] = 0.0f;
-    const float b5 = net.params[OFF_B5];
+    if (t < 16) misc[t] = 0.0f;
     if (t == 0) {
         mbar_init(bar, 1);
         mbar_init(wbar, 1);
@@ -703,10 +727,6 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleS
     uint32_t phase = 0;
     bool ok = true;
 
-    const int64_t ntiles = (m + 127) / 128;
-    const int64_t per = (ntiles + gridDim.x - 1) / gridDim.x;
-    const int64_t t0 = (int64_t)blockIdx.x * per;
-    const int64_t t1 = t0 + per < ntiles ? t0 + per : ntiles;
 
     // weight copies (thread 0 only): bit b of `pend` / `wph` is buffer b's
     // pending flag / phase
@@ -728,17 +748,13 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleS
             }
         }
     };
-    if (t == 0 && t1 > t0) {
-        load_w(0, IMG_W1, 20480);
-        load_w(1, IMG_W2, 32768);
-    }
     // row r's sample of tile `tile` into sample buffer b (warpgroup 3), in
     // three stages: ids (slots 0, 1: ray id; 3: direction index; 2: sorted
     // position and 6: target by asynchronous copy), the mean (slots 4, 5, 2
     // by asynchronous copy), the ray (slots 0-5)
-    auto draw_ids = [&](int64_t tile, int b) {
+    auto draw_ids = [&](int64_t tile, int b, int64_t step) {
         float *o = smp + b * 7 * 128 + r;
-        const SampleIdx a = sample_index(S, tile * 128 + r, m);
+        const SampleIdx a = sample_index(S, tile * 128 + r, m, step);
         o[0] = __int_as_float((int)(a.rid & 0xffffffff));
         o[128] = __int_as_float((int)(a.rid >> 32));
         o[384] = __int_as_float(a.k);
@@ -791,10 +807,35 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleS
         o[512] = d.y;
         o[640] = d.z;
     };
-    if (q == 3 && t1 > t0) {
-        draw_ids(t0, 0);
-        draw_mean(0);
-        draw_ray(0);
+    if (q == 3) {
+        if (S.pf_use) {
+            const float *pf = S.pf + (int64_t)blockIdx.x * 7 * 128 + r;
+#pragma unroll
+            for (int j = 0; j < 7; ++j) smp[128 * j + r] = pf[128 * j];
+        } else {
+            draw_ids(t0, 0, S.step);
+            draw_mean(0);
+            draw_ray(0);
+        }
+    }
+    __syncthreads();
+    if (q < 3) {  // the first tile's encoding (the loop encodes the others)
+        const float *smr = smp + r;
+        encode_part(x0, r, q, smr[768] >= 0.0f, make_float3(smr[0], smr[128], smr[256]),
+                    make_float3(smr[384], smr[512], smr[640]), net);
+    }
+    grid_dependency_wait();
+    if (t < 128) {
+        bias[t] = net.params[OFF_B1 + t];
+        bias[128 + t] = net.params[OFF_B2 + t];
+        bias[256 + t] = net.params[OFF_B3 + t];
+        bias[384 + t] = net.params[OFF_B4 + t];
+        w5[t] = net.params[OFF_W5 + t];
+    }
+    const float b5 = net.params[OFF_B5];
+    if (t == 0) {
+        load_w(0, IMG_W1, 20480);
+        load_w(1, IMG_W2, 32768);
     }
     __syncthreads();
 
@@ -817,14 +858,18 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleS
     for (int64_t tile = t0; tile < t1 && ok; ++tile) {
         const bool first = tile == t0;
         const int sb = (int)((tile - t0) & 1);
+        // warpgroup 3 draws the samples of the CTA's next tile, or after the
+        // last one those of its first tile in the next training step
+        const bool more = tile + 1 < t1, ahead = more || S.pf_make;
         const float *smr = smp + sb * 7 * 128 + r;
         const float y = smr[768];
         const bool valid = y >= 0.0f;
         if (q < 3) {
-            encode_part(x0, r, q, valid, make_float3(smr[0], smr[128], smr[256]),
-                        make_float3(smr[384], smr[512], smr[640]), net);
-        } else if (tile + 1 < t1) {
-            draw_ids(tile + 1, sb ^ 1);  // completed in this tile's dW1 phase
+            if (!first)
+                encode_part(x0, r, q, valid, make_float3(smr[0], smr[128], smr[256]),
+                            make_float3(smr[384], smr[512], smr[640]), net);
+        } else if (ahead) {
+            draw_ids(more ? tile + 1 : t0, sb ^ 1, more ? S.step : S.step + 1);  // completed in the dW1 phase
         }
         // ---- forward: layer l reads x_l (x0, h1, h2, h3) and W_{l+1} ----
         float h4[32];
@@ -858,7 +903,6 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleS
             for (int k = 0; k < 32; ++k) v[k] += bias[128 * l + c0 + k];
             if (l < 3) {
                 store_chunk_relu(hb(l), r, c0, v);
-                if (l == 0 && q == 3 && tile + 1 < t1) draw_mean(sb ^ 1);
             } else {
                 float zp = 0.0f;
 #pragma unroll
@@ -867,6 +911,8 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleS
                     zp = fmaf(w5[c0 + k], h4[k], zp);
                 }
                 z5p[128 * q + r] = zp;
+                // four MMA phases after the ids: their gathers have landed
+                if (q == 3 && ahead) draw_mean(sb ^ 1);
             }
         }
         __syncthreads();
@@ -886,12 +932,15 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleS
                 lv += __shfl_xor_sync(FULL, lv, off);
                 db5 += __shfl_xor_sync(FULL, db5, off);
             }
-            if (lane == 0) {
-                atomicAdd(misc + 1, lv);
-                atomicAdd(misc + 0, db5);
+            if (lane == 0) {  // read by the first backward epilogue (after a barrier)
+                misc[8 + (warp & 3)] = lv;
+                misc[12 + (warp & 3)] = db5;
             }
         }
-        // dz4 = bf16(dz5 * w5 * [h4 > 0]) (rounded by the store); dw5 += dz5 * h4
+        // dz4 = bf16(dz5 * w5 * [h4 > 0]) (rounded by the store); this
+        // warp's 32 rows of dz5 * h4, summed per column, go to z5p in the
+        // first backward epilogue (z5p is still being read here)
+        float dw5w;
         {
             float g[32];
 #pragma unroll
@@ -900,7 +949,7 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleS
                 h4[k] *= dz5;
             }
             store_chunk(dz, r, c0, g);
-            atomicAdd(dw5 + c0 + lane, transpose_reduce32(h4, lane));
+            dw5w = transpose_reduce32(h4, lane);
         }
         // ---- backward through layers 4, 3, 2: dz_{l+1} (dz or h_{l+1}'s
         // buffer) and W_{l+1} (B1, B0, B1) ----
@@ -926,6 +975,10 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleS
                 if (l == 3) load_w(1, IMG_W2, 32768);                     // W4 read: B1 takes W2
                 if (l == 2 && tile + 1 < t1) load_w(0, IMG_W1, 20480);    // W3 read: B0 takes W1
             }
+            // sums over the tile's rows in a fixed order (no atomics): the
+            // per-warp dw5 sums are stored after one barrier; warpgroup 3
+            // adds them (and the loss and db5 sums) in the dW1 phase
+            if (l == 3) z5p[128 * (warp & 3) + c0 + lane] = dw5w;
             // dz_l = bf16(dX_l) * [h_l > 0] on bf16 pairs, written over h_l
             uint8_t *hl = hb(l - 1);
             float v[32];
@@ -951,15 +1004,16 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleS
             tc_commit(bar);
         }
         wait_mma();
-        // fire-and-forget vector adds: each address of this CTA's partial
-        // is only ever added to by this thread, in tile order, so the sums
-        // are deterministic; warpgroup 3 has no dW1 columns
+        // fire-and-forget vector adds (stores for the first tile): each
+        // address of this CTA's partial is only ever written by this thread,
+        // in tile order, so the sums are deterministic; warpgroup 3 has no
+        // dW1 columns
         if (q < 2) {
             float *row = part + OFF_W1 + (int64_t)r * IN + c0;
             float v[32];
             tmem_ld32(tm_work + lane_off + c0, v);
 #pragma unroll
-            for (int k = 0; k < 8; ++k) red_add_v4(row + 4 * k, v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+            for (int k = 0; k < 8; ++k) add_v4(row + 4 * k, v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3], first);
         } else if (q == 2) {
             // columns 64..95: dW1 64..79 (78: db1), then db4's product (94)
             float *row = part + OFF_W1 + (int64_t)r * IN + c0;
@@ -969,14 +1023,19 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleS
             dbias[384 + r] += v[30];
             v[14] = 0.0f;  // the pad weight's gradient
 #pragma unroll
-            for (int k = 0; k < 4; ++k) red_add_v4(row + 4 * k, v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+            for (int k = 0; k < 4; ++k) add_v4(row + 4 * k, v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3], first);
         } else {
             // columns 96..127: db3's and db2's products (110, 126)
             float v[32];
             tmem_ld32(tm_work + lane_off + c0, v);
             dbias[256 + r] += v[14];
             dbias[128 + r] += v[30];
-            if (tile + 1 < t1) draw_ray(sb ^ 1);  // the next tile's rays, read after its first barrier
+            dw5[r] += (z5p[r] + z5p[128 + r]) + (z5p[256 + r] + z5p[384 + r]);
+            if (r == 0) {
+                misc[1] += (misc[8] + misc[9]) + (misc[10] + misc[11]);
+                misc[0] += (misc[12] + misc[13]) + (misc[14] + misc[15]);
+            }
+            if (ahead) draw_ray(sb ^ 1);  // the next tile's rays, read after its first barrier
         }
         tc_fence_before();
         // the end-of-tile barrier doubles as the vote
@@ -989,6 +1048,9 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleS
             mbar_wait(bar + 3, 0, WAIT_CYCLES);
         }
     }
+    // the partial reduction may be launched now; it waits for this grid
+    // to complete before it reads the partials
+    grid_dependents_launch();
     // weight copies still in flight (only after a give-up): let them land
     if (t == 0) {
 #pragma unroll
@@ -999,7 +1061,14 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleS
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const bool any = t1 > t0 && ok;
+    // the next step's first tile for the next launch
+    if (S.pf_make && q == 3) {
+        const float *o = smp + (int)((t1 - t0) & 1) * 7 * 128 + r;
+        float *pf = S.pf + (int64_t)blockIdx.x * 7 * 128 + r;
+#pragma unroll
+        for (int j = 0; j < 7; ++j) pf[128 * j] = o[128 * j];
+    }
+    const bool any = ok;
     const int offW[3] = {OFF_W2, OFF_W3, OFF_W4};
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
@@ -1039,6 +1108,11 @@ __global__ void __launch_bounds__(32 * RA_GROUPS) k_mlp_reduce_adam(
     const float *partial, int nparts, float *grad_out, float *loss_out, float *params, float *mo, float *vo,
     uint8_t *img, float lr, float b1, float b2, float eps, float c1, float c2, int adam) {
     __shared__ float sums[RA_GROUPS][32];
+    // the partials are complete; only then may the next training launch
+    // start its set-up (which reads the sample buffer the training launch
+    // before this one wrote)
+    grid_dependency_wait();
+    grid_dependents_launch();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int q = blockIdx.x * 32 + lane;
     float g = 0.0f;
@@ -1127,7 +1201,8 @@ struct rt_surrogate {
     uint8_t *img;
     float *partial;  // [nparts][TR_PSTRIDE]
     int nparts;
-    float *scratch;  // [NPARAM+1] misc device scratch
+    float *scratch;   // [NPARAM+1] misc device scratch
+    float *prefetch;  // [nparts][7][128]: the next training step's first tile per CTA
 };
 
 namespace {
@@ -1166,11 +1241,49 @@ rt_status set_smem_attrs() {
     return RT_OK;
 }
 
-rt_status train_launch(const rt_surrogate *s, const SampleSrc &S, int64_t m, float inv_batch, cudaStream_t st) {
+// CTAs of a training launch over m samples, and how many of them have tiles
+// (and so write a partial): the first ceil(ntiles / per), per = ceil(ntiles / grid)
+int train_grid(const rt_surrogate *s, int64_t m) {
+    const int64_t ntiles = (m + 127) / 128;
+    const int grid = (int)(ntiles < s->nparts ? ntiles : s->nparts);
+    return grid < 1 ? 1 : grid;
+}
+int train_parts(const rt_surrogate *s, int64_t m) {
+    const int64_t ntiles = (m + 127) / 128, per = (ntiles + train_grid(s, m) - 1) / train_grid(s, m);
+    return (int)((ntiles + per - 1) / per);
+}
+
+// Launch with programmatic stream serialisation: the kernel may start while
+// the previous one in the stream finishes; it orders its own reads and
+// writes against that kernel with griddepcontrol.wait.
+template <typename... P, typename... A>
+rt_status launch_dependent(void (*kernel)(P...), int grid, int block, size_t smem, cudaStream_t st, A... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, kernel, static_cast<P>(args)...) != cudaSuccess) {
+        cudaGetLastError();
+        return RT_ERR_CUDA;
+    }
+    return RT_OK;
+}
+
+// `dependent`: launched with programmatic stream serialisation (the training
+// loop, where the launch before it is the partial reduction)
+rt_status train_launch(const rt_surrogate *s, const SampleSrc &S, int64_t m, float inv_batch, cudaStream_t st,
+                       bool dependent = false) {
     RT_TRY(set_smem_attrs());
-    int64_t ntiles = (m + 127) / 128;
-    int grid = (int)(ntiles < s->nparts ? ntiles : s->nparts);
-    if (grid < 1) grid = 1;
+    const int grid = train_grid(s, m);
+    if (dependent)
+        return launch_dependent(k_mlp_train, grid, TR_THREADS, TR_SMEM_TOTAL, st, mlp_dev(s), S, m, inv_batch,
+                                s->partial, rt_status_ptr());
     k_mlp_train<<<grid, TR_THREADS, TR_SMEM_TOTAL, st>>>(mlp_dev(s), S, m, inv_batch, s->partial,
                                                          rt_status_ptr());
     RT_TRY(rt_check_launch());
@@ -1218,7 +1331,8 @@ extern "C" rt_status rt_surrogate_create(const rt_mlp_cfg *cfg, uint64_t seed, r
     s->nparts = rt_num_sms();
     const size_t pbytes = ((size_t)(NPARAM + 1) * 4 + 255) & ~(size_t)255;
     static_assert((((size_t)(NPARAM + 1) * 4 + 255) & ~(size_t)255) >= (size_t)TR_PSTRIDE * 4, "partial rows");
-    const size_t total = 3 * pbytes + IMG_BYTES + (size_t)s->nparts * pbytes + pbytes;
+    const size_t total = 3 * pbytes + IMG_BYTES + (size_t)s->nparts * pbytes + pbytes +
+                         (size_t)s->nparts * 7 * 128 * sizeof(float);
     rt_status r = rt_alloc(&s->block, total, stream);
     if (r != RT_OK) {
         delete s;
@@ -1231,6 +1345,7 @@ extern "C" rt_status rt_surrogate_create(const rt_mlp_cfg *cfg, uint64_t seed, r
     s->img = (uint8_t *)(b + 3 * pbytes);
     s->partial = (float *)(b + 3 * pbytes + IMG_BYTES);
     s->scratch = (float *)(b + 3 * pbytes + IMG_BYTES + (size_t)s->nparts * pbytes);
+    s->prefetch = (float *)(b + 3 * pbytes + IMG_BYTES + (size_t)s->nparts * pbytes + pbytes);
     // partial rows are TR_PSTRIDE floats apart (pbytes >= 4 * TR_PSTRIDE)
     k_mlp_init<<<64, 256, 0, st>>>(s->params, seed);
     k_fill<<<64, 256, 0, st>>>(s->adam_m, NPARAM, 0.f);
@@ -1342,8 +1457,7 @@ extern "C" rt_status rt_surrogate_loss_grad(const rt_surrogate *s, const float *
     S.dir = dir;
     S.y = y;
     RT_TRY(train_launch(s, S, m, 1.0f / (float)m, st));
-    int64_t ntiles = (m + 127) / 128;
-    int nparts = (int)(ntiles < s->nparts ? ntiles : s->nparts);
+    const int nparts = train_parts(s, m);
     k_mlp_reduce_adam<<<RA_BLOCKS, 32 * RA_GROUPS, 0, st>>>(s->partial, nparts, grad_out, loss_out, nullptr,
                                                            nullptr, nullptr, nullptr, 0.f, 0.f, 0.f, 0.f, 1.f,
                                                            1.f, 0);
@@ -1370,18 +1484,22 @@ extern "C" rt_status rt_surrogate_train(rt_surrogate *s, const rt_bvh *bvh, cons
     S.seed = seed;
     S.R = R;
     const int64_t B = s->cfg.batch;
-    const int64_t ntiles = (B + 127) / 128;
-    const int nparts = (int)(ntiles < s->nparts ? ntiles : s->nparts);
+    const int nparts = train_parts(s, B);
+    S.pf = s->prefetch;
     for (int32_t k = 0; k < steps; ++k) {
         S.step = s->step;
-        RT_TRY(train_launch(s, S, B, 1.0f / (float)B, st));
+        S.pf_use = k > 0;             // drawn by the previous step's launch
+        S.pf_make = k + 1 < steps;
+        // the first launch follows whatever the stream ran before (no
+        // early start); later ones may overlap the previous reduction
+        RT_TRY(train_launch(s, S, B, 1.0f / (float)B, st, k > 0));
         s->step += 1;
         const double c1 = 1.0 - pow((double)s->cfg.beta1, (double)s->step);
         const double c2 = 1.0 - pow((double)s->cfg.beta2, (double)s->step);
-        k_mlp_reduce_adam<<<RA_BLOCKS, 32 * RA_GROUPS, 0, st>>>(
-            s->partial, nparts, nullptr, loss_curve ? loss_curve + k : nullptr, s->params, s->adam_m, s->adam_v,
-            s->img, s->cfg.lr, s->cfg.beta1, s->cfg.beta2, s->cfg.eps, (float)c1, (float)c2, 1);
-        RT_TRY(rt_check_launch());
+        RT_TRY(launch_dependent(k_mlp_reduce_adam, RA_BLOCKS, 32 * RA_GROUPS, 0, st, s->partial, nparts,
+                                (float *)nullptr, loss_curve ? loss_curve + k : (float *)nullptr, s->params,
+                                s->adam_m, s->adam_v, s->img, s->cfg.lr, s->cfg.beta1, s->cfg.beta2,
+                                s->cfg.eps, (float)c1, (float)c2, 1));
     }
     return RT_OK;
 }

@@ -75,9 +75,6 @@ def test_surrogate_waits_give_up_together_and_context_survives():
     torch.cuda.synchronize()
     assert rt.rt_status_last() == 0
     assert torch.equal(p0, p1)
-    # the per-CTA sums of the bias gradients use shared-memory atomics, so
-    # the gradient is reproducible up to float32 summation order
-    assert torch.allclose(loss1, loss0, rtol=1e-6, atol=0)
-    assert torch.allclose(g1, g0, rtol=1e-4, atol=1e-6 * float(g0.abs().max()))
+    assert torch.equal(loss1, loss0) and torch.equal(g1, g0)  # fixed-order sums
     with pytest.raises(rt.RTError):
         rt.rt_set_wait_limit(-1)

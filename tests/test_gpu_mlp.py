@@ -235,6 +235,39 @@ def test_one_adam_step_matches_oracle(orc, small_trace):
     np.testing.assert_allclose(P1[big], w[big], atol=2e-5)
 
 
+def test_training_is_bit_reproducible_and_split_invariant(small_trace):
+    """Every gradient sum of a training step runs in a fixed order, so a run
+    is bit-reproducible; and five steps in one call (each launch drawing the
+    next step's first tile of samples ahead, for the next launch) equal five
+    calls of one step (each launch drawing its own), loss curve included.  The
+    batch of 40,000 samples is 313 tiles, three per CTA, the last one ragged."""
+    from paper_2311_16043_gb300 import rt
+    sc, dirs, ref, o, d = small_trace
+    dv = {k: _dev(v) for k, v in sc.items()}
+    bvh = rt.rt_build_bvh(dv["mean"], dv["scale"], dv["quat"], dv["opacity"])
+    rs = rt.rayspec(rt.RT_RAYS_DIRS, dirs=_dev(dirs))
+    T_target = _dev(ref["T"].astype(np.float32))
+    P = _dev(rand_params(13))
+
+    def run(split):
+        s = rt.rt_surrogate_create(rt.mlp_cfg(batch=40000, lr=1e-3, pos_weight=4.0), seed=1)
+        rt.rt_surrogate_set_params(s, P)
+        if split:
+            curve = torch.cat([rt.rt_surrogate_train(s, bvh, rs, T_target, steps=1, seed=77) for _ in range(5)])
+        else:
+            curve = rt.rt_surrogate_train(s, bvh, rs, T_target, steps=5, seed=77)
+        torch.cuda.synchronize()
+        return rt.rt_surrogate_get_params(s), curve
+
+    pa, ca = run(False)
+    pb, cb = run(False)
+    pc, cc = run(True)
+    assert rt.rt_status_last() == 0
+    assert torch.equal(pa, pb) and torch.equal(ca, cb)
+    assert torch.equal(pa, pc) and torch.equal(ca, cc)
+    assert not torch.equal(pa, P)  # the steps moved the weights
+
+
 def test_training_and_fallback():
     """The bench workload: train on the tracer's visibility table of the
     2M-Gaussian object scene x 128 directions (weight 4 on the lit term,
