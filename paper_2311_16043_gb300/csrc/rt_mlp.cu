@@ -567,6 +567,8 @@ constexpr int TR_SMP = TR_F + (4 * 128 + 128 + 4 * 128 + 128 + 4 * 128 + 16) * 4
 constexpr int TR_BAR = TR_SMP + 2 * 7 * 128 * 4;
 constexpr int TR_SMEM_TOTAL = TR_BAR + 64;
 static_assert(TR_SMEM_TOTAL <= 232448, "shared memory of the training kernel");
+constexpr int TR_ROWB = 528;  // padded row of the dW staging area at the flush
+static_assert(3 * 128 * TR_ROWB <= TR_F && TR_ROWB % 16 == 0, "dW staging below the float area");
 static_assert(TR_PSTRIDE >= NPARAM + 1 && TR_PSTRIDE % 4 == 0, "partial stride");
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
@@ -590,6 +592,19 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 __device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void grid_dependents_launch() {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Bulk async copy shared -> global (16-byte aligned, size a multiple of 16)
+// in this thread's bulk group; bulk_commit_wait() waits for the group's
+// copies to complete.
+__device__ __forceinline__ void bulk_s2g(void *dst, const void *src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit_wait() {
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
 // 13 features of one scalar x (held as the pair xh + xl, see encode()):
@@ -1069,10 +1084,15 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleS
         for (int j = 0; j < 7; ++j) pf[128 * j] = o[128 * j];
     }
     const bool any = ok;
-    const int offW[3] = {OFF_W2, OFF_W3, OFF_W4};
+    // dW2..dW4: TMEM -> shared memory rows (every activation and weight
+    // buffer is dead now; rows padded to TR_ROWB bytes so that each 16-byte
+    // store of a warp hits 8 distinct bank groups) -> one bulk copy per row
+    // into the partial (stores straight from the row-per-thread registers
+    // would write 16 bytes per 512-byte row stride across a warp)
+    uint8_t *stage = smem;  // [3][128] rows
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
-        float4 *row = reinterpret_cast<float4 *>(part + offW[l] + (int64_t)r * H + c0);
+        float4 *row = reinterpret_cast<float4 *>(stage + (l * 128 + r) * TR_ROWB + c0 * 4);
         float v[32];
         tmem_ld32(tm_dw(l) + lane_off + c0, v);
 #pragma unroll
@@ -1080,7 +1100,14 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(MlpDev net, SampleS
             row[k] = any ? make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3])
                          : make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    fence_async_smem();  // the rows, written by this proxy, are read by the bulk copies
     __syncthreads();
+    if (q == 0) {
+        const int offW[3] = {OFF_W2, OFF_W3, OFF_W4};
+#pragma unroll
+        for (int l = 0; l < 3; ++l) bulk_s2g(part + offW[l] + r * H, stage + (l * 128 + r) * TR_ROWB, H * 4);
+        bulk_commit_wait();
+    }
     if (t < 128) {
         part[OFF_B1 + t] = any ? dbias[t] : 0.0f;
         part[OFF_B2 + t] = any ? dbias[128 + t] : 0.0f;
@@ -1117,8 +1144,19 @@ __global__ void __launch_bounds__(32 * RA_GROUPS) k_mlp_reduce_adam(
     const int q = blockIdx.x * 32 + lane;
     float g = 0.0f;
     if (q <= NPARAM) {
-#pragma unroll 8
-        for (int c = w; c < nparts; c += RA_GROUPS) g += partial[(int64_t)c * TR_PSTRIDE + q];
+        // the first RA_BATCH partials of this warp loaded before any is
+        // added, so they are all in flight at once
+        constexpr int RA_BATCH = 19;
+        float x[RA_BATCH];
+#pragma unroll
+        for (int i = 0; i < RA_BATCH; ++i) {
+            const int c = w + RA_GROUPS * i;
+            x[i] = c < nparts ? __ldcg(partial + (int64_t)c * TR_PSTRIDE + q) : 0.0f;
+        }
+#pragma unroll
+        for (int i = 0; i < RA_BATCH; ++i) g += x[i];
+        for (int c = w + RA_GROUPS * RA_BATCH; c < nparts; c += RA_GROUPS)
+            g += __ldcg(partial + (int64_t)c * TR_PSTRIDE + q);
     }
     sums[w][lane] = g;
     __syncthreads();
