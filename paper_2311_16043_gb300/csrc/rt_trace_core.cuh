@@ -890,14 +890,17 @@ __device__ __forceinline__ float trace_warp_ray(const BvhDev &b, float3 o, float
         const uint32_t node = active ? wstk[size - 1 - lane] : 0u;
         size -= k;
         __syncwarp();
-        uint32_t push[4];
-        int n_push = 0;
+        // internal children to push: a mask over c (a register array indexed by
+        // a running count would live in local memory)
+        uint32_t r[4] = {0u, 0u, 0u, 0u}, pm = 0u;
         if (active) {
             const float4 *w = b.wide + 8 * (int64_t)node;
             const float4 lx = __ldg(w), hx = __ldg(w + 1), ly = __ldg(w + 2), hy = __ldg(w + 3),
                          lz = __ldg(w + 4), hz = __ldg(w + 5), rf = __ldg(w + 6);
-            const uint32_t r[4] = {__float_as_uint(rf.x), __float_as_uint(rf.y), __float_as_uint(rf.z),
-                                   __float_as_uint(rf.w)};
+            r[0] = __float_as_uint(rf.x);
+            r[1] = __float_as_uint(rf.y);
+            r[2] = __float_as_uint(rf.z);
+            r[3] = __float_as_uint(rf.w);
             bool h[4];
             slab4(lx, hx, ly, hy, lz, hz, oi, inv, h);
             if (COUNT) wc.box += (r[0] != RT_EMPTY) + (r[1] != RT_EMPTY) + (r[2] != RT_EMPTY) + (r[3] != RT_EMPTY);
@@ -911,11 +914,12 @@ __device__ __forceinline__ float trace_warp_ray(const BvhDev &b, float3 o, float
                         if (gauss_hit(b, p, o, d, Tl) && COUNT) wc.hits++;
                     }
                 } else {
-                    push[n_push++] = r[c];
+                    pm |= 1u << c;
                 }
             }
         }
         // warp prefix sum of the pushes, then write them above the stack top
+        const int n_push = __popc(pm);
         int pre = n_push;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
@@ -923,8 +927,10 @@ __device__ __forceinline__ float trace_warp_ray(const BvhDev &b, float3 o, float
             if (lane >= off) pre += v;
         }
         const int total = __shfl_sync(FULL, pre, 31);
-        const int base = size + pre - n_push;
-        for (int q = 0; q < n_push; ++q) wstk[base + q] = push[q];
+        int at = size + pre - n_push;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if ((pm >> c) & 1u) wstk[at++] = r[c];
         size += total;
         __syncwarp();
         if (warp_product(Tl) < b.t_min || size == 0) break;
