@@ -86,14 +86,15 @@ def test_refit_reports_bad_inputs_through_the_status_word():
     assert rt.rt_status_last() == 0
 
 
-@pytest.mark.parametrize("pinned", [True, False])
-def test_precompute_from_host_buffers(pinned):
+@pytest.mark.parametrize("pinned,K", [(True, 32), (False, 32), (True, 100), (True, 128), (False, 128)])
+def test_precompute_from_host_buffers(pinned, K):
     """rt_visibility_dirs_host (copies in, build, trace, copy out) gives the
     device path's table bit for bit, from page-locked or pageable memory,
-    with the library's pool and with the caller's allocator."""
+    with the library's pool and with the caller's allocator, for direction
+    counts that are and are not multiples of the warp width."""
     from paper_2311_16043_gb300 import rt
     sc = scenes.object_scene(30_000, 4)
-    dirs_np = scenes.fibonacci_sphere(32)
+    dirs_np = scenes.fibonacci_sphere(K)
     d = _dev(sc)
     bvh = rt.rt_build_bvh(d["mean"], d["scale"], d["quat"], d["opacity"])
     ref = rt.rt_trace_visibility_dirs(bvh, torch.from_numpy(dirs_np).cuda()).cpu()
@@ -106,7 +107,7 @@ def test_precompute_from_host_buffers(pinned):
     for torch_alloc in (False, True):
         rt.use_torch_allocator(torch_alloc)
         try:
-            hT = torch.full((30_000, 32), -1.0, pin_memory=pinned)
+            hT = torch.full((30_000, K), -1.0, pin_memory=pinned)
             out = rt.rt_visibility_dirs_host(host["mean"], host["scale"], host["quat"], host["opacity"], hdirs, hT)
             torch.cuda.synchronize()
         finally:
