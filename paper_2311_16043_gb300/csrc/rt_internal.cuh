@@ -80,6 +80,10 @@ int *rt_status_ptr();
 rt_status rt_check_launch();
 rt_status rt_alloc(void **p, size_t bytes, rt_stream_t s);
 void rt_free(void *p, rt_stream_t s);
+// Stable LSD radix sort (8-bit digits) of n <= 2^31 (key, value) pairs in
+// place by the low `bits` bits of the keys; scratch from rt_alloc, released
+// in stream order (rt_build.cu).
+rt_status rt_sort_pairs_u32(uint32_t *keys, int32_t *vals, int64_t n, int bits, rt_stream_t stream);
 int rt_num_sms();
 
 #define RT_TRY(x)                              \

@@ -245,6 +245,52 @@ def test_warp_per_ray_id_subset(small):
     rt.rt_status_clear()
 
 
+@pytest.mark.parametrize("kind", ["dirs", "hemi"])
+def test_long_id_list_sorted_trace(orc, kind):
+    """AUTO on an id list longer than 2^22 rays traces it sorted by
+    (direction, the tree's order) and writes each T back to its place: the
+    same values, bit for bit, as the per-ray traversal of the list in the
+    caller's order; an invalid id among them gives NaN at its place and sets
+    the status.  300k object scene x 32 directions, 5M of its 9.6M rays in
+    random order; 256 of them against the oracle's CPU BVH tracer."""
+    from paper_2311_16043_gb300 import rt
+    sc = scenes.object_scene(300_000, 2)
+    bvh = build(sc)
+    K = 32
+    if kind == "dirs":
+        dirs = scenes.fibonacci_sphere(K)
+        rs_kw = dict(dirs=_dev(dirs))
+        rkind = rt.RT_RAYS_DIRS
+    else:
+        nrm = scenes.shortest_axis_normals(sc["scale"], sc["quat"])
+        rs_kw = dict(dirs=_dev(scenes.fibonacci_hemisphere(K)), normals=_dev(nrm))
+        rkind = rt.RT_RAYS_HEMI
+    rng = np.random.default_rng(21)
+    sel = rng.permutation(300_000 * K)[:5_000_000].astype(np.int64)
+    rs = rt.rayspec(rkind, ray_ids=_dev(sel), **rs_kw)
+    T_auto = rt.rt_trace_visibility(bvh, rs)
+    T_ray = rt.rt_trace_visibility(bvh, rs, opts=rt.trace_opts(kernel=rt.RT_KERNEL_RAY_WIDE))
+    torch.cuda.synchronize()
+    assert rt.rt_status_last() == 0
+    assert torch.equal(T_auto, T_ray)
+    if kind == "dirs":
+        pick = rng.choice(sel.size, 256, replace=False)
+        ref = orc.BvhTracer(sc).trace_dirs(dirs, ids=sel[pick])
+        ok = ref["flags"] == 0
+        assert ok.mean() > 0.95
+        err = np.abs(T_auto.cpu().numpy()[pick].astype(np.float64) - ref["T"])
+        assert err[ok].max() <= TOL
+    bad = sel.copy()
+    bad[123_456] = 300_000 * K
+    T_bad = rt.rt_trace_visibility(bvh, rt.rayspec(rkind, ray_ids=_dev(bad), **rs_kw))
+    torch.cuda.synchronize()
+    assert rt.rt_status_last() == 1
+    rt.rt_status_clear()
+    Tb = T_bad.cpu().numpy()
+    assert np.isnan(Tb[123_456]) and np.isfinite(np.delete(Tb, 123_456)).all()
+    assert np.array_equal(np.delete(Tb, 123_456), np.delete(T_ray.cpu().numpy(), 123_456))
+
+
 def test_materialized_rays_bit_exact(orc, small):
     from paper_2311_16043_gb300 import rt
     sc, dirs, _ = small
