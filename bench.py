@@ -55,9 +55,9 @@ KERNEL_NAMES = ["auto", "per-ray binary", "packet binary", "packet 4-wide", "per
 ENV_SAMPLES = 512
 METRIC = "traced rays/s & ms per 2M-Gaussian visibility precompute; surrogate speedup at MAE"
 TRACE_SOURCES = ["paper_2311_16043_gb300/csrc/rt_trace.cu", "paper_2311_16043_gb300/csrc/rt_trace_core.cuh"]
-# input check, bounds, morton, 4 x (hist, scan, scatter), perm, prep, karras,
-# refit, and the 4-wide collapse: one launch per level, 63 levels
-BUILD_KERNELS_PER_STEP = 19 + 63
+# input check, bounds, morton, 4 x (hist, 3-kernel scan, scatter), perm,
+# prep, karras, refit, and the 4-wide collapse: one launch per level, 63 levels
+BUILD_KERNELS_PER_STEP = 27 + 63
 
 
 def parse():
