@@ -860,7 +860,8 @@ def main():
                 e_ms.append(e0.elapsed_time(e1))
         e_clk = e_clocks.stop()
         # this machine's host link, for reading the gap between e2e and value:
-        # one plain copy of the T table to the same page-locked buffer
+        # one plain copy of the T table to the same page-locked buffer, right
+        # after the last step's copy (a warm link)
         c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         c0.record()
         hT.copy_(T, non_blocking=True)
@@ -887,6 +888,13 @@ def main():
         phases = {"h2d_ms": pe[0].elapsed_time(pe[1]), "build_ms": pe[1].elapsed_time(pe[2]),
                   "trace_ms": pe[2].elapsed_time(pe[3]), "d2h_ms": pe[3].elapsed_time(pe[4])}
         phases["sum_ms"] = sum(phases.values())
+        # the same copy again, back to back: the first host transfer after the
+        # link has idled (here through the trace) runs slower than a repeat
+        c0.record()
+        hT.copy_(T, non_blocking=True)
+        c1.record()
+        torch.cuda.synchronize()
+        phases["d2h_repeat_ms"] = c0.elapsed_time(c1)
         em = reduce_max(statistics.mean(e_ms), world, dev)
         e2e = {"value": replica_rate(R, em, world), "unit": "rays/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": em, "ms_each": e_ms,
