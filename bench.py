@@ -888,8 +888,8 @@ def main():
         phases = {"h2d_ms": pe[0].elapsed_time(pe[1]), "build_ms": pe[1].elapsed_time(pe[2]),
                   "trace_ms": pe[2].elapsed_time(pe[3]), "d2h_ms": pe[3].elapsed_time(pe[4])}
         phases["sum_ms"] = sum(phases.values())
-        # the same copy again, back to back: the first host transfer after the
-        # link has idled (here through the trace) runs slower than a repeat
+        # the same copy again, back to back (the host link's rate varies from
+        # moment to moment on a shared machine)
         c0.record()
         hT.copy_(T, non_blocking=True)
         c1.record()
