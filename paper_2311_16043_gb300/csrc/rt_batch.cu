@@ -145,24 +145,23 @@ __device__ __forceinline__ void batch_refill(const BatchJobDev *__restrict__ job
                      hz = __ldg(w + 5), rf = __ldg(w + 6);
         const uint32_t r[4] = {__float_as_uint(rf.x), __float_as_uint(rf.y), __float_as_uint(rf.z),
                                __float_as_uint(rf.w)};
-        bool h[4];
-        slab4(lx, hx, ly, hy, lz, hz, oi, inv, h);
-        int next = -1;
-        bool overflow = false;
+        float tn[4];
+        slab4_near(lx, hx, ly, hy, lz, hz, oi, inv, tn);
+        const float inf = __int_as_float(0x7f800000);
+        float ti[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            if (!h[c]) continue;
+            ti[c] = inf;
+            if (!(tn[c] < inf)) continue;
             if (r[c] & RT_LEAF_BIT) {
                 const int32_t p = (int32_t)(r[c] & ~RT_LEAF_BIT);
                 if (p != src) gauss_hit(b, p, o, d, T);
-            } else if (next < 0) {
-                next = (int)r[c];
-            } else if (sp < RT_WIDE_STACK) {
-                stack[sp++] = r[c];
             } else {
-                overflow = true;
+                ti[c] = tn[c];
             }
         }
+        int next = -1;
+        const bool overflow = !near_first(ti[0], ti[1], ti[2], ti[3], r[0], r[1], r[2], r[3], stack, sp, next);
         if (overflow) rt_set_error(status, RT_ERR_STACK_OVERFLOW);
         bool done = overflow || T < b.t_min;
         if (!done) {

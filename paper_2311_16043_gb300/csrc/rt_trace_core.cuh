@@ -105,6 +105,67 @@ __device__ __forceinline__ void slab4(float4 lx, float4 hx, float4 ly, float4 hy
           make_float2(lz.z, lz.w), make_float2(hz.z, hz.w), ix, iy, iz, ox, oy, oz, h[2], h[3]);
 }
 
+// The four children of a 4-wide node against a ray: each box's entry
+// distance along the ray (the near distance of slab2's test), +inf where
+// the ray misses the box.
+__device__ __forceinline__ void slab4_near(float4 lx, float4 hx, float4 ly, float4 hy, float4 lz, float4 hz,
+                                           float3 oi, float3 inv, float (&tn)[4]) {
+    const float2 ix = make_float2(inv.x, inv.x), iy = make_float2(inv.y, inv.y), iz = make_float2(inv.z, inv.z);
+    const float2 ox = make_float2(-oi.x, -oi.x), oy = make_float2(-oi.y, -oi.y), oz = make_float2(-oi.z, -oi.z);
+    const float inf = __int_as_float(0x7f800000);
+#pragma unroll
+    for (int pr = 0; pr < 2; ++pr) {
+        const float2 l_x = pr ? make_float2(lx.z, lx.w) : make_float2(lx.x, lx.y);
+        const float2 h_x = pr ? make_float2(hx.z, hx.w) : make_float2(hx.x, hx.y);
+        const float2 l_y = pr ? make_float2(ly.z, ly.w) : make_float2(ly.x, ly.y);
+        const float2 h_y = pr ? make_float2(hy.z, hy.w) : make_float2(hy.x, hy.y);
+        const float2 l_z = pr ? make_float2(lz.z, lz.w) : make_float2(lz.x, lz.y);
+        const float2 h_z = pr ? make_float2(hz.z, hz.w) : make_float2(hz.x, hz.y);
+        const float2 tx0 = __ffma2_rn(l_x, ix, ox), tx1 = __ffma2_rn(h_x, ix, ox);
+        const float2 ty0 = __ffma2_rn(l_y, iy, oy), ty1 = __ffma2_rn(h_y, iy, oy);
+        const float2 tz0 = __ffma2_rn(l_z, iz, oz), tz1 = __ffma2_rn(h_z, iz, oz);
+        const float na = fmaxf(fmaxf(fminf(tx0.x, tx1.x), fminf(ty0.x, ty1.x)), fmaxf(fminf(tz0.x, tz1.x), 0.0f));
+        const float fa = fminf(fminf(fmaxf(tx0.x, tx1.x), fmaxf(ty0.x, ty1.x)), fmaxf(tz0.x, tz1.x));
+        const float nb = fmaxf(fmaxf(fminf(tx0.y, tx1.y), fminf(ty0.y, ty1.y)), fmaxf(fminf(tz0.y, tz1.y), 0.0f));
+        const float fb = fminf(fminf(fmaxf(tx0.y, tx1.y), fmaxf(ty0.y, ty1.y)), fmaxf(tz0.y, tz1.y));
+        tn[2 * pr] = na <= fmaf(fabsf(fa), 1e-6f, fa) ? na : inf;
+        tn[2 * pr + 1] = nb <= fmaf(fabsf(fb), 1e-6f, fb) ? nb : inf;
+    }
+}
+
+__device__ __forceinline__ void cswap_near(float &ta, uint32_t &qa, float &tb, uint32_t &qb) {
+    const bool sw = tb < ta;
+    const float t = sw ? tb : ta;
+    const uint32_t q = sw ? qb : qa;
+    tb = sw ? ta : tb;
+    qb = sw ? qa : qb;
+    ta = t;
+    qa = q;
+}
+
+// The per-ray walk's next node among a visited node's internal children hit
+// (entry distances t, +inf for the others): the nearest becomes `next` (-1:
+// none) and the rest are pushed far-first, so the stack pops them
+// near-first; the hits close to the origin, where a ray's transmittance
+// falls first, come early and the walk stops sooner once T < T_min.
+// Returns false (nothing pushed) if the stack would overflow.
+__device__ __forceinline__ bool near_first(float t0, float t1, float t2, float t3, uint32_t r0, uint32_t r1,
+                                           uint32_t r2, uint32_t r3, uint32_t *stack, int &sp, int &next) {
+    const float inf = __int_as_float(0x7f800000);
+    cswap_near(t0, r0, t1, r1);
+    cswap_near(t2, r2, t3, r3);
+    cswap_near(t0, r0, t2, r2);
+    cswap_near(t1, r1, t3, r3);
+    cswap_near(t1, r1, t2, r2);
+    next = t0 < inf ? (int)r0 : -1;
+    const int n = (t1 < inf) + (t2 < inf) + (t3 < inf);
+    if (sp + n > RT_WIDE_STACK) return false;
+    if (t3 < inf) stack[sp++] = r3;
+    if (t2 < inf) stack[sp++] = r2;
+    if (t1 < inf) stack[sp++] = r1;
+    return true;
+}
+
 // slab_sorted for two children at once: the plane distances of both along
 // an axis come from one packed FMA (fma.rn.f32x2 rounds each half as fmaf),
 // so the results equal two slab_sorted calls and each packed instruction
@@ -518,14 +579,15 @@ __device__ __forceinline__ void trace_ray_wide_run(const BvhDev &b, float3 o, fl
                      hz = __ldg(w + 5), rf = __ldg(w + 6);
         const uint32_t r[4] = {__float_as_uint(rf.x), __float_as_uint(rf.y), __float_as_uint(rf.z),
                                __float_as_uint(rf.w)};
-        bool h[4];
-        slab4(lx, hx, ly, hy, lz, hz, oi, inv, h);
+        float tn[4];
+        slab4_near(lx, hx, ly, hy, lz, hz, oi, inv, tn);
         if (COUNT) wc.box += (r[0] != RT_EMPTY) + (r[1] != RT_EMPTY) + (r[2] != RT_EMPTY) + (r[3] != RT_EMPTY);
-        int next = -1;
-        bool overflow = false;
+        const float inf = __int_as_float(0x7f800000);
+        float ti[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            if (!h[c]) continue;
+            ti[c] = inf;
+            if (!(tn[c] < inf)) continue;
             if (r[c] & RT_LEAF_BIT) {
                 const int32_t p = (int32_t)(r[c] & ~RT_LEAF_BIT);
                 if (p != src) {
@@ -535,14 +597,12 @@ __device__ __forceinline__ void trace_ray_wide_run(const BvhDev &b, float3 o, fl
                         log_hit(lg, b, p);
                     }
                 }
-            } else if (next < 0) {
-                next = (int)r[c];
-            } else if (sp < RT_WIDE_STACK) {
-                stack[sp++] = r[c];
             } else {
-                overflow = true;
+                ti[c] = tn[c];
             }
         }
+        int next = -1;
+        const bool overflow = !near_first(ti[0], ti[1], ti[2], ti[3], r[0], r[1], r[2], r[3], stack, sp, next);
         if (overflow) {
             rt_set_error(status, RT_ERR_STACK_OVERFLOW);
             break;
@@ -806,28 +866,27 @@ __device__ __forceinline__ void trace_refill(const BvhDev &b, const RaySetDev &r
                      hz = __ldg(w + 5), rf = __ldg(w + 6);
         const uint32_t r[4] = {__float_as_uint(rf.x), __float_as_uint(rf.y), __float_as_uint(rf.z),
                                __float_as_uint(rf.w)};
-        bool h[4];
-        slab4(lx, hx, ly, hy, lz, hz, oi, inv, h);
+        float tn[4];
+        slab4_near(lx, hx, ly, hy, lz, hz, oi, inv, tn);
         if (COUNT) wc.box += (r[0] != RT_EMPTY) + (r[1] != RT_EMPTY) + (r[2] != RT_EMPTY) + (r[3] != RT_EMPTY);
-        int next = -1;
-        bool overflow = false;
+        const float inf = __int_as_float(0x7f800000);
+        float ti[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            if (!h[c]) continue;
+            ti[c] = inf;
+            if (!(tn[c] < inf)) continue;
             if (r[c] & RT_LEAF_BIT) {
                 const int32_t p = (int32_t)(r[c] & ~RT_LEAF_BIT);
                 if (p != src) {
                     if (COUNT) wc.gauss++;
                     if (gauss_hit(b, p, o, d, T) && COUNT) wc.hits++;
                 }
-            } else if (next < 0) {
-                next = (int)r[c];
-            } else if (sp < RT_WIDE_STACK) {
-                stack[sp++] = r[c];
             } else {
-                overflow = true;
+                ti[c] = tn[c];
             }
         }
+        int next = -1;
+        const bool overflow = !near_first(ti[0], ti[1], ti[2], ti[3], r[0], r[1], r[2], r[3], stack, sp, next);
         if (overflow) rt_set_error(aux.status, RT_ERR_STACK_OVERFLOW);
         bool done = overflow || T < b.t_min;
         if (!done) {
