@@ -243,10 +243,12 @@ rt_status rt_materialize_rays(const rt_bvh *bvh, const rt_rayspec *rays, const i
 /* ------------------------------------------------------------------------ */
 
 typedef enum {
-    RT_KERNEL_AUTO = 0,   /* DIRS sets: WIDE; ENV and HEMI sets: RAY_REFILL;
-                             explicit rays and id lists: WARP_RAY up to 2^22
-                             rays (RAY_WIDE with a hit log), RAY_WIDE beyond;
-                             the binary forms when there is no 4-wide tree   */
+    RT_KERNEL_AUTO = 0,   /* DIRS sets: RAY_WIDE up to 2^19 Gaussians, WIDE
+                             beyond; ENV and HEMI sets: RAY_REFILL; explicit
+                             rays and id lists: WARP_RAY up to 2^22 rays
+                             (RAY_WIDE with a hit log), RAY_WIDE beyond (an id
+                             list traced in the tree's order); the binary
+                             forms when there is no 4-wide tree              */
     RT_KERNEL_RAY = 1,    /* one thread per ray, private stack, binary tree    */
     RT_KERNEL_PACKET = 2, /* one warp per 32 rays of neighbouring Gaussians in
                              one direction, shared stack, binary tree          */
