@@ -199,16 +199,18 @@ rt_status rt_trace_launch(const rt_bvh *bvh, const rt_rayspec *rays, float *T_ou
               : o.kernel == RT_KERNEL_PACKET ? 1 : 0;
     // one warp per ray needs the 4-wide tree and keeps no hit log
     if (strat == 6 && (bvh->n_wide == 0 || o.hit_ids)) strat = bvh->n_wide ? 4 : 0;
-    // AUTO: warp packets sharing the direction for a direction set; per-ray
-    // traversal with lane refill for env-map and hemisphere sets (directions
-    // differ across a tile); for explicit rays and id lists (scattered rays)
-    // one warp per ray up to 2^22 rays, whose lanes share one ray's nodes
-    // (2M object scene, scattered ids: 2^16 rays 3.7x and 2^20 rays 1.25x
-    // the per-ray traversals), and one thread per ray over the 4-wide tree
-    // for longer lists (2^24 rays: 6 % faster than one warp per ray)
-    // (direction sets of up to 2^19 Gaussians: the per-ray walk with its
-    // near-first order beats the packets — object scenes: 100k 18 %, 300k
-    // 5 %, 500k 2.7 % faster; 1M and up the packets win)
+    // AUTO:
+    // - a direction set: warp packets sharing the direction, except over at
+    //   most 2^19 Gaussians, where the per-ray walk with its near-first order
+    //   is faster (object scenes: 100k 18 %, 300k 5 %, 500k 2.7 %; from 1M
+    //   on the packets win);
+    // - env-map and hemisphere sets (directions differ across a tile): the
+    //   per-ray walk with lane refill;
+    // - explicit rays and id lists (scattered rays): one warp per ray up to
+    //   2^22 rays, its lanes sharing one ray's nodes (2M object scene,
+    //   scattered ids: 2^16 rays 3.7x and 2^20 rays 1.25x the per-ray
+    //   walks), and one thread per ray over the 4-wide tree for longer lists
+    //   (2^24 rays: 6 % faster than one warp per ray).
     if (o.kernel == RT_KERNEL_AUTO && job.mode == MODE_FULL)
         strat = rays->kind == RT_RAYS_DIRS ? (bvh->n <= (int64_t(1) << 19) ? 4 : 2) : 5;
     if (o.kernel == RT_KERNEL_AUTO && job.mode != MODE_FULL) strat = count <= (int64_t(1) << 22) ? 6 : 4;

@@ -67,16 +67,6 @@ __device__ __forceinline__ bool slab(float lox, float hix, float loy, float hiy,
     return tnear <= fmaf(fabsf(tfar), 1e-6f, tfar);
 }
 
-// Slab test with the planes already ordered along the ray (near plane first
-// on every axis): same result as slab() without the per-axis min/max.
-__device__ __forceinline__ bool slab_sorted(float nx, float fx, float ny, float fy, float nz, float fz,
-                                            float3 oi, float3 inv) {
-    const float tnear = fmaxf(fmaxf(fmaf(nx, inv.x, -oi.x), fmaf(ny, inv.y, -oi.y)),
-                              fmaxf(fmaf(nz, inv.z, -oi.z), 0.0f));
-    const float tfar = fminf(fminf(fmaf(fx, inv.x, -oi.x), fmaf(fy, inv.y, -oi.y)), fmaf(fz, inv.z, -oi.z));
-    return tnear <= fmaf(fabsf(tfar), 1e-6f, tfar);
-}
-
 // slab for two children at once (children a, b of a 4-wide node, lo/hi as
 // (a, b) pairs), packed FMAs as in slab_sorted2; same results as two slab
 // calls.
@@ -166,9 +156,10 @@ __device__ __forceinline__ bool near_first(float t0, float t1, float t2, float t
     return true;
 }
 
-// slab_sorted for two children at once: the plane distances of both along
-// an axis come from one packed FMA (fma.rn.f32x2 rounds each half as fmaf),
-// so the results equal two slab_sorted calls and each packed instruction
+// The slab test of two children at once with the planes already ordered
+// along the ray (near plane first on every axis: slab() without the per-axis
+// min/max): the plane distances of both along an axis come from one packed
+// FMA (fma.rn.f32x2 rounds each half as fmaf), so each packed instruction
 // does the work of two issued ones.  i* = (inv, inv), o* = (-oi, -oi).
 __device__ __forceinline__ void slab_sorted2(float2 nx, float2 fx, float2 ny, float2 fy, float2 nz, float2 fz,
                                              float2 ix, float2 iy, float2 iz, float2 ox, float2 oy, float2 oz,
