@@ -63,7 +63,7 @@ def _load():
         sig = {
             "oracle_rotation": (None, [P, P]),
             "oracle_trace": (None, [i64, P, P, P, P, i64, P, P, P, f64, f64, f64,
-                                    f64, f64, f64, f64, P, P, P, P]),
+                                    f64, f64, f64, f64, P, P, P, P, P, P]),
             "oracle_trace_hits": (None, [i64, P, P, P, P, i64, P, P, P, f64, f64, i32, P, P]),
             "oracle_trace_grad": (None, [i64, P, P, P, P, i64, P, P, P, f64, f64, f64,
                                          P, P, P, P, P, P]),
@@ -75,9 +75,9 @@ def _load():
             "oracle_leaf_boxes": (None, [i64, P, P, P, P, f64, f64, i32, P]),
             "oracle_bvh_create": (P, [i64, P, P, P, P, f64, f64]),
             "oracle_bvh_destroy": (None, [P]),
-            "oracle_bvh_trace": (None, [P, i64, P, P, P, f64, f64, f64, f64, f64, P, P, P, P, P]),
+            "oracle_bvh_trace": (None, [P, i64, P, P, P, f64, f64, f64, f64, f64, P, P, P, P, P, P, P]),
             "oracle_bvh_trace_dirs": (None, [P, i32, P, f32, P, i64, f64, f64, f64, f64, f64,
-                                             P, P, P, P, P]),
+                                             P, P, P, P, P, P, P]),
             "oracle_hemi_rays": (None, [i64, P, P, i32, P, f32, P, i64, P, P, P]),
             "oracle_brdf_spec": (None, [i64, P, P, P, P, P, P]),
             "oracle_sh_basis": (None, [i64, P, P]),
@@ -123,7 +123,10 @@ def rotation(q) -> np.ndarray:
 
 def trace(scene, ray_o, ray_d, ray_src=None, k_sigma=3.0, alpha_min=1.0 / 255.0,
           t_min=1e-4, bands=None):
-    """Brute-force visibility.  Returns dict(T, T_exact, hits, flags)."""
+    """Brute-force visibility.  Returns dict(T, T_exact, hits, flags, T_lo,
+    T_hi): T_lo / T_hi bound the unsnapped product over any choice of the
+    flagged (borderline) candidates; both equal T_exact when no candidate
+    set a band bit."""
     mean, scale, quat, opac = _scene(scene)
     ray_o = _c(ray_o, np.float64).reshape(-1, 3)
     ray_d = _c(ray_d, np.float64).reshape(-1, 3)
@@ -136,11 +139,12 @@ def trace(scene, ray_o, ray_d, ray_src=None, k_sigma=3.0, alpha_min=1.0 / 255.0,
     Te = np.empty(R, np.float64)
     hits = np.empty(R, np.int32)
     flags = np.empty(R, np.uint32)
+    lo, hi = np.empty(R, np.float64), np.empty(R, np.float64)
     _load().oracle_trace(mean.shape[0], _p(mean), _p(scale), _p(quat), _p(opac), R, _p(ray_o),
                          _p(ray_d), _p(src), k_sigma, alpha_min, t_min, b["band_m2"],
                          b["band_alpha"], b["band_t"], b["band_T"], _p(T), _p(Te), _p(hits),
-                         _p(flags))
-    return {"T": T, "T_exact": Te, "hits": hits, "flags": flags}
+                         _p(flags), _p(lo), _p(hi))
+    return {"T": T, "T_exact": Te, "hits": hits, "flags": flags, "T_lo": lo, "T_hi": hi}
 
 
 def trace_hits(scene, ray_o, ray_d, ray_src=None, k_sigma=3.0, alpha_min=1.0 / 255.0, cap=256):
@@ -283,7 +287,8 @@ class BvhTracer:
 
     def _out(self, m):
         return {"T": np.empty(m), "T_exact": np.empty(m), "hits": np.empty(m, np.int32),
-                "flags": np.empty(m, np.uint32), "counts": np.zeros(2, np.int64)}
+                "flags": np.empty(m, np.uint32), "counts": np.zeros(2, np.int64),
+                "T_lo": np.empty(m), "T_hi": np.empty(m)}
 
     def trace(self, ray_o, ray_d, ray_src=None, alpha_min=1.0 / 255.0, t_min=1e-4):
         ray_o = _c(ray_o, np.float64).reshape(-1, 3)
@@ -293,7 +298,8 @@ class BvhTracer:
         o, b = self._out(m), self.bands
         _load().oracle_bvh_trace(self._h, m, _p(ray_o), _p(ray_d), _p(src), alpha_min, t_min,
                                  b["band_alpha"], b["band_t"], b["band_T"], _p(o["T"]), _p(o["T_exact"]),
-                                 _p(o["hits"]), _p(o["flags"]), _p(o["counts"]))
+                                 _p(o["hits"]), _p(o["flags"]), _p(o["counts"]), _p(o["T_lo"]),
+                                 _p(o["T_hi"]))
         return o
 
     def trace_dirs(self, dirs, ids=None, eps=1e-4, alpha_min=1.0 / 255.0, t_min=1e-4):
@@ -306,7 +312,8 @@ class BvhTracer:
         o, b = self._out(m), self.bands
         _load().oracle_bvh_trace_dirs(self._h, K, _p(dirs), eps, _p(ids), m, alpha_min, t_min,
                                       b["band_alpha"], b["band_t"], b["band_T"], _p(o["T"]),
-                                      _p(o["T_exact"]), _p(o["hits"]), _p(o["flags"]), _p(o["counts"]))
+                                      _p(o["T_exact"]), _p(o["hits"]), _p(o["flags"]), _p(o["counts"]),
+                                      _p(o["T_lo"]), _p(o["T_hi"]))
         return o
 
 

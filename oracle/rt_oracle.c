@@ -150,13 +150,20 @@ static double peak_m2(const gauss64 *g, const double ro[3], const double rd[3],
  *   T[r]       = 0 if T_exact < t_min else T_exact
  *   hits[r]    = number of accepted Gaussians
  *   flags[r]   = band bits above (band widths are arguments).
+ *   T_lo[r], T_hi[r] = the products with every candidate that set a band bit
+ *                (a "borderline" candidate: one threshold test within its
+ *                band, the others passed within theirs) taken / left out,
+ *                and every other candidate as in T_exact: an exact float32
+ *                evaluation may take any subset of the borderline ones, so
+ *                its unsnapped product lies in [T_lo, T_hi] (equal to
+ *                T_exact when flags has no candidate bit).
  * Output pointers other than T may be NULL.
  */
 void oracle_trace(int64_t n, const double *mean, const double *scale, const double *quat,
                   const double *opac, int64_t n_rays, const double *ray_o, const double *ray_d,
                   const int32_t *ray_src, double k_sigma, double alpha_min, double t_min,
                   double band_m2, double band_alpha, double band_t, double band_T,
-                  double *T, double *T_exact, int32_t *hits, uint32_t *flags)
+                  double *T, double *T_exact, int32_t *hits, uint32_t *flags, double *T_lo, double *T_hi)
 {
     gauss64 *g = load_gaussians(n, mean, scale, quat, opac);
     const double K2 = k_sigma * k_sigma;
@@ -165,7 +172,7 @@ void oracle_trace(int64_t n, const double *mean, const double *scale, const doub
         double ro[3] = {ray_o[3 * r], ray_o[3 * r + 1], ray_o[3 * r + 2]};
         double rd[3] = {ray_d[3 * r], ray_d[3 * r + 1], ray_d[3 * r + 2]};
         int64_t src = ray_src ? ray_src[r] : -1;
-        double tr = 1.0;
+        double tr = 1.0, tlo = 1.0, thi = 1.0;
         int32_t nh = 0;
         uint32_t fl = 0;
         for (int64_t j = 0; j < n; ++j) {
@@ -178,15 +185,24 @@ void oracle_trace(int64_t n, const double *mean, const double *scale, const doub
             int near_t = fabs(t) <= band_t, near_m = fabs(m2 - K2) <= band_m2,
                 near_a = fabs(alpha - alpha_min) <= band_alpha;
             int lo_t = ok_t || near_t, lo_m = ok_m || near_m, lo_a = ok_a || near_a;
-            if (near_t && lo_m && lo_a) fl |= ORC_FLAG_T;
-            if (near_m && lo_t && lo_a) fl |= ORC_FLAG_M2;
-            if (near_a && lo_t && lo_m) fl |= ORC_FLAG_ALPHA;
+            int border = 0;
+            if (near_t && lo_m && lo_a) { fl |= ORC_FLAG_T; border = 1; }
+            if (near_m && lo_t && lo_a) { fl |= ORC_FLAG_M2; border = 1; }
+            if (near_a && lo_t && lo_m) { fl |= ORC_FLAG_ALPHA; border = 1; }
             if (ok_t && ok_m && ok_a) {
                 tr *= (1.0 - alpha);
                 ++nh;
             }
+            if (border) {
+                tlo *= (1.0 - alpha);
+            } else if (ok_t && ok_m && ok_a) {
+                tlo *= (1.0 - alpha);
+                thi *= (1.0 - alpha);
+            }
         }
         if (t_min > 0.0 && fabs(tr - t_min) <= band_T) fl |= ORC_FLAG_TMIN;
+        if (T_lo) T_lo[r] = tlo;
+        if (T_hi) T_hi[r] = thi;
         if (T_exact) T_exact[r] = tr;
         T[r] = (tr < t_min) ? 0.0 : tr;
         if (hits) hits[r] = nh;
@@ -675,12 +691,15 @@ void oracle_leaf_boxes(int64_t n, const double *mean, const double *scale, const
  *     of oracle_trace.
  * Every candidate that oracle_trace accepts or flags has m^2 <= K^2 + band_m2
  * and t* >= -band_t, so it is visited.  The one difference: with t_min > 0 the
- * walk stops once the product of the accepted factors is below
- * t_min - band_T.  T is then 0 whatever follows (the product only falls), and
- * a band flag that brute force would raise further along changes nothing.  So
- * T agrees with oracle_trace up to the order of the product, the flags here
- * are a subset of brute force's, and a ray flagged only by brute force has
- * T = 0.  Children are visited nearer entry first so that the stop comes early.
+ * walk stops once the product of the accepted factors other than the
+ * borderline ones (T_hi) is below t_min - band_T.  T is then 0 whatever
+ * follows and whichever borderline factors are taken (the products only
+ * fall), and a band flag that brute force would raise further along changes
+ * nothing.  So T agrees with oracle_trace up to the order of the product, the
+ * flags here are a subset of brute force's, and a ray flagged only by brute
+ * force has T = 0; T_lo and T_hi are those of oracle_trace for a ray walked
+ * to the end, and both below t_min - band_T for a stopped one.  Children are
+ * visited nearer entry first so that the stop comes early.
  */
 typedef struct {
     int64_t n;
@@ -807,17 +826,20 @@ typedef struct {
 } orc_rule;
 
 /* One ray through the tree; returns T and writes T_exact (of the accepted
- * factors met before a stop), hits, flags and the box / Gaussian test counts. */
+ * factors met before a stop), hits, flags, the bounds T_lo / T_hi of
+ * oracle_trace and the box / Gaussian test counts.  The walk stops once even
+ * T_hi (the product without the borderline candidates) is below
+ * t_min - band_T: every subset then snaps to 0. */
 static double bvh_ray(const orc_bvh *b, const orc_rule *u, const double ro[3], const double rd[3],
                       int64_t src, double *te_out, int32_t *hits_out, uint32_t *flags_out,
-                      int64_t *nbox, int64_t *ngauss)
+                      double *tlo_out, double *thi_out, int64_t *nbox, int64_t *ngauss)
 {
     const double K2 = b->k_sigma * b->k_sigma;
     const double t0 = -(2.0 * u->band_t + 1e-12);
     const double stop = u->t_min > 0.0 ? u->t_min - u->band_T : -1.0;
     double inv[3];
     for (int a = 0; a < 3; ++a) inv[a] = 1.0 / rd[a];
-    double tr = 1.0;
+    double tr = 1.0, tlo = 1.0, thi = 1.0;
     int32_t nh = 0;
     uint32_t fl = 0;
     uint32_t stk[130];
@@ -827,7 +849,7 @@ static double bvh_ray(const orc_bvh *b, const orc_rule *u, const double ro[3], c
         ++*nbox;
         if (slab64(node_box(b, root), ro, inv, t0) < INFINITY) stk[top++] = root;
     }
-    while (top > 0 && tr >= stop) {
+    while (top > 0 && thi >= stop) {
         uint32_t ref = stk[--top];
         if (ref & ORC_LEAF) {
             int64_t j = b->leaf_id[ref & ~ORC_LEAF];
@@ -840,12 +862,19 @@ static double bvh_ray(const orc_bvh *b, const orc_rule *u, const double ro[3], c
             int near_t = fabs(t) <= u->band_t, near_m = fabs(m2 - K2) <= u->band_m2,
                 near_a = fabs(alpha - u->alpha_min) <= u->band_alpha;
             int lo_t = ok_t || near_t, lo_m = ok_m || near_m, lo_a = ok_a || near_a;
-            if (near_t && lo_m && lo_a) fl |= ORC_FLAG_T;
-            if (near_m && lo_t && lo_a) fl |= ORC_FLAG_M2;
-            if (near_a && lo_t && lo_m) fl |= ORC_FLAG_ALPHA;
+            int border = 0;
+            if (near_t && lo_m && lo_a) { fl |= ORC_FLAG_T; border = 1; }
+            if (near_m && lo_t && lo_a) { fl |= ORC_FLAG_M2; border = 1; }
+            if (near_a && lo_t && lo_m) { fl |= ORC_FLAG_ALPHA; border = 1; }
             if (ok_t && ok_m && ok_a) {
                 tr *= (1.0 - alpha);
                 ++nh;
+            }
+            if (border) {
+                tlo *= (1.0 - alpha);
+            } else if (ok_t && ok_m && ok_a) {
+                tlo *= (1.0 - alpha);
+                thi *= (1.0 - alpha);
             }
             continue;
         }
@@ -862,18 +891,20 @@ static double bvh_ray(const orc_bvh *b, const orc_rule *u, const double ro[3], c
     *te_out = tr;
     *hits_out = nh;
     *flags_out = fl;
+    *tlo_out = tlo;
+    *thi_out = thi;
     return tr < u->t_min ? 0.0 : tr;
 }
 
 /*
  * Visibility of explicit rays through the tree (same arguments and outputs
- * as oracle_trace; T_exact, hits, flags, counts may be NULL).  counts[0..1]
- * receive the total box and Gaussian tests.
+ * as oracle_trace; T_exact, hits, flags, counts, T_lo, T_hi may be NULL).
+ * counts[0..1] receive the total box and Gaussian tests.
  */
 void oracle_bvh_trace(const void *h, int64_t n_rays, const double *ray_o, const double *ray_d,
                       const int32_t *ray_src, double alpha_min, double t_min, double band_alpha,
                       double band_t, double band_T, double *T, double *T_exact, int32_t *hits,
-                      uint32_t *flags, int64_t *counts)
+                      uint32_t *flags, int64_t *counts, double *T_lo, double *T_hi)
 {
     const orc_bvh *b = (const orc_bvh *)h;
     orc_rule u = {alpha_min, t_min, b->band_m2, band_alpha, band_t, band_T};
@@ -882,10 +913,12 @@ void oracle_bvh_trace(const void *h, int64_t n_rays, const double *ray_o, const 
     for (int64_t r = 0; r < n_rays; ++r) {
         double ro[3] = {ray_o[3 * r], ray_o[3 * r + 1], ray_o[3 * r + 2]};
         double rd[3] = {ray_d[3 * r], ray_d[3 * r + 1], ray_d[3 * r + 2]};
-        double te;
+        double te, tlo, thi;
         int32_t nh;
         uint32_t fl;
-        T[r] = bvh_ray(b, &u, ro, rd, ray_src ? ray_src[r] : -1, &te, &nh, &fl, &nb, &ng);
+        T[r] = bvh_ray(b, &u, ro, rd, ray_src ? ray_src[r] : -1, &te, &nh, &fl, &tlo, &thi, &nb, &ng);
+        if (T_lo) T_lo[r] = tlo;
+        if (T_hi) T_hi[r] = thi;
         if (T_exact) T_exact[r] = te;
         if (hits) hits[r] = nh;
         if (flags) flags[r] = fl;
@@ -902,7 +935,7 @@ void oracle_bvh_trace(const void *h, int64_t n_rays, const double *ray_o, const 
 void oracle_bvh_trace_dirs(const void *h, int32_t K, const float *dirs, float eps, const int64_t *ids,
                            int64_t m, double alpha_min, double t_min, double band_alpha, double band_t,
                            double band_T, double *T, double *T_exact, int32_t *hits, uint32_t *flags,
-                           int64_t *counts)
+                           int64_t *counts, double *T_lo, double *T_hi)
 {
     const orc_bvh *b = (const orc_bvh *)h;
     orc_rule u = {alpha_min, t_min, b->band_m2, band_alpha, band_t, band_T};
@@ -920,10 +953,12 @@ void oracle_bvh_trace_dirs(const void *h, int32_t K, const float *dirs, float ep
             ro[a] = o;
             rd[a] = d;
         }
-        double te;
+        double te, tlo, thi;
         int32_t nh;
         uint32_t fl;
-        T[i] = bvh_ray(b, &u, ro, rd, g, &te, &nh, &fl, &nb, &ng);
+        T[i] = bvh_ray(b, &u, ro, rd, g, &te, &nh, &fl, &tlo, &thi, &nb, &ng);
+        if (T_lo) T_lo[i] = tlo;
+        if (T_hi) T_hi[i] = thi;
         if (T_exact) T_exact[i] = te;
         if (hits) hits[i] = nh;
         if (flags) flags[i] = fl;

@@ -8,6 +8,7 @@ import pytest
 import torch
 
 import scenes
+from conftest import check_flagged_bounds
 
 pytestmark = pytest.mark.gpu
 
@@ -61,6 +62,7 @@ def test_batch_equals_single_launches(orc, autotune):
     got = jobs[8][2].cpu().numpy().astype(np.float64)[sel]
     ok = ref["flags"] == 0
     assert np.abs(got - ref["T"])[ok].max() <= 1e-5
+    check_flagged_bounds(got, ref)
     batch.destroy()
     E.destroy()
 

@@ -10,6 +10,7 @@ import pytest
 import torch
 
 import scenes
+from conftest import check_flagged_bounds
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
@@ -63,13 +64,15 @@ def test_batch_workload_sampled(orc, kind):
             err = np.abs(got - ref["T"])
             bad = np.nonzero(ok & (err > TOL))[0]
             assert bad.size == 0, (s, rays, sel[bad[:5]], got[bad[:5]], ref["T"][bad[:5]])
+            check_flagged_bounds(got, ref, TOL)
             checked += int(ok.sum())
             excluded += int((~ok).sum())
             if ok.any():
                 worst = max(worst, float(err[ok].max()))
         tracer.close()
     # flattened object-scale Gaussians put more rays within the m^2 rounding
-    # band of some candidate's 3-sigma support; they are excluded and counted
+    # band of some candidate's 3-sigma support; those are held to the
+    # oracle's bounds over that candidate, and counted
     assert excluded <= (0.02 if kind == "uniform" else 0.08) * (checked + excluded), excluded
     print(f"{kind} batch workload: {checked} sampled rays within {worst:.2e}, {excluded} in a rounding band")
     batch.destroy()

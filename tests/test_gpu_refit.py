@@ -10,6 +10,7 @@ import pytest
 import torch
 
 import scenes
+from conftest import check_flagged_bounds
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
@@ -130,6 +131,7 @@ def test_refit_trace_matches_oracle_on_moved_scene(orc, amount):
     for k, t in T.items():
         err = np.abs(t.astype(np.float64) - ref["T"])
         assert err[ok].max() <= TOL, (k, err[ok].max())
+        check_flagged_bounds(t, ref, TOL)
 
 
 def test_refit_tiny_scenes():

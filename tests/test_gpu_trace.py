@@ -1,9 +1,11 @@
 """GPU parity of the visibility trace against the FP64 brute-force oracle.
 
-Bar: |T_gpu - T_oracle| <= 1e-5 on every ray, except rays the oracle flags as
-having a candidate inside a rounding band of a threshold (m^2 = K^2,
-alpha = 1/255, t* = 0, T = T_min); those are excluded and counted, and must
-stay rare.  The per-ray and packet traversals of the binary tree visit each
+Bar: |T_gpu - T_oracle| <= 1e-5 on every ray the oracle does not flag.  A
+flagged ray has a candidate inside a rounding band of a threshold (m^2 = K^2,
+alpha = 1/255, t* = 0) or T_exact near T = T_min, where a float32 evaluation
+may decide either way: its T must lie within 1e-5 of the oracle's bounds
+[T_lo, T_hi] over taking or leaving each such candidate (or be 0 where the
+bounds reach below T_min).  Flagged rays are counted and must stay rare.  The per-ray and packet traversals of the binary tree visit each
 ray's accepted Gaussians in the same order, so they agree bit for bit; the
 4-wide traversal visits them in another order (same factors, another product
 rounding).
@@ -13,6 +15,7 @@ import pytest
 import torch
 
 import scenes
+from conftest import check_flagged_bounds
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
@@ -37,11 +40,12 @@ def trace_dirs(bvh, dirs, kernel=0, **opt):
     return T.cpu().numpy().astype(np.float64)
 
 
-def compare(T_gpu, ref, max_excluded=0.002):
+def compare(T_gpu, ref, max_excluded=0.002, t_min=1e-4):
     ok = ref["flags"] == 0
     err = np.abs(T_gpu - ref["T"])
     bad = np.nonzero(ok & (err > TOL))[0]
     assert bad.size == 0, (bad[:10], err[bad[:10]], T_gpu[bad[:10]], ref["T"][bad[:10]])
+    check_flagged_bounds(T_gpu, ref, TOL, t_min)  # flagged rays: within the oracle's bounds
     assert (~ok).mean() <= max_excluded, (~ok).sum()
     return err[ok].max(), int((~ok).sum())
 
@@ -276,10 +280,7 @@ def test_long_id_list_sorted_trace(orc, kind):
     if kind == "dirs":
         pick = rng.choice(sel.size, 256, replace=False)
         ref = orc.BvhTracer(sc).trace_dirs(dirs, ids=sel[pick])
-        ok = ref["flags"] == 0
-        assert ok.mean() > 0.95
-        err = np.abs(T_auto.cpu().numpy()[pick].astype(np.float64) - ref["T"])
-        assert err[ok].max() <= TOL
+        compare(T_auto.cpu().numpy()[pick].astype(np.float64), ref, max_excluded=0.05)
     bad = sel.copy()
     bad[123_456] = 300_000 * K
     T_bad = rt.rt_trace_visibility(bvh, rt.rayspec(rkind, ray_ids=_dev(bad), **rs_kw))
@@ -430,9 +431,10 @@ def test_bench_workload_sampled(orc):
     o, d, s = orc.dir_rays(sc["mean"], dirs, sel)
     ref = orc.trace(sc, o, d, s)
     # ~170 candidate Gaussians per ray here, so a few % of rays have one within
-    # the m^2 rounding band of the 3-sigma support; they are excluded and counted
-    maxerr, excluded = compare(T[sel], ref, max_excluded=0.06)
-    print(f"2M scene: max |dT| {maxerr:.2e} over {512 - excluded} rays, {excluded} in a rounding band")
+    # the m^2 rounding band of the 3-sigma support; those are held to the
+    # oracle's bounds over that candidate, and counted
+    maxerr, flagged = compare(T[sel], ref, max_excluded=0.06)
+    print(f"2M scene: max |dT| {maxerr:.2e} over {512 - flagged} rays, {flagged} in a rounding band (bounded)")
     assert np.all((T >= 0) & (T <= 1))
 
 

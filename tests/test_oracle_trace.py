@@ -284,6 +284,37 @@ def test_band_flags(orc):
     assert r["flags"][0] == 0
 
 
+def test_borderline_bounds(orc):
+    """T_lo / T_hi: a candidate inside a band is taken in T_lo and left out of
+    T_hi whichever way the exact test went; the other candidates count as in
+    T_exact; no band bit -> T_lo = T_hi = T_exact."""
+    sig = 0.1
+    sure = scene([0, 0, 5], sig, o=0.3)  # head on: alpha = 0.3, far from every band
+    ro, rd = ray([0, 0, 0], [0, 0, 1])
+    for b, took in ((3 * sig * (1 - 1e-7), True), (3 * sig * (1 + 1e-7), False)):
+        # a second Gaussian the ray passes at m = 3 (1 -/+ 1e-7): in the m^2 band
+        sc = {k: np.concatenate([sure[k], scene([-b, 0, 2], sig, o=0.99)[k]]) for k in sure}
+        r = orc.trace(sc, ro, rd)
+        a = 0.99 * math.exp(-((b / sig) ** 2) / 2)
+        assert r["flags"][0] & orc.FLAG_M2
+        assert r["T_hi"][0] == pytest.approx(0.7, rel=1e-14)
+        assert r["T_lo"][0] == pytest.approx(0.7 * (1 - a), rel=1e-14)
+        assert r["T_exact"][0] == pytest.approx(0.7 * (1 - a) if took else 0.7, rel=1e-14)
+    r = orc.trace(sure, ro, rd)
+    assert r["flags"][0] == 0 and r["T_lo"][0] == r["T_hi"][0] == r["T_exact"][0]
+    # a scene of many rays: the bounds bracket T_exact, equal it without a
+    # candidate bit, and the tree walk gives the brute force's bounds
+    sc, ro2, rd2, src = _dir_scene(orc, 300, 12)
+    res = orc.trace(sc, ro2, rd2, src, t_min=0.0)
+    cand = (res["flags"] & (orc.FLAG_M2 | orc.FLAG_ALPHA | orc.FLAG_T)) != 0
+    assert np.all(res["T_lo"] <= res["T_exact"] * (1 + 1e-12)) and np.all(res["T_exact"] <= res["T_hi"] * (1 + 1e-12))
+    assert np.array_equal(res["T_lo"][~cand], res["T_exact"][~cand]) and np.array_equal(res["T_hi"][~cand],
+                                                                                          res["T_exact"][~cand])
+    tb = orc.BvhTracer(sc).trace(ro2, rd2, src, t_min=0.0)
+    np.testing.assert_allclose(tb["T_lo"], res["T_lo"], rtol=1e-12, atol=0)
+    np.testing.assert_allclose(tb["T_hi"], res["T_hi"], rtol=1e-12, atol=0)
+
+
 def test_hit_lists_agree_with_trace(orc):
     sc, ro, rd, src = _dir_scene(orc, 300, 12)
     res = orc.trace(sc, ro, rd, src, t_min=0.0)
