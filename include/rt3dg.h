@@ -513,7 +513,12 @@ rt_status rt_surrogate_loss_grad(const rt_surrogate *s, const float *pos, const 
  * word x and R rays in the set), builds the ray as the tracer does and uses
  * T_target[r] (the traced visibility of the whole set) as the target.  Sets
  * the scene bounds from `bvh`.  loss_curve (device float32[steps], may be
- * NULL) receives each step's mean loss. */
+ * NULL) receives each step's mean loss.  Every sum of a step runs in a fixed
+ * order, so training is bit-reproducible, and n steps in one call give the
+ * same parameters as n one-step calls with the same seed.  Within a call the
+ * steps' kernels are launched with programmatic stream serialisation (each
+ * orders itself against the previous one); work the caller enqueues after
+ * the call follows the last of them in plain stream order. */
 rt_status rt_surrogate_train(rt_surrogate *s, const rt_bvh *bvh, const rt_rayspec *samples,
                              const float *T_target, int32_t steps, uint64_t seed,
                              float *loss_curve, rt_stream_t stream);
