@@ -42,12 +42,17 @@ std::map<TuneKey, std::pair<int, int>> g_tune_cache;
 constexpr int kTuneBlocks = 4;
 constexpr float kTuneMargin = 0.97f;
 
-// The strategy used without tuning: 4-wide packets sharing a direction for a
-// direction set, one thread per ray on the 4-wide tree with lane refill for
-// env-map and hemisphere rays (their directions differ within a tile), binary
-// variants when there is no 4-wide tree.
+// The strategy used without tuning, as the single-scene AUTO: for a
+// direction set 4-wide packets sharing the direction, or one thread per ray
+// on the 4-wide tree (near-first) for scenes of at most 2^19 Gaussians; one
+// thread per ray on the 4-wide tree with lane refill for env-map and
+// hemisphere rays (their directions differ within a tile); binary variants
+// when there is no 4-wide tree.
 int default_kernel(const rt_bvh *bvh, int32_t kind) {
-    if (kind == RT_RAYS_DIRS) return bvh->n_wide > 0 ? RT_KERNEL_WIDE : RT_KERNEL_PACKET;
+    if (kind == RT_RAYS_DIRS) {
+        if (bvh->n_wide == 0) return RT_KERNEL_PACKET;
+        return bvh->n <= (int64_t(1) << 19) ? RT_KERNEL_RAY_WIDE : RT_KERNEL_WIDE;
+    }
     return bvh->n_wide > 0 ? RT_KERNEL_RAY_REFILL : RT_KERNEL_RAY;
 }
 

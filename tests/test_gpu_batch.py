@@ -20,7 +20,8 @@ def _dev(a):
 @pytest.mark.parametrize("autotune", [True, False])
 def test_batch_equals_single_launches(orc, autotune):
     """Without tuning the env-map jobs run with lane refill (the batch's
-    per-ray slot queue), the direction sets as warp packets."""
+    per-ray slot queue) and the direction sets, all over fewer than 2^19
+    Gaussians here, with the per-ray 4-wide walk, as the single-scene AUTO."""
     from paper_2311_16043_gb300 import rt
     sizes = [700, 9000, 31, 2500, 20000]
     env = scenes.envmap(399)
@@ -40,7 +41,7 @@ def test_batch_equals_single_launches(orc, autotune):
     batch = rt.rt_batch_create(jobs, autotune=autotune)
     info = batch.info()
     if not autotune:
-        assert info["kernel"] == [3, 5] * len(sizes)
+        assert info["kernel"] == [rt.RT_KERNEL_RAY_WIDE, rt.RT_KERNEL_RAY_REFILL] * len(sizes)
     # single launches with each job's chosen strategy give the same T bit for bit
     for (bvh, rs, T), kernel in zip(jobs, info["kernel"]):
         refs.append(rt.rt_trace_visibility(bvh, rs, opts=rt.trace_opts(kernel=kernel)))
