@@ -444,7 +444,10 @@ def trace_instances(objects, xforms, ray_o, ray_d, src_inst, src_local, alpha_mi
     object i's Gaussians under Eq. 13-15 (CPU BVH tracer, no early stop),
     skipping the ray's own Gaussian; T_exact is the product over all
     instances, band flags are or-ed, and T is snapped to 0 below t_min.
-    Returns dict(T, T_exact, flags)."""
+    T_lo / T_hi are the products of the instances' bounds (every borderline
+    candidate taken / left out; each factor lies in (0, 1], so the product
+    is monotone in each and the bounds multiply).
+    Returns dict(T, T_exact, flags, T_lo, T_hi)."""
     b = dict(DEFAULT_BANDS)
     if bands:
         b.update(bands)
@@ -452,6 +455,8 @@ def trace_instances(objects, xforms, ray_o, ray_d, src_inst, src_local, alpha_mi
     ray_d = _c(ray_d, np.float32)
     R_ = ray_o.shape[0]
     te = np.ones(R_)
+    lo = np.ones(R_)
+    hi = np.ones(R_)
     fl = np.zeros(R_, np.uint32)
     tracers = {}
     for i, (sc, xf) in enumerate(zip(objects, xforms)):
@@ -465,11 +470,13 @@ def trace_instances(objects, xforms, ray_o, ray_d, src_inst, src_local, alpha_mi
         src = np.where(src_inst == i, src_local, -1).astype(np.int32)
         r = tracers[id(sc)].trace(ol, dl, src, alpha_min=alpha_min, t_min=0.0)
         te *= r["T_exact"]
+        lo *= r["T_lo"]
+        hi *= r["T_hi"]
         fl |= r["flags"]
     if t_min > 0.0:
         fl[np.abs(te - t_min) <= b["band_T"]] |= FLAG_TMIN
     T = np.where(te < t_min, 0.0, te)
-    return {"T": T, "T_exact": te, "flags": fl}
+    return {"T": T, "T_exact": te, "flags": fl, "T_lo": lo, "T_hi": hi}
 
 
 def bf16_round(x) -> np.ndarray:

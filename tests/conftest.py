@@ -34,3 +34,14 @@ def check_flagged_bounds(T_gpu, ref, tol=1e-5, t_min=1e-4):
     bad = np.nonzero(fl & ~inside & ~snapped)[0]
     assert bad.size == 0, (bad[:10], T_gpu[bad[:10]], lo[bad[:10]], hi[bad[:10]])
     return int(fl.sum())
+
+
+def visibility_range(ref, tol=1e-5, t_min=1e-4):
+    """Per ray, the interval [lo, hi] that a correct float32 trace may
+    return: the oracle's bounds widened by tol, reaching down to 0 where
+    the lower bound lies below T_min (the trace may snap there).  For the
+    consumers that are monotone in each ray's T (an average, Eq. 10's
+    colour)."""
+    import numpy as np
+    lo = np.where(ref["T_lo"] < t_min + tol, 0.0, ref["T_lo"] - tol)
+    return np.maximum(lo, 0.0), ref["T_hi"] + tol

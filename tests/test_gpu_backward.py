@@ -10,6 +10,7 @@ import pytest
 import torch
 
 import scenes
+from conftest import check_flagged_bounds
 
 pytestmark = pytest.mark.gpu
 
@@ -69,6 +70,7 @@ def test_backward_matches_oracle(case, use_log):
     torch.cuda.synchronize()
     assert rt.rt_status_last() == 0
     assert np.abs(T.cpu().numpy() - ref["T"])[ref["flags"] == 0].max() < 1e-5
+    check_flagged_bounds(T.cpu().numpy(), ref, 1e-5, t_min=0.0)
     for k in ("opacity", "mean", "scale", "quat"):
         _check(g[k].cpu().numpy(), want[k], k)
 

@@ -12,6 +12,7 @@ import pytest
 import torch
 
 import scenes
+from conftest import check_flagged_bounds
 
 pytestmark = pytest.mark.gpu
 
@@ -166,6 +167,7 @@ def test_infer_matches_oracle(orc, kind, ids_mode, w):
     ok = ref["flags"] == 0
     assert ok.mean() > 0.95
     assert np.abs(q[fb][ok] - ref["T"][ok]).max() <= 1e-5
+    check_flagged_bounds(q[fb], ref, 1e-5)
     if E is not None:
         E.destroy()
     s.destroy()

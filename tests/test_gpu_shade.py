@@ -2,17 +2,17 @@
 per-Gaussian PBR colour of Eq. 10 (from a visibility table and fused with the
 trace) and ambient occlusion, against the oracle.
 
-Tolerances: rays |dT| <= 1e-5 (the trace bar; rays in a rounding band are
-excluded and counted).  PBR colour: the GPU evaluates Eq. 9-10 in float32
+Tolerances: rays |dT| <= 1e-5 (the trace bar; rays in a rounding band lie
+within the oracle's bounds, and are counted).  PBR colour: the GPU evaluates Eq. 9-10 in float32
 (acosf/atan2f for the map lookup, rsqrtf for the half vector) against the
 oracle's float64.  Most terms agree to ~1e-6 relative, but the GGX lobe is
 steep: |d ln D / d theta_h| reaches ~2/alpha = 1250 per radian at the
 smallest roughness (alpha = 0.04^2), and the float32 directions (normal,
 hemisphere rotation, view, half vector) carry ~1.2e-7 rad of rounding, so a
 near-mirror term can be off by ~3e-4 relative.  Bar: rtol 1e-3 with an
-absolute floor of 1e-6, and a median relative error below 1e-5.  Gaussians
-with a band-flagged ray are excluded when the oracle's V comes from its own
-trace.  Fused and table forms run the same source for the traversal and the
+absolute floor of 1e-6, and a median relative error below 1e-5.  Where the
+oracle's V comes from its own trace, a Gaussian with a band-flagged ray is
+held between the colours (or AO) of its rays' bounds instead.  Fused and table forms run the same source for the traversal and the
 shading, but in separately compiled kernels whose multiply-adds the compiler
 may contract differently: they agree to a few float32 roundings (1e-5)."""
 import numpy as np
@@ -20,6 +20,7 @@ import pytest
 import torch
 
 import scenes
+from conftest import check_flagged_bounds, visibility_range
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
@@ -52,6 +53,7 @@ def _compare_T(T, ref, max_excluded=0.01):
     err = np.abs(T - ref["T"])
     bad = np.nonzero(ok & (err > TOL))[0]
     assert bad.size == 0, (bad[:10], err[bad[:10]])
+    check_flagged_bounds(T, ref, TOL)
     assert (~ok).mean() <= max_excluded, (~ok).sum()
     return int((~ok).sum())
 
@@ -103,7 +105,7 @@ def test_hemi_trace_object_scene_every_ray(orc):
     for c in range(0, ids.size, 1 << 22):
         o, d, s = orc.hemi_rays(sc["mean"], nrm, hemi, ids[c:c + (1 << 22)])
         out.append(B.trace(o, d, s))
-    ref = {k: np.concatenate([r[k] for r in out]) for k in ("T", "flags")}
+    ref = {k: np.concatenate([r[k] for r in out]) for k in ("T", "flags", "T_lo", "T_hi")}
     excluded = _compare_T(T, ref)
     print(f"hemisphere 300k x 64: {T.size - excluded} rays compared, {excluded} in a rounding band, "
           f"mean T {T.mean():.3f}")
@@ -191,6 +193,14 @@ def test_pbr_fused_matches_oracle(orc):
     assert ok.mean() > 0.98
     got = rgb.cpu().numpy().astype(np.float64)
     _compare_rgb(got[ok], want[ok], atol=1e-5)
+    # the colour is non-decreasing in each V (Eq. 10: non-negative BRDF,
+    # direct light and cosine), so a Gaussian with a flagged ray lies
+    # between the colours of its bounds
+    v_lo, v_hi = visibility_range(ref, TOL)
+    lo = orc.pbr(sc, nrm, m, hemi, v_lo, env, np.array(cam))
+    hi = orc.pbr(sc, nrm, m, hemi, v_hi, env, np.array(cam))
+    slack = 1e-3 * np.abs(hi) + 1e-5
+    assert np.all(got[~ok] >= lo[~ok] - slack[~ok]) and np.all(got[~ok] <= hi[~ok] + slack[~ok])
     assert (ref["T"] < 1).mean() > 0.05  # shadows matter in this scene
 
 
@@ -221,6 +231,10 @@ def test_ao_matches_oracle(orc, kind):
         assert rt.rt_status_last() == 0
         got = ao.cpu().numpy().astype(np.float64)
         assert np.abs(got - want)[ok].max() <= TOL
+        # a Gaussian with a flagged ray: between the means of its bounds
+        v_lo, v_hi = visibility_range(ref, TOL)
+        assert np.all(got >= v_lo.reshape(n, K).mean(1) - 1e-6)
+        assert np.all(got <= v_hi.reshape(n, K).mean(1) + 1e-6)
         if kernel:
             # the table of the same traversal: only the float32 sum differs
             T = rt.rt_trace_visibility(bvh, rs, opts=rt.trace_opts(kernel=kernel))

@@ -1,7 +1,8 @@
 """Pins of the oracle's composed-scene tracer (CPU only): one instance under
 the identity map is the plain object; a composition equals the union scene
-(every Gaussian moved to the world in FP64, brute force); and a rigid motion
-of the whole composition (instances and directions) leaves T unchanged."""
+(every Gaussian moved to the world in FP64, brute force), bounds included;
+and a rigid motion of the whole composition (instances and directions)
+leaves T unchanged."""
 import numpy as np
 from scipy.spatial.transform import Rotation
 
@@ -55,6 +56,9 @@ def test_identity_instance_is_the_object(orc):
     full = ref["T"] > 0
     np.testing.assert_allclose(got["T"], ref["T"], atol=1e-14)
     np.testing.assert_array_equal(got["flags"][full], ref["flags"][full])
+    # a walk that ran to the end (T > 0) gives the plain tracer's bounds
+    np.testing.assert_allclose(got["T_lo"][full], ref["T_lo"][full], rtol=1e-12, atol=0)
+    np.testing.assert_allclose(got["T_hi"][full], ref["T_hi"][full], rtol=1e-12, atol=0)
 
 
 def test_composition_is_the_union_scene(orc):
@@ -70,6 +74,20 @@ def test_composition_is_the_union_scene(orc):
     assert ok.mean() > 0.99
     assert np.abs(got["T"] - ref["T"])[ok].max() <= TOL
     assert (got["T"] < 0.5).mean() > 0.2  # the instances do shadow each other
+    # the bounds: they bracket T_exact, close on it without a borderline
+    # candidate, and equal the union scene's where both flag the same tests
+    cand = orc.FLAG_M2 | orc.FLAG_ALPHA | orc.FLAG_T
+    assert np.all(got["T_lo"] <= got["T_exact"] * (1 + 1e-12))
+    assert np.all(got["T_exact"] <= got["T_hi"] * (1 + 1e-12))
+    plain = (got["flags"] & cand) == 0
+    assert np.array_equal(got["T_lo"][plain], got["T_exact"][plain])
+    assert np.array_equal(got["T_hi"][plain], got["T_exact"][plain])
+    same = got["flags"] == ref["flags"]
+    assert same.mean() > 0.99 and (same & ~plain).sum() >= 5
+    assert np.abs(got["T_lo"] - ref["T_lo"])[same].max() <= TOL
+    assert np.abs(got["T_hi"] - ref["T_hi"])[same].max() <= TOL
+    wide = ~plain & (got["T_hi"] > 1e-3)
+    assert np.all(got["T_lo"][wide] < got["T_hi"][wide])
 
 
 def test_rigid_motion_of_the_composition(orc):
