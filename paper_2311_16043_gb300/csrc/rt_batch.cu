@@ -44,7 +44,7 @@ constexpr float kTuneMargin = 0.97f;
 
 // The strategy used without tuning, as the single-scene AUTO: for a
 // direction set 4-wide packets sharing the direction, or one thread per ray
-// on the 4-wide tree (near-first) for scenes of at most 2^19 Gaussians; one
+// on the 4-wide tree (far-first) for scenes of at most 2^19 Gaussians; one
 // thread per ray on the 4-wide tree with lane refill for env-map and
 // hemisphere rays (their directions differ within a tile); binary variants
 // when there is no 4-wide tree.
@@ -145,6 +145,7 @@ __device__ __forceinline__ void batch_refill(const BatchJobDev *__restrict__ job
         }
         if (!has) continue;
         const BvhDev &b = jobs[jl].b;
+        const bool far = far_first(jobs[jl].rs);
         const float4 *w = b.wide + 8 * (int64_t)node;
         const float4 lx = __ldg(w), hx = __ldg(w + 1), ly = __ldg(w + 2), hy = __ldg(w + 3), lz = __ldg(w + 4),
                      hz = __ldg(w + 5), rf = __ldg(w + 6);
@@ -166,7 +167,7 @@ __device__ __forceinline__ void batch_refill(const BatchJobDev *__restrict__ job
             }
         }
         int next = -1;
-        const bool overflow = !near_first(ti[0], ti[1], ti[2], ti[3], r[0], r[1], r[2], r[3], stack, sp, next);
+        const bool overflow = !visit_order(ti[0], ti[1], ti[2], ti[3], r[0], r[1], r[2], r[3], far, stack, sp, next);
         if (overflow) rt_set_error(status, RT_ERR_STACK_OVERFLOW);
         bool done = overflow || T < b.t_min;
         if (!done) {

@@ -114,7 +114,8 @@ __global__ void __launch_bounds__(128, RT_SCENE_MIN_BLOCKS) k_scene_trace(const 
                 const InstDev &I = inst[i];
                 const float3 x = make_float3(__fsub_rn(o.x, I.t[0]), __fsub_rn(o.y, I.t[1]), __fsub_rn(o.z, I.t[2]));
                 const float3 ol = rot_t(I.R, x), dl = rot_t(I.R, d);
-                trace_ray_wide_run<false>(I.b, ol, dl, i == lo ? (int32_t)p : -1, T, lg, wc, status);
+                trace_ray_wide_run<false>(I.b, ol, dl, i == lo ? (int32_t)p : -1, T, lg, wc, status,
+                                          far_first(rs));
                 continue;
             }
             const TopNode nd = top[ref];

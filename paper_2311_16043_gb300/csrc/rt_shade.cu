@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(128, 8) k_trace_reduce(BvhDev b, RaySetDev rs,
             if (valid) implicit_ray(rs, g * rs.K + k, k, g, mu, o, d);
             const int32_t src = valid ? (int32_t)p : -1;
             float T;
-            if (STRAT == 4) T = valid ? trace_ray_wide<false>(b, o, d, src, lg, wc, status) : 1.0f;
+            if (STRAT == 4) T = valid ? trace_ray_wide<false>(b, o, d, src, lg, wc, status, far_first(rs)) : 1.0f;
             else T = trace_wide<false, STRAT == 3>(b, o, d, src, valid, lg, wc, status, stk);
             if (!valid) continue;
             if (MODE == 0) {

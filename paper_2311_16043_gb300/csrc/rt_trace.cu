@@ -201,9 +201,9 @@ rt_status rt_trace_launch(const rt_bvh *bvh, const rt_rayspec *rays, float *T_ou
     if (strat == 6 && (bvh->n_wide == 0 || o.hit_ids)) strat = bvh->n_wide ? 4 : 0;
     // AUTO:
     // - a direction set: warp packets sharing the direction, except over at
-    //   most 2^19 Gaussians, where the per-ray walk with its near-first order
-    //   is faster (object scenes: 100k 18 %, 300k 5 %, 500k 2.7 %; from 1M
-    //   on the packets win);
+    //   most 2^19 Gaussians, where the per-ray walk (farthest child first)
+    //   is faster (object scenes: 100k 18 %, 300k 5 %, 500k 2.7 % with the
+    //   nearest child first; from 1M on the packets win);
     // - env-map and hemisphere sets (directions differ across a tile): the
     //   per-ray walk with lane refill;
     // - explicit rays and id lists (scattered rays): one warp per ray up to

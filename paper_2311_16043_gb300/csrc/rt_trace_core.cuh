@@ -134,14 +134,21 @@ __device__ __forceinline__ void cswap_near(float &ta, uint32_t &qa, float &tb, u
 }
 
 // The per-ray walk's next node among a visited node's internal children hit
-// (entry distances t, +inf for the others): the nearest becomes `next` (-1:
-// none) and the rest are pushed far-first, so the stack pops them
-// near-first; the hits close to the origin, where a ray's transmittance
-// falls first, come early and the walk stops sooner once T < T_min.
+// (entry distances t, +inf for the others): the nearest (far: the farthest)
+// becomes `next` (-1: none) and the rest are pushed so that the stack pops
+// them in the same order.  The order decides only how soon the walk stops
+// once T < T_min: the accepted set and the factors are the same.
 // Returns false (nothing pushed) if the stack would overflow.
-__device__ __forceinline__ bool near_first(float t0, float t1, float t2, float t3, uint32_t r0, uint32_t r1,
-                                           uint32_t r2, uint32_t r3, uint32_t *stack, int &sp, int &next) {
+__device__ __forceinline__ bool visit_order(float t0, float t1, float t2, float t3, uint32_t r0, uint32_t r1,
+                                            uint32_t r2, uint32_t r3, bool far, uint32_t *stack, int &sp,
+                                            int &next) {
     const float inf = __int_as_float(0x7f800000);
+    if (far) {
+        t0 = t0 < inf ? -t0 : inf;
+        t1 = t1 < inf ? -t1 : inf;
+        t2 = t2 < inf ? -t2 : inf;
+        t3 = t3 < inf ? -t3 : inf;
+    }
     cswap_near(t0, r0, t1, r1);
     cswap_near(t2, r2, t3, r3);
     cswap_near(t0, r0, t2, r2);
@@ -155,6 +162,16 @@ __device__ __forceinline__ bool near_first(float t0, float t1, float t2, float t
     if (t1 < inf) stack[sp++] = r1;
     return true;
 }
+
+// The per-ray walks' order for a ray set.  A direction set covers the whole
+// sphere about each Gaussian: about half its rays go into the body the
+// Gaussian lies on, and their occluders are that body's far side, while the
+// near boxes hold the Gaussian's own neighbours, which such a ray enters and
+// leaves mostly without a hit; so direction rays visit the farthest child
+// first.  Hemisphere and env-map rays leave the surface: the occluders that
+// put them in shadow come first along the ray, so they visit the nearest
+// child first.
+__device__ __forceinline__ bool far_first(const RaySetDev &rs) { return rs.kind == RT_RAYS_DIRS; }
 
 // The slab test of two children at once with the planes already ordered
 // along the ray (near plane first on every axis: slab() without the per-axis
@@ -547,9 +564,10 @@ __device__ __forceinline__ float trace_wide(const BvhDev &b, float3 o, float3 d,
 // for rays without a shared direction (env-map samples, explicit rays).
 // Multiplies the running transmittance T by this tree's accepted factors and
 // stops once T < t_min (no snap: a ray may go on through other trees).
+// Children in visit_order (far: farthest first).
 template <bool COUNT>
 __device__ __forceinline__ void trace_ray_wide_run(const BvhDev &b, float3 o, float3 d, int32_t src, float &T,
-                                                   LaneLog &lg, WorkCounts &wc, int *status) {
+                                                   LaneLog &lg, WorkCounts &wc, int *status, bool far) {
     if (b.n <= 0) return;
     if (b.n == 1) {
         if (COUNT) wc.gauss++;
@@ -593,7 +611,7 @@ __device__ __forceinline__ void trace_ray_wide_run(const BvhDev &b, float3 o, fl
             }
         }
         int next = -1;
-        const bool overflow = !near_first(ti[0], ti[1], ti[2], ti[3], r[0], r[1], r[2], r[3], stack, sp, next);
+        const bool overflow = !visit_order(ti[0], ti[1], ti[2], ti[3], r[0], r[1], r[2], r[3], far, stack, sp, next);
         if (overflow) {
             rt_set_error(status, RT_ERR_STACK_OVERFLOW);
             break;
@@ -610,9 +628,9 @@ __device__ __forceinline__ void trace_ray_wide_run(const BvhDev &b, float3 o, fl
 
 template <bool COUNT>
 __device__ __forceinline__ float trace_ray_wide(const BvhDev &b, float3 o, float3 d, int32_t src, LaneLog &lg,
-                                                WorkCounts &wc, int *status) {
+                                                WorkCounts &wc, int *status, bool far) {
     float T = 1.0f;
-    trace_ray_wide_run<COUNT>(b, o, d, src, T, lg, wc, status);
+    trace_ray_wide_run<COUNT>(b, o, d, src, T, lg, wc, status, far);
     return T < b.t_min ? 0.0f : T;
 }
 
@@ -753,7 +771,7 @@ __device__ __forceinline__ void trace_item(const BvhDev &b, const RaySetDev &rs,
     lg.count = 0;
     float T;
     if (STRAT == 4) {
-        T = valid ? trace_ray_wide<COUNT>(b, o, d, src, lg, wc, aux.status) : 1.0f;
+        T = valid ? trace_ray_wide<COUNT>(b, o, d, src, lg, wc, aux.status, far_first(rs)) : 1.0f;
     } else if (STRAT == 3) {
         T = trace_wide<COUNT, true>(b, o, d, src, valid, lg, wc, aux.status, stk);
     } else if (STRAT == 2) {
@@ -815,6 +833,7 @@ __device__ __forceinline__ void trace_refill(const BvhDev &b, const RaySetDev &r
     uint32_t node = 0;
     int sp = 0;
     uint32_t stack[RT_WIDE_STACK];
+    const bool far = far_first(rs);
     for (;;) {
         const unsigned idle = __ballot_sync(FULL, !has);
         const int n_idle = __popc(idle);
@@ -877,7 +896,7 @@ __device__ __forceinline__ void trace_refill(const BvhDev &b, const RaySetDev &r
             }
         }
         int next = -1;
-        const bool overflow = !near_first(ti[0], ti[1], ti[2], ti[3], r[0], r[1], r[2], r[3], stack, sp, next);
+        const bool overflow = !visit_order(ti[0], ti[1], ti[2], ti[3], r[0], r[1], r[2], r[3], far, stack, sp, next);
         if (overflow) rt_set_error(aux.status, RT_ERR_STACK_OVERFLOW);
         bool done = overflow || T < b.t_min;
         if (!done) {
