@@ -63,7 +63,7 @@ def _load():
         sig = {
             "oracle_rotation": (None, [P, P]),
             "oracle_trace": (None, [i64, P, P, P, P, i64, P, P, P, f64, f64, f64,
-                                    f64, f64, f64, f64, P, P, P, P, P, P]),
+                                    f64, f64, f64, f64, P, P, P, P, P, P, P]),
             "oracle_trace_hits": (None, [i64, P, P, P, P, i64, P, P, P, f64, f64, i32, P, P]),
             "oracle_trace_grad": (None, [i64, P, P, P, P, i64, P, P, P, f64, f64, f64,
                                          P, P, P, P, P, P]),
@@ -124,9 +124,9 @@ def rotation(q) -> np.ndarray:
 def trace(scene, ray_o, ray_d, ray_src=None, k_sigma=3.0, alpha_min=1.0 / 255.0,
           t_min=1e-4, bands=None):
     """Brute-force visibility.  Returns dict(T, T_exact, hits, flags, T_lo,
-    T_hi): T_lo / T_hi bound the unsnapped product over any choice of the
-    flagged (borderline) candidates; both equal T_exact when no candidate
-    set a band bit."""
+    T_hi, n_border): T_lo / T_hi bound the unsnapped product over any choice
+    of the flagged (borderline) candidates; both equal T_exact when no
+    candidate set a band bit; n_border counts those candidates."""
     mean, scale, quat, opac = _scene(scene)
     ray_o = _c(ray_o, np.float64).reshape(-1, 3)
     ray_d = _c(ray_d, np.float64).reshape(-1, 3)
@@ -140,11 +140,12 @@ def trace(scene, ray_o, ray_d, ray_src=None, k_sigma=3.0, alpha_min=1.0 / 255.0,
     hits = np.empty(R, np.int32)
     flags = np.empty(R, np.uint32)
     lo, hi = np.empty(R, np.float64), np.empty(R, np.float64)
+    nb = np.empty(R, np.int32)
     _load().oracle_trace(mean.shape[0], _p(mean), _p(scale), _p(quat), _p(opac), R, _p(ray_o),
                          _p(ray_d), _p(src), k_sigma, alpha_min, t_min, b["band_m2"],
                          b["band_alpha"], b["band_t"], b["band_T"], _p(T), _p(Te), _p(hits),
-                         _p(flags), _p(lo), _p(hi))
-    return {"T": T, "T_exact": Te, "hits": hits, "flags": flags, "T_lo": lo, "T_hi": hi}
+                         _p(flags), _p(lo), _p(hi), _p(nb))
+    return {"T": T, "T_exact": Te, "hits": hits, "flags": flags, "T_lo": lo, "T_hi": hi, "n_border": nb}
 
 
 def trace_hits(scene, ray_o, ray_d, ray_src=None, k_sigma=3.0, alpha_min=1.0 / 255.0, cap=256):

@@ -157,13 +157,16 @@ static double peak_m2(const gauss64 *g, const double ro[3], const double rd[3],
  *                evaluation may take any subset of the borderline ones, so
  *                its unsnapped product lies in [T_lo, T_hi] (equal to
  *                T_exact when flags has no candidate bit).
+ *   n_border[r] = the number of those borderline candidates: such an
+ *                evaluation accepts hits[r] of them give or take n_border[r].
  * Output pointers other than T may be NULL.
  */
 void oracle_trace(int64_t n, const double *mean, const double *scale, const double *quat,
                   const double *opac, int64_t n_rays, const double *ray_o, const double *ray_d,
                   const int32_t *ray_src, double k_sigma, double alpha_min, double t_min,
                   double band_m2, double band_alpha, double band_t, double band_T,
-                  double *T, double *T_exact, int32_t *hits, uint32_t *flags, double *T_lo, double *T_hi)
+                  double *T, double *T_exact, int32_t *hits, uint32_t *flags, double *T_lo, double *T_hi,
+                  int32_t *n_border)
 {
     gauss64 *g = load_gaussians(n, mean, scale, quat, opac);
     const double K2 = k_sigma * k_sigma;
@@ -173,7 +176,7 @@ void oracle_trace(int64_t n, const double *mean, const double *scale, const doub
         double rd[3] = {ray_d[3 * r], ray_d[3 * r + 1], ray_d[3 * r + 2]};
         int64_t src = ray_src ? ray_src[r] : -1;
         double tr = 1.0, tlo = 1.0, thi = 1.0;
-        int32_t nh = 0;
+        int32_t nh = 0, nb = 0;
         uint32_t fl = 0;
         for (int64_t j = 0; j < n; ++j) {
             if (j == src) continue;
@@ -195,6 +198,7 @@ void oracle_trace(int64_t n, const double *mean, const double *scale, const doub
             }
             if (border) {
                 tlo *= (1.0 - alpha);
+                ++nb;
             } else if (ok_t && ok_m && ok_a) {
                 tlo *= (1.0 - alpha);
                 thi *= (1.0 - alpha);
@@ -207,6 +211,7 @@ void oracle_trace(int64_t n, const double *mean, const double *scale, const doub
         T[r] = (tr < t_min) ? 0.0 : tr;
         if (hits) hits[r] = nh;
         if (flags) flags[r] = fl;
+        if (n_border) n_border[r] = nb;
     }
     free(g);
 }

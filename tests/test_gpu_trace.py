@@ -213,6 +213,13 @@ def test_hit_log_matches_oracle(orc, small):
     for j in np.nonzero(ok & (rcnt <= cap))[0][:2000]:
         r = sel[j]
         assert set(ids[r, :cnt[r]]) == set(rid[j, :rcnt[j]])
+    # a flagged ray: each borderline candidate may go either way, so the
+    # count and the listed set differ from the exact ones by at most that many
+    nb = ref["n_border"]
+    assert np.all(np.abs(cnt[sel] - rcnt) <= nb)
+    for j in np.nonzero(~ok & (rcnt <= cap) & (cnt[sel] <= cap))[0][:2000]:
+        r = sel[j]
+        assert len(set(ids[r, :cnt[r]]) ^ set(rid[j, :rcnt[j]])) <= nb[j]
 
 
 def test_id_subset_matches_full_trace(small):

@@ -300,8 +300,18 @@ def test_borderline_bounds(orc):
         assert r["T_hi"][0] == pytest.approx(0.7, rel=1e-14)
         assert r["T_lo"][0] == pytest.approx(0.7 * (1 - a), rel=1e-14)
         assert r["T_exact"][0] == pytest.approx(0.7 * (1 - a) if took else 0.7, rel=1e-14)
+        assert r["n_border"][0] == 1 and r["hits"][0] == (2 if took else 1)
+    # two borderline candidates, one either side of 3 sigma
+    b1, b2 = 3 * sig * (1 - 1e-7), 3 * sig * (1 + 1e-7)
+    sc = {k: np.concatenate([sure[k], scene([-b1, 0, 2], sig, o=0.99)[k], scene([0, b2, 3], sig, o=0.99)[k]])
+          for k in sure}
+    r = orc.trace(sc, ro, rd)
+    a1, a2 = (0.99 * math.exp(-((b / sig) ** 2) / 2) for b in (b1, b2))
+    assert r["n_border"][0] == 2 and r["hits"][0] == 2
+    assert r["T_lo"][0] == pytest.approx(0.7 * (1 - a1) * (1 - a2), rel=1e-14)
+    assert r["T_hi"][0] == pytest.approx(0.7, rel=1e-14)
     r = orc.trace(sure, ro, rd)
-    assert r["flags"][0] == 0 and r["T_lo"][0] == r["T_hi"][0] == r["T_exact"][0]
+    assert r["flags"][0] == 0 and r["T_lo"][0] == r["T_hi"][0] == r["T_exact"][0] and r["n_border"][0] == 0
     # a scene of many rays: the bounds bracket T_exact, equal it without a
     # candidate bit, and the tree walk gives the brute force's bounds
     sc, ro2, rd2, src = _dir_scene(orc, 300, 12)
@@ -310,6 +320,7 @@ def test_borderline_bounds(orc):
     assert np.all(res["T_lo"] <= res["T_exact"] * (1 + 1e-12)) and np.all(res["T_exact"] <= res["T_hi"] * (1 + 1e-12))
     assert np.array_equal(res["T_lo"][~cand], res["T_exact"][~cand]) and np.array_equal(res["T_hi"][~cand],
                                                                                           res["T_exact"][~cand])
+    assert np.array_equal(res["n_border"] > 0, cand) and cand.any()
     tb = orc.BvhTracer(sc).trace(ro2, rd2, src, t_min=0.0)
     np.testing.assert_allclose(tb["T_lo"], res["T_lo"], rtol=1e-12, atol=0)
     np.testing.assert_allclose(tb["T_hi"], res["T_hi"], rtol=1e-12, atol=0)
