@@ -10,7 +10,11 @@
 // the ray expressed in i's frame, fl(R_i^T (o - t_i)) and fl(R_i^T d); the
 // transmittance product runs across instances in one register and stops
 // below T_min.  One thread per ray (the 4-wide per-ray traversal): lanes of
-// a warp may be in different instances.
+// a warp may be in different instances.  Each instance's tree is walked
+// nearest child first for every ray set: the instances overlap, so a ray's
+// occluders include other instances' surfaces close to its origin (16
+// instances x 125k Gaussians x 128 directions: 684 ms nearest-first, 700 ms
+// farthest-first).
 #include <math.h>
 #include <string.h>
 
@@ -114,8 +118,7 @@ __global__ void __launch_bounds__(128, RT_SCENE_MIN_BLOCKS) k_scene_trace(const 
                 const InstDev &I = inst[i];
                 const float3 x = make_float3(__fsub_rn(o.x, I.t[0]), __fsub_rn(o.y, I.t[1]), __fsub_rn(o.z, I.t[2]));
                 const float3 ol = rot_t(I.R, x), dl = rot_t(I.R, d);
-                trace_ray_wide_run<false>(I.b, ol, dl, i == lo ? (int32_t)p : -1, T, lg, wc, status,
-                                          far_first(rs));
+                trace_ray_wide_run<false>(I.b, ol, dl, i == lo ? (int32_t)p : -1, T, lg, wc, status, false);
                 continue;
             }
             const TopNode nd = top[ref];
