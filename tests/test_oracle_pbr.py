@@ -3,8 +3,9 @@
 closed-form poles of the frame construction, GGX normalisation, the microfacet
 change of variables (which fixes the factor 4 of Eq. 9), Fresnel and Smith
 limits, reciprocity, SH orthonormality and the addition theorem, bilinear
-environment lookup at pixel centres and across the azimuth seam, and closed
-forms of the Eq. 10 sum (the Fibonacci midpoint rule integrates cos exactly)."""
+environment lookup at pixel centres and across the azimuth seam, closed
+forms of the Eq. 10 sum (the Fibonacci midpoint rule integrates cos exactly),
+and its monotonicity in each visibility."""
 import math
 
 import numpy as np
@@ -207,6 +208,28 @@ def test_pbr_linear_in_light_and_visibility(orc):
     np.testing.assert_allclose(ci, float(np.float32(0.3)) * 0.5 / math.sqrt(math.pi) * cu, rtol=1e-12)
     # a negative indirect radiance is clamped to 0
     assert np.all(orc.pbr(sc, nrm, dict(mat, sh=-sh), hemi, 0 * V, env, cam) == 0)
+
+
+def test_pbr_monotone_in_visibility(orc):
+    """Eq. 10 with indirect light: raising any V[g, k] changes only Gaussian
+    g's colour and never lowers it (non-negative BRDF, direct light and
+    cosine), which is what lets a consumer of a flagged ray's visibility be
+    bounded by the colours of its visibility bounds."""
+    sc, nrm, hemi, mat = _pbr_case(orc)
+    n, K = nrm.shape[0], hemi.shape[0]
+    rng = np.random.default_rng(11)
+    V = rng.uniform(0, 1, (n, K))
+    env = scenes.light_envmap(3).astype(np.float64)
+    cam = np.array([0.5, 4.0, 1.0])
+    assert mat["sh"] is not None
+    c = orc.pbr(sc, nrm, mat, hemi, V, env, cam)
+    V2 = V + rng.uniform(0, 1, (n, K)) * (1 - V)
+    c2 = orc.pbr(sc, nrm, mat, hemi, V2, env, cam)
+    assert np.all(c2 >= c * (1 - 1e-13)) and np.any(c2 > c)
+    V3 = V.copy()
+    V3[3, 5] = 1.0
+    c3 = orc.pbr(sc, nrm, mat, hemi, V3, env, cam)
+    assert np.array_equal(np.delete(c3, 3, 0), np.delete(c, 3, 0)) and np.all(c3[3] >= c[3])
 
 
 def test_pbr_view_from_behind_is_finite(orc):
